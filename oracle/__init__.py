@@ -1,0 +1,244 @@
+"""CPU ORACLE -- test infrastructure only.
+
+Plain, slow restatement of INSPIRIT's schedule evaluation (arxiv 2404.03226),
+used by the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU baseline.
+The library never imports it and it imports nothing from the library: the two
+share only the seeded input generators in ``inputs``.
+
+The arithmetic lives in ``oracle.c`` (single-threaded C, compiled with gcc);
+this module compiles it on demand and wraps it with ctypes.  See the header of
+``oracle.c`` for the definitions and readings each function follows.
+
+Parity status: every function here is pinned by CPU tests (closed forms,
+brute force on tiny DAGs, hand-traced controller cases, bounds and an
+exhaustive optimum); the exact controller decisions on full-size paper-shaped
+workloads are "parity unpinned" beyond those pins because the paper prints no
+schedule to compare against.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+_lock = threading.Lock()
+_lib = None
+
+OK, EINVAL, ENOTTOPO, ENOMEM, EOVERFLOW = 0, 1, 2, 3, 6
+POLICY_INSPIRIT, POLICY_FIFO, POLICY_LEARNED = 0, 1, 2
+MODE_FIFO, MODE_ABILITY, MODE_EFI, MODE_EFI_LOC, MODE_LEARNED = 0, 1, 2, 3, 4
+STATE_INC, STATE_DEC = 0, 1
+MLP_IN, MLP_H = 16, 64
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_i16p = ctypes.POINTER(ctypes.c_int16)
+
+
+class Policy(ctypes.Structure):
+    """Scheduling policy; zero fields take the defaults for P workers (task
+    window, s_inc, s_dec, dec_step = P; c = max(1, P/2); k_inc = P tasks per
+    unit time)."""
+    _fields_ = [("policy", ctypes.c_int32), ("task_window", ctypes.c_int32), ("s_inc", ctypes.c_int32),
+                ("s_dec", ctypes.c_int32), ("dec_step", ctypes.c_int32), ("c", ctypes.c_int32),
+                ("k_inc_tasks", ctypes.c_int64), ("k_inc_ns", ctypes.c_int64)]
+
+
+class Ctrl(ctypes.Structure):
+    _fields_ = [("peak", ctypes.c_int64), ("prev_n", ctypes.c_int64), ("prev_t", ctypes.c_int64),
+                ("count", ctypes.c_int64), ("mode", ctypes.c_int32), ("state", ctypes.c_int32)]
+
+
+class _Trace(ctypes.Structure):
+    _fields_ = [("t", _i64p), ("nready", _i32p), ("mode", _i32p), ("task", _i32p), ("worker", _i32p),
+                ("npop", ctypes.c_int32), ("feat_pop", ctypes.c_int32), ("feat_cap", ctypes.c_int32),
+                ("n_feat", ctypes.c_int32), ("feat_task", _i32p), ("feat", _i32p)]
+
+
+class _Force(ctypes.Structure):
+    _fields_ = [("force_pop", ctypes.c_int32), ("force_task", ctypes.c_int32)]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so."""
+    with _lock:
+        if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+            tmp = _SO + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC])
+            os.replace(tmp, _SO)
+    return _SO
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        lib.orc_check_dag.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int64]
+        lib.orc_ia.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        lib.orc_ie.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, ctypes.c_int64, _i32p]
+        lib.orc_default_unit_time.restype = ctypes.c_int64
+        lib.orc_default_unit_time.argtypes = [ctypes.c_int32, _i64p]
+        lib.orc_resolve_policy.argtypes = [ctypes.POINTER(Policy), ctypes.c_int32, ctypes.c_int64,
+                                           ctypes.POINTER(Policy)]
+        lib.orc_ctrl_step.argtypes = [ctypes.POINTER(Ctrl), ctypes.POINTER(Policy), ctypes.c_int64, ctypes.c_int64]
+        lib.orc_mlp_score.restype = ctypes.c_int64
+        lib.orc_mlp_score.argtypes = [_i16p, _i32p]
+        lib.orc_mlp_nweights.restype = ctypes.c_int32
+        lib.orc_simulate.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int64, ctypes.POINTER(Policy), ctypes.c_int64, _i32p, _i32p, _i16p,
+                                     ctypes.POINTER(_Force), _i32p, _i64p, _i64p, _i64p, ctypes.POINTER(_Trace)]
+        lib.orc_validate.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_int64, _i32p, _i64p, _i64p, ctypes.c_int64, _i32p]
+        lib.orc_optimum.restype = ctypes.c_int64
+        lib.orc_optimum.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_int64, ctypes.c_int64]
+        _lib = lib
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, dtype=np.int64)
+
+
+def check_dag(dag, xfer_ns: int = 0) -> int:
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    return _L().orc_check_dag(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_cpu), _i64p),
+                              _p(_i64(dag.c_gpu), _i64p), xfer_ns)
+
+
+def ia(dag) -> np.ndarray:
+    """Inspiring ability: strict descendant count of every task."""
+    out = np.zeros(max(dag.n, 1), np.int32)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    rc = _L().orc_ia(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(out, _i32p))
+    if rc:
+        raise RuntimeError(f"orc_ia failed: {rc}")
+    return out[:dag.n]
+
+
+def ie(dag, unit_time: int | None = None) -> np.ndarray:
+    """Inspiring efficiency for unit time T (default: default_unit_time)."""
+    T = default_unit_time(dag) if not unit_time else int(unit_time)
+    out = np.zeros(max(dag.n, 1), np.int32)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    rc = _L().orc_ie(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_gpu), _i64p), T, _p(out, _i32p))
+    if rc:
+        raise RuntimeError(f"orc_ie failed: {rc}")
+    return out[:dag.n]
+
+
+def default_unit_time(dag) -> int:
+    """4 x the lower median of the DAG's GPU costs (at least 1)."""
+    cg = _i64(dag.c_gpu) if dag.n > 0 else np.zeros(1, np.int64)
+    return int(_L().orc_default_unit_time(dag.n, _p(cg, _i64p)))
+
+
+def resolve_policy(policy: Policy, n_workers: int, unit_time: int) -> Policy:
+    out = Policy()
+    _L().orc_resolve_policy(ctypes.byref(policy), n_workers, unit_time, ctypes.byref(out))
+    return out
+
+
+def ctrl_step(state: Ctrl, policy: Policy, cur: int, now: int) -> Ctrl:
+    """Apply one Nready-controller judgement in place; returns the state."""
+    _L().orc_ctrl_step(ctypes.byref(state), ctypes.byref(policy), cur, now)
+    return state
+
+
+def mlp_nweights() -> int:
+    return int(_L().orc_mlp_nweights())
+
+
+def mlp_score(weights_k: np.ndarray, feat: np.ndarray) -> int:
+    """Score (units of 1/64) of one integer feature vector; weights are int16 grid numerators."""
+    w = np.ascontiguousarray(weights_k, dtype=np.int16)
+    f = _i32(feat)
+    assert w.size == mlp_nweights() and f.size == MLP_IN
+    return int(_L().orc_mlp_score(_p(w, _i16p), _p(f, _i32p)))
+
+
+def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None = None, ia_=None, ie_=None,
+             mlp_weights=None, force=None, trace: bool = False, feat_pop: int = -1, feat_cap: int = 0):
+    """Run the event simulation; returns a dict with worker/start/end/makespan
+    (and the per-pop trace when requested).  ia_/ie_ default to the oracle's
+    own attributes for unit_time."""
+    pol = policy or Policy()
+    T = int(unit_time) if unit_time else default_unit_time(dag)
+    a = _i32(ia(dag) if ia_ is None else ia_)
+    e = _i32(ie(dag, T) if ie_ is None else ie_)
+    n = dag.n
+    worker = np.zeros(max(n, 1), np.int32)
+    start = np.zeros(max(n, 1), np.int64)
+    end = np.zeros(max(n, 1), np.int64)
+    mk = np.zeros(1, np.int64)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    cc, cg = _i64(dag.c_cpu), _i64(dag.c_gpu)
+    w = None if mlp_weights is None else np.ascontiguousarray(mlp_weights, dtype=np.int16)
+    fobj = None
+    if force is not None:
+        fobj = _Force(int(force[0]), int(force[1]))
+    tr = None
+    bufs = {}
+    if trace or feat_pop >= 0:
+        cap = max(n, 1)
+        bufs = dict(t=np.zeros(cap, np.int64), nready=np.zeros(cap, np.int32), mode=np.zeros(cap, np.int32),
+                    task=np.zeros(cap, np.int32), worker=np.zeros(cap, np.int32),
+                    feat_task=np.zeros(max(feat_cap, 1), np.int32), feat=np.zeros(max(feat_cap, 1) * MLP_IN, np.int32))
+        tr = _Trace(_p(bufs["t"], _i64p), _p(bufs["nready"], _i32p), _p(bufs["mode"], _i32p),
+                    _p(bufs["task"], _i32p), _p(bufs["worker"], _i32p), 0, feat_pop, feat_cap, 0,
+                    _p(bufs["feat_task"], _i32p), _p(bufs["feat"], _i32p))
+    rc = _L().orc_simulate(n, _p(rp, _i32p), _p(ci, _i32p), _p(cc, _i64p), _p(cg, _i64p), machine.n_cpu,
+                           machine.n_gpu, machine.xfer_ns, ctypes.byref(pol), T, _p(a, _i32p), _p(e, _i32p),
+                           None if w is None else _p(w, _i16p), None if fobj is None else ctypes.byref(fobj),
+                           _p(worker, _i32p), _p(start, _i64p), _p(end, _i64p), _p(mk, _i64p),
+                           None if tr is None else ctypes.byref(tr))
+    out = dict(rc=rc, worker=worker[:n], start=start[:n], end=end[:n], makespan=int(mk[0]), ia=a, ie=e,
+               unit_time=T)
+    if tr is not None:
+        k = tr.npop
+        out["trace"] = {key: bufs[key][:k] for key in ("t", "nready", "mode", "task", "worker")}
+        nf = tr.n_feat if feat_pop >= 0 else 0
+        out["feat_task"] = bufs["feat_task"][:nf]
+        out["feat"] = bufs["feat"][:nf * MLP_IN].reshape(nf, MLP_IN)
+    return out
+
+
+def validate(dag, machine, worker, start, end, makespan) -> tuple[int, int]:
+    """(code, task): code 0 if feasible; see orc_validate for the rule codes."""
+    bad = np.zeros(1, np.int32)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    code = _L().orc_validate(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_cpu), _i64p),
+                             _p(_i64(dag.c_gpu), _i64p), machine.n_cpu, machine.n_gpu, machine.xfer_ns,
+                             _p(_i32(worker), _i32p), _p(_i64(start), _i64p), _p(_i64(end), _i64p),
+                             int(makespan), _p(bad, _i32p))
+    return int(code), int(bad[0])
+
+
+def optimum(dag, machine, upper_bound: int = 0) -> int:
+    """Exact minimum makespan by branch and bound (n <= 10 recommended)."""
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    return int(_L().orc_optimum(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_cpu), _i64p),
+                                _p(_i64(dag.c_gpu), _i64p), machine.n_cpu, machine.n_gpu, machine.xfer_ns,
+                                upper_bound))
+
+
+def simulate_batch(batch, machine, policy: Policy | None = None, idx=None, unit_time: int | None = None):
+    """Simulate DAGs of a batch one after another (single thread)."""
+    res = []
+    for d in (range(batch.ndag) if idx is None else idx):
+        res.append(simulate(batch.dag(int(d)), machine, policy, unit_time))
+    return res

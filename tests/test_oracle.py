@@ -1,0 +1,287 @@
+"""CPU pins of the oracle against facts that do not come from the oracle itself:
+the paper's worked statements, closed forms, brute force by path enumeration,
+hand-traced schedules and controller steps, bounds and an exhaustive optimum."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from oracle import brute
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_dag(rng, n, p, cmax=50):
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n) if rng.random() < p]
+    return inputs.make_dag(n, edges, rng.integers(1, cmax, n), rng.integers(1, cmax, n))
+
+
+def _chain(n, c_cpu, c_gpu):
+    return inputs.make_dag(n, [(i, i + 1) for i in range(n - 1)], [c_cpu] * n, [c_gpu] * n)
+
+
+# ------------------------------------------------------------ inspiring ability
+def test_ia_paper_statements():
+    g = json.load(open(os.path.join(GOLD, "attributes_paper.json")))
+    for case in g["cases"]:
+        n = case["n"]
+        edges = [(u, v) for u in range(n) for v in range(u + 1, n)] if case["edges"] == "complete" else case["edges"]
+        d = inputs.make_dag(n, edges, [1] * n, [1] * n)
+        ia = oracle.ia(d)
+        if "ia" in case:
+            assert list(ia) == case["ia"], case["name"]
+        if "ia_source" in case:
+            assert ia[0] == case["ia_source"]
+
+
+def test_ia_closed_forms():
+    for n in (1, 2, 7, 40):
+        assert list(oracle.ia(_chain(n, 3, 1))) == [n - 1 - i for i in range(n)]
+    diamond = inputs.make_dag(4, [(0, 1), (0, 2), (1, 3), (2, 3)], [1] * 4, [1] * 4)
+    assert list(oracle.ia(diamond)) == [3, 1, 1, 0]  # a path count would give 4 for task 0
+    indep = inputs.make_dag(5, [], [1] * 5, [1] * 5)
+    assert list(oracle.ia(indep)) == [0] * 5
+
+
+def test_ia_cholesky8_source():
+    d = inputs.cholesky8().dag(0)
+    ia = oracle.ia(d)
+    assert d.n == 120 and ia[0] == 119  # every task depends on the first POTRF
+    assert ia[-1] == 0  # the last POTRF has no successor
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_ia_matches_path_enumeration(seed):
+    rng = np.random.default_rng(seed)
+    d = _rand_dag(rng, int(rng.integers(1, 13)), float(rng.uniform(0.1, 0.6)))
+    assert list(oracle.ia(d)) == brute.ia(d)
+
+
+# --------------------------------------------------------- inspiring efficiency
+@pytest.mark.parametrize("seed", range(12))
+def test_ie_matches_path_enumeration(seed):
+    rng = np.random.default_rng(100 + seed)
+    d = _rand_dag(rng, int(rng.integers(1, 12)), float(rng.uniform(0.1, 0.6)), cmax=20)
+    for T in (1, 10, 25, 60, 200):
+        assert list(oracle.ie(d, T)) == brute.ie(d, T), T
+
+
+def test_ie_limits():
+    """Too small a unit time gives zero, a large one converges to IA (Sec. 4.2)."""
+    rng = np.random.default_rng(7)
+    for _ in range(5):
+        d = _rand_dag(rng, 30, 0.15)
+        big = int(d.c_gpu.sum())
+        assert list(oracle.ie(d, big)) == list(oracle.ia(d))
+        # every counted task finishes after at least two executions (v and itself)
+        assert not oracle.ie(d, int(d.c_gpu.min())).any()
+
+
+def test_ie_chain_closed_form():
+    for n, c, T in [(10, 5, 23), (10, 5, 5), (10, 5, 50), (12, 7, 1000), (6, 3, 2)]:
+        ie = oracle.ie(_chain(n, 100, c), T)
+        assert list(ie) == [max(0, min(n - 1 - i, T // c - 1)) for i in range(n)]
+
+
+def test_ie_uses_longest_path():
+    # 0 -> 1 -> 2 and 0 -> 2: task 2 is reached at 2 over the short path but
+    # only at 12 over the long one; it fits in T=5 only under a shortest-path
+    # reading, so its inspiring efficiency count from task 0 is 0.
+    d = inputs.make_dag(3, [(0, 1), (0, 2), (1, 2)], [1, 1, 1], [1, 10, 1])
+    assert list(oracle.ie(d, 5)) == [0, 0, 0]
+    assert list(oracle.ie(d, 12)) == [2, 1, 0]
+
+
+def test_default_unit_time():
+    d = inputs.make_dag(4, [], [1] * 4, [3, 1, 2, 5])
+    assert oracle.default_unit_time(d) == 8  # 4 x lower median (2)
+    d = inputs.make_dag(3, [], [1] * 3, [9, 1, 4])
+    assert oracle.default_unit_time(d) == 16
+
+
+# ------------------------------------------------------------- the controller
+def test_controller_hand_traced():
+    g = json.load(open(os.path.join(GOLD, "controller_hand_traced.json")))
+    for seqn in g["sequences"]:
+        pol = oracle.Policy(0, **seqn["policy"])
+        st = oracle.Ctrl(0, 0, 0, 0, oracle.MODE_FIFO, oracle.STATE_INC)
+        for k, step in enumerate(seqn["steps"]):
+            oracle.ctrl_step(st, pol, step["cur"], step["now"])
+            got = dict(mode=st.mode, peak=st.peak, count=st.count, prev_n=st.prev_n, prev_t=st.prev_t)
+            exp = {key: step[key] for key in got}
+            assert got == exp, (k, step["_why"])
+
+
+def test_policy_defaults():
+    p = oracle.resolve_policy(oracle.Policy(), 10, 12345)
+    assert (p.task_window, p.s_inc, p.s_dec, p.dec_step, p.c, p.k_inc_tasks, p.k_inc_ns) == (10, 10, 10, 10, 5, 10, 12345)
+    p = oracle.resolve_policy(oracle.Policy(0, 3, 0, 0, 0, 0, 0, 0), 1, 7)
+    assert (p.task_window, p.c, p.k_inc_tasks) == (3, 1, 1)
+
+
+# ------------------------------------------------------------- the simulation
+def _policy(name):
+    return oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO}[name])
+
+
+def test_simulation_hand_traced():
+    g = json.load(open(os.path.join(GOLD, "sim_hand_traced.json")))
+    for case in g["cases"]:
+        d = inputs.make_dag(case["n"], case["edges"], case["c_cpu"], case["c_gpu"])
+        m = inputs.Machine(*case["machine"])
+        for pname in case["policies"]:
+            r = oracle.simulate(d, m, _policy(pname), trace=True)
+            assert r["rc"] == 0
+            assert list(r["worker"]) == case["worker"], (case["name"], pname)
+            assert list(r["start"]) == case["start"], (case["name"], pname)
+            assert list(r["end"]) == case["end"], (case["name"], pname)
+            assert r["makespan"] == case["makespan"]
+            if "order" in case:
+                assert list(r["trace"]["task"]) == case["order"]
+            if "modes" in case:
+                assert list(r["trace"]["mode"]) == case["modes"]
+
+
+@pytest.mark.parametrize("policy", ["inspirit", "fifo"])
+def test_one_worker_sums(policy):
+    """A chain, or independent tasks, on one worker: makespan = sum of costs."""
+    rng = np.random.default_rng(3)
+    for n in (1, 5, 33):
+        costs = rng.integers(1, 1000, n)
+        chain = inputs.make_dag(n, [(i, i + 1) for i in range(n - 1)], costs, costs)
+        indep = inputs.make_dag(n, [], costs, costs)
+        for d in (chain, indep):
+            for m in (inputs.Machine(1, 0, 77), inputs.Machine(0, 1, 77)):
+                assert oracle.simulate(d, m, _policy(policy))["makespan"] == int(costs.sum())
+
+
+def test_chain_on_one_kind():
+    """A chain where the GPU is always faster stays on the GPU: makespan = sum of GPU costs."""
+    n = 17
+    d = _chain(n, 100, 7)
+    r = oracle.simulate(d, inputs.Machine(4, 1, 1000), _policy("inspirit"))
+    assert r["makespan"] == 7 * n and set(r["worker"]) == {4}
+
+
+@pytest.mark.parametrize("P,n,c", [(3, 10, 7), (4, 4, 5), (5, 23, 11), (8, 1, 3)])
+def test_identical_workers_independent_tasks(P, n, c):
+    d = inputs.make_dag(n, [], [c] * n, [c] * n)
+    for pol in ("fifo", "inspirit"):
+        assert oracle.simulate(d, inputs.Machine(P, 0, 0), _policy(pol))["makespan"] == -(-n // P) * c
+
+
+def _lower_bound(d, m):
+    cmin = np.minimum(d.c_cpu, d.c_gpu) if m.n_gpu and m.n_cpu else (d.c_cpu if m.n_cpu else d.c_gpu)
+    cp = np.zeros(d.n, np.int64)
+    for u in range(d.n - 1, -1, -1):
+        succ = d.col_idx[d.row_ptr[u]:d.row_ptr[u + 1]]
+        cp[u] = cmin[u] + (cp[succ].max() if len(succ) else 0)
+    return max(int(cp.max()) if d.n else 0, -(-int(cmin.sum()) // m.n_workers))
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_random_schedules_valid_and_bounded(seed):
+    rng = np.random.default_rng(1000 + seed)
+    d = _rand_dag(rng, int(rng.integers(2, 60)), float(rng.uniform(0.02, 0.3)), cmax=100)
+    m = inputs.Machine(int(rng.integers(1, 4)), int(rng.integers(0, 3)), int(rng.integers(0, 40)))
+    for pol in ("inspirit", "fifo"):
+        r = oracle.simulate(d, m, _policy(pol))
+        assert r["rc"] == 0
+        assert oracle.validate(d, m, r["worker"], r["start"], r["end"], r["makespan"]) == (0, -1)
+        assert r["makespan"] >= _lower_bound(d, m)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_exhaustive_optimum(seed):
+    """makespan >= exact optimum >= lower bound on DAGs of at most 8 tasks."""
+    rng = np.random.default_rng(2000 + seed)
+    d = _rand_dag(rng, int(rng.integers(2, 9)), 0.3, cmax=30)
+    m = inputs.Machine(int(rng.integers(1, 3)), 1, int(rng.integers(0, 10)))
+    best = oracle.optimum(d, m)
+    assert best >= _lower_bound(d, m)
+    for pol in ("inspirit", "fifo"):
+        assert oracle.simulate(d, m, _policy(pol))["makespan"] >= best
+
+
+def test_optimum_known_cases():
+    # two independent tasks of 5 on two workers: 5; a chain of three 2-ns tasks
+    # across CPU/GPU with a 100 ns transfer: stays on one worker, 6
+    assert oracle.optimum(inputs.make_dag(2, [], [5, 5], [5, 5]), inputs.Machine(1, 1, 0)) == 5
+    assert oracle.optimum(_chain(3, 2, 2), inputs.Machine(1, 1, 100)) == 6
+    assert oracle.optimum(_chain(3, 9, 2), inputs.Machine(1, 1, 100)) == 6
+
+
+def test_validator_catches_planted_errors():
+    d = inputs.make_dag(3, [(0, 1), (1, 2)], [4, 4, 4], [2, 2, 2])
+    m = inputs.Machine(1, 1, 10)
+    r = oracle.simulate(d, m, _policy("fifo"))
+    w, s, e = r["worker"].copy(), r["start"].copy(), r["end"].copy()
+    assert oracle.validate(d, m, w, s, e, r["makespan"])[0] == 0
+    s2, e2 = s.copy(), e.copy()
+    s2[2] -= 1; e2[2] -= 1
+    assert oracle.validate(d, m, w, s2, e2, r["makespan"] - 1)[0] == 3
+    w2 = w.copy(); w2[1] = 0
+    assert oracle.validate(d, m, w2, s, e, r["makespan"])[0] == 2
+    assert oracle.validate(d, m, w, s, e, r["makespan"] + 1)[0] == 5
+
+
+def test_cholesky8_bounds_and_validity():
+    d = inputs.cholesky8().dag(0)
+    m = inputs.MACHINE_CHOLESKY8
+    for pol in ("inspirit", "fifo"):
+        r = oracle.simulate(d, m, _policy(pol))
+        assert oracle.validate(d, m, r["worker"], r["start"], r["end"], r["makespan"]) == (0, -1)
+        assert r["makespan"] >= 2_040_000  # critical path at the fastest cost: 2040 us
+    assert _lower_bound(d, m) == 2_040_000
+
+
+def test_check_dag_errors():
+    good = inputs.make_dag(3, [(0, 1), (1, 2)], [1, 1, 1], [1, 1, 1])
+    assert oracle.check_dag(good) == oracle.OK
+    bad = inputs.make_dag(3, [(0, 1)], [1, 0, 1], [1, 1, 1])
+    assert oracle.check_dag(bad) == oracle.EINVAL
+    back = inputs.Dag(2, np.array([0, 0, 1], np.int32), np.array([0], np.int32), np.zeros(2, np.uint8),
+                      np.ones(2, np.int64), np.ones(2, np.int64))
+    assert oracle.check_dag(back) == oracle.ENOTTOPO
+    dup = inputs.Dag(2, np.array([0, 2, 2], np.int32), np.array([1, 1], np.int32), np.zeros(2, np.uint8),
+                     np.ones(2, np.int64), np.ones(2, np.int64))
+    assert oracle.check_dag(dup) == oracle.EINVAL
+    huge = inputs.make_dag(2, [], [1 << 53, (1 << 53) + 1], [1, 1])
+    assert oracle.check_dag(huge) == oracle.EOVERFLOW
+
+
+# ----------------------------------------------------------------- the scorer
+def test_mlp_score_closed_form():
+    nw = oracle.mlp_nweights()
+    assert nw == 16 * 64 + 64 + 64 * 64 + 64 + 64 + 1
+    w = np.zeros(nw, np.int16)
+    assert oracle.mlp_score(w, np.zeros(16, np.int32)) == 0
+    # one path: W1[0][0] = 64 (1.0), W2[0][0] = 64, W3[0] = 128 (2.0), b3 = 5
+    W1 = 0; b1 = 16 * 64; W2 = b1 + 64; b2 = W2 + 64 * 64; W3 = b2 + 64; b3 = W3 + 64
+    w[W1 + 0] = 64; w[W2 + 0] = 64; w[W3 + 0] = 128; w[b3] = 5
+    f = np.zeros(16, np.int32); f[0] = 7
+    assert oracle.mlp_score(w, f) == 128 * 7 + 5
+    f[0] = 200; w[W1 + 0] = 128  # hidden 400 clamps at 255, then 255
+    assert oracle.mlp_score(w, f) == 128 * 255 + 5
+    w[b1 + 0] = -100 * 64  # negative pre-activation: relu gives 0
+    assert oracle.mlp_score(w, f) == 128 * 255 + 5 - 0 if 400 - 100 >= 255 else True
+    w[W1 + 0] = 1; w[b1 + 0] = -63  # (200 - 63) / 64 = 2.14 -> floor 2
+    assert oracle.mlp_score(w, f) == 128 * 2 + 5
+
+
+def test_mlp_score_matches_float_network():
+    """The integer restatement equals an fp64 evaluation of the same network."""
+    rng = np.random.default_rng(5)
+    nw = oracle.mlp_nweights()
+    for _ in range(20):
+        k = rng.integers(-128, 129, nw).astype(np.int16)
+        f = rng.integers(0, 256, 16)
+        W1 = k[:1024].reshape(16, 64) / 64.0; b1 = k[1024:1088] / 64.0
+        W2 = k[1088:5184].reshape(64, 64) / 64.0; b2 = k[5184:5248] / 64.0
+        W3 = k[5248:5312] / 64.0; b3 = k[5312] / 64.0
+        h1 = np.clip(np.floor(np.maximum(f @ W1 + b1, 0)), 0, 255)
+        h2 = np.clip(np.floor(np.maximum(h1 @ W2 + b2, 0)), 0, 255)
+        assert oracle.mlp_score(k, f) == int(round((h2 @ W3 + b3) * 64))
