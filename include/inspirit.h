@@ -1,0 +1,168 @@
+/*
+ * inspirit.h -- C ABI of the B300 INSPIRIT schedule evaluator.
+ *
+ * Evaluates the INSPIRIT scheduling policy (arxiv 2404.03226) on task DAGs and
+ * a modelled heterogeneous machine, entirely in CUDA kernels for sm_103a:
+ *
+ *   insp_attributes*  inspiring ability and inspiring efficiency of every task
+ *                     (Sec. 4.2 definitions, Sec. 4.3 computation);
+ *   insp_simulate*    the list-scheduling run (Sec. 2.1 push/pop over per-worker
+ *                     queues, Sec. 4.1 steps 1-3, Sec. 4.4 Nready regulation by
+ *                     adaptive priority) returning each task's worker, start and
+ *                     end time and each DAG's makespan.
+ *
+ * Conventions for every entry point
+ *   - Status: every function returns INSP_OK (0) or one of the INSP_E* codes
+ *     below; nothing aborts.  insp_last_error() returns a thread-local message
+ *     for the last failure on the calling thread.
+ *   - Ownership: load functions copy their inputs into library-owned device
+ *     memory; the caller may free its arrays after the call returns.  Output
+ *     arrays are caller-owned.
+ *   - Pointers: inputs and outputs may be host or device pointers (detected
+ *     with cudaPointerGetAttributes).  When every output is a device pointer
+ *     the call only enqueues work on `stream` and returns; results and the
+ *     per-DAG status (insp_batch_status) are valid after the caller
+ *     synchronises the stream.  When any array is a host pointer the call
+ *     stages through device buffers, synchronises `stream` and returns the
+ *     final status, including device-side errors.
+ *   - Streams: `stream` is a cudaStream_t passed as void*; NULL means the
+ *     legacy default stream.  Calls on one batch must not overlap in time.
+ *   - Numbering: tasks of a DAG are 0..n-1 and every edge (u, v) must satisfy
+ *     u < v (ids are a topological order); successor lists are strictly
+ *     increasing.  Workers 0..n_cpu-1 are CPUs, n_cpu..n_cpu+n_gpu-1 GPUs.
+ *   - Time: all costs and times are int64 nanoseconds; costs are >= 1.
+ */
+#ifndef INSPIRIT_H
+#define INSPIRIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define INSP_OK 0
+#define INSP_EINVAL 1    /* malformed argument: bad CSR, id out of range, duplicate or unsorted successor, cost < 1, type >= n_types, bad size */
+#define INSP_ENOTTOPO 2  /* an edge (u, v) with v <= u: ids are not a topological order */
+#define INSP_ENOMEM 3    /* device or host allocation failed */
+#define INSP_ECUDA 4     /* a CUDA runtime call failed (message in insp_last_error) */
+#define INSP_ETIMEOUT 5  /* a bounded device-side wait gave up (no GPU hang; the DAG's outputs are invalid) */
+#define INSP_EOVERFLOW 6 /* sum over tasks of (max cost + transfer) exceeds 2^54 ns, so times could overflow */
+
+/* ---------------------------------------------------------------- policy */
+#define INSP_POLICY_INSPIRIT 0 /* adaptive priority by the Nready controller (default) */
+#define INSP_POLICY_FIFO 1     /* DMDA without priorities: pop in push order (Sec. 2.1) */
+#define INSP_POLICY_LEARNED 2  /* controller runs, but the pop takes the learned scorer's best candidate */
+
+/* Controller parameters of Sec. 4.4 (the paper gives no values).  A zero
+ * field takes its default for P = n_cpu + n_gpu workers and the DAG's default
+ * unit time T (4 x the lower median of its GPU costs):
+ *   task_window = s_inc = s_dec = dec_step = P, c = max(1, P / 2),
+ *   k_inc = k_inc_tasks / k_inc_ns = P tasks per T ns. */
+typedef struct {
+    int32_t policy;      /* INSP_POLICY_* */
+    int32_t task_window; /* re-judge the state when Nready moved by at least this much */
+    int32_t s_inc;       /* minimum Nready growth before the slope is tested (ascending state) */
+    int32_t s_dec;       /* stage size of the descending peak threshold */
+    int32_t dec_step;    /* INC if Nready >= peak - dec_step, else DEC */
+    int32_t c;           /* slack below the next stage threshold for efficiency+locality picks */
+    int64_t k_inc_tasks; /* ascending slope threshold, numerator (tasks) */
+    int64_t k_inc_ns;    /* ascending slope threshold, denominator (ns) */
+} insp_policy;
+
+/* --------------------------------------------------------------- objects */
+typedef struct insp_machine insp_machine; /* workers, transfer cost, policy, scorer */
+typedef struct insp_batch insp_batch;     /* one or more DAGs resident in device memory */
+typedef struct insp_batch insp_dag;       /* a batch holding exactly one DAG */
+
+/* Create a machine of n_cpu CPU workers (memory node 0) and n_gpu GPU workers
+ * (GPU g is memory node 1+g); an edge whose two tasks run on different memory
+ * nodes costs xfer_ns before the successor can start (DMDA's transfer-aware
+ * placement, Sec. 2.1).  1 <= n_cpu + n_gpu <= 64, xfer_ns >= 0.  `policy`
+ * may be NULL (all defaults).  Errors: INSP_EINVAL, INSP_ENOMEM. */
+int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy,
+                        insp_machine **out);
+void insp_machine_destroy(insp_machine *m);
+
+/* Install the learned proposal scorer used by INSP_POLICY_LEARNED: an MLP
+ * 16 -> 64 -> 64 -> 1 with BF16 weights and FP32 accumulation (no
+ * counterpart in the paper).  `bf16_weights` holds, in this order, W1[16][64],
+ * b1[64], W2[64][64], b2[64], W3[64], b3[1] as raw BF16 bit patterns
+ * (nbytes = 5313 * 2); every value must be k / 64 with integer |k| <= 128.
+ * Host pointer.  Errors: INSP_EINVAL (size or off-grid value). */
+int insp_set_scorer(insp_machine *m, const uint16_t *bf16_weights, size_t nbytes);
+
+/* Load one DAG of n tasks (CSR, Sec. 2.1 task graph).
+ *   row_ptr[n+1] int32, row_ptr[0] = 0, non-decreasing; col_idx[row_ptr[n]]
+ *   int32 successor ids; type[n] uint8 < n_types (<= 64);
+ *   type_cost[n_types][2] int64 (CPU ns, GPU ns) used when task_cost is NULL;
+ *   task_cost[n][2] int64 per-task (CPU ns, GPU ns), overrides type_cost.
+ * Validation runs on the device; errors: INSP_EINVAL, INSP_ENOTTOPO,
+ * INSP_EOVERFLOW, INSP_ENOMEM, INSP_ECUDA.  n <= 2^24 - 1.  Synchronous. */
+int insp_dag_load_csr(insp_machine *m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                      const uint8_t *type, int32_t n_types, const int64_t *type_cost, const int64_t *task_cost,
+                      insp_dag **out);
+
+/* Load ndag DAGs at once (the batched form).  Arrays are the per-DAG arrays
+ * of insp_dag_load_csr concatenated:
+ *   task_base[ndag+1], edge_base[ndag+1] int64 prefix sums of task and edge
+ *   counts; row_ptr[task_base[ndag] + ndag]: DAG d's n_d+1 local offsets start
+ *   at task_base[d] + d; col_idx[edge_base[ndag]] local successor ids;
+ *   type[task_base[ndag]]; type_cost[ndag][n_types][2] (one table per DAG) or
+ *   NULL when task_cost[task_base[ndag]][2] is given.
+ * The first invalid DAG's error is returned.  Synchronous. */
+int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *task_base, const int64_t *edge_base,
+                        const int32_t *row_ptr, const int32_t *col_idx, const uint8_t *type, int32_t n_types,
+                        const int64_t *type_cost, const int64_t *task_cost, insp_batch **out);
+void insp_batch_destroy(insp_batch *b);
+void insp_dag_destroy(insp_dag *d);
+
+/* Inspiring ability and efficiency (Sec. 4.2, Sec. 4.3):
+ *   ia[t] = number of strict descendants of t (the dependencies its completion
+ *           eventually releases);
+ *   ie[t] = number of strict descendants u whose longest path from the start
+ *           of t, over GPU execution times with t's own time included, fits in
+ *           the unit time T (every path from t to u takes at most T).
+ * unit_time_ns <= 0 selects the DAG's default T (4 x lower median GPU cost).
+ * ia, ie: int32[n] (batch: int32[task_base[ndag]] in concatenated order). */
+int insp_attributes(insp_dag *d, int64_t unit_time_ns, int32_t *ia, int32_t *ie, void *stream);
+/* unit_time_ns: int64[ndag] per-DAG unit times (host or device), or NULL for defaults. */
+int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, void *stream);
+
+/* The schedule (Sec. 2.1 push/pop, Sec. 4.4), with the machine's policy:
+ *   - completions at time t are processed together; released tasks are pushed
+ *     in ascending id to the worker with the earliest expected finish
+ *     (max(now, busy) + queued work, data arrival incl. transfer, plus cost;
+ *     ties to the lowest worker);
+ *   - idle workers pop in ascending worker id; the Nready controller picks
+ *     FIFO / highest IA / highest IE / local-then-highest IE (ties: lowest id);
+ *   - a task starts when its worker pops it and its data has arrived.
+ * Inputs ia, ie: int32 per task (from insp_attributes or the caller's own).
+ * Outputs: worker int32, start int64, end int64 per task; makespan int64 per DAG. */
+int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                  int64_t *end, int64_t *makespan, void *stream);
+int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                        int64_t *end, int64_t *makespan, void *stream);
+
+/* The same simulation launched once per DAG (one warp on the GPU per launch,
+ * serial on `stream`): the unbatched form used as the throughput baseline. */
+int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                          int64_t *end, int64_t *makespan, void *stream);
+
+/* Per-DAG device-side status of the last attributes / simulate call on the
+ * batch (INSP_OK or INSP_ETIMEOUT), copied to the host array status[ndag].
+ * Synchronises the batch's last stream.  Returns the first non-OK status. */
+int insp_batch_status(insp_batch *b, int32_t *status);
+
+/* Batch facts: number of DAGs, total tasks, total edges. */
+int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges);
+
+/* Thread-local description of the last error on the calling thread ("" if none). */
+const char *insp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* INSPIRIT_H */

@@ -56,31 +56,33 @@ enum { ST_INC = 0, ST_DEC = 1 };
 
 EXPORT int orc_check_dag(int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                          const int64_t *c_cpu, const int64_t *c_gpu, int64_t xfer) {
+    /* Precedence when several rules fail: malformed input (EINVAL) first, then
+     * a non-topological numbering, then a possible time overflow. */
     if (n < 0 || xfer < 0) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
+    int bad = 0, nottopo = 0, overflow = 0;
     if (row_ptr[0] != 0) return ORC_EINVAL;
     for (int32_t u = 0; u < n; ++u)
         if (row_ptr[u + 1] < row_ptr[u]) return ORC_EINVAL;
     for (int32_t u = 0; u < n; ++u) {
         for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
             int32_t v = col_idx[e];
-            if (v < 0 || v >= n) return ORC_EINVAL;
-        }
-    }
-    for (int32_t u = 0; u < n; ++u) {
-        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-            if (col_idx[e] <= u) return ORC_ENOTTOPO;
-            if (e > row_ptr[u] && col_idx[e] <= col_idx[e - 1]) return ORC_EINVAL;
+            if (v < 0 || v >= n) bad = 1;
+            else if (e > row_ptr[u] && v <= col_idx[e - 1]) bad = 1;
+            else if (v <= u) nottopo = 1;
         }
     }
     int64_t total = 0;
     for (int32_t t = 0; t < n; ++t) {
-        if (c_cpu[t] < 1 || c_gpu[t] < 1) return ORC_EINVAL;
+        if (c_cpu[t] < 1 || c_gpu[t] < 1) { bad = 1; continue; }
         int64_t c = c_cpu[t] > c_gpu[t] ? c_cpu[t] : c_gpu[t];
-        if (c > TIME_BOUND || xfer > TIME_BOUND) return ORC_EOVERFLOW;
-        total += c + xfer;
-        if (total > TIME_BOUND) return ORC_EOVERFLOW;
+        if (c > TIME_BOUND || xfer > TIME_BOUND) { overflow = 1; continue; }
+        if (total <= TIME_BOUND) total += c + xfer;
     }
+    if (total > TIME_BOUND) overflow = 1;
+    if (bad) return ORC_EINVAL;
+    if (nottopo) return ORC_ENOTTOPO;
+    if (overflow) return ORC_EOVERFLOW;
     return ORC_OK;
 }
 

@@ -1,0 +1,97 @@
+"""B300-native evaluation of INSPIRIT's adaptive-priority list scheduling
+(arxiv 2404.03226).
+
+The work runs in CUDA kernels for sm_103a behind the C ABI of
+``include/inspirit.h`` (libinspirit.so, built in-tree).  ``_lib`` binds that
+ABI one function per entry point; the classes below only hold handles and
+torch output tensors.  There is no CPU fallback: without the CUDA library or a
+GPU the calls raise.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import (INSP_POLICY_FIFO, INSP_POLICY_INSPIRIT, INSP_POLICY_LEARNED, InspError,  # noqa: F401
+                   insp_policy)
+
+__all__ = ["Machine", "DagBatch", "InspError", "insp_policy", "INSP_POLICY_INSPIRIT", "INSP_POLICY_FIFO",
+           "INSP_POLICY_LEARNED"]
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Machine:
+    """A modelled machine: n_cpu CPU workers, n_gpu GPU workers, a transfer
+    cost between memory nodes, and the scheduling policy."""
+
+    def __init__(self, n_cpu: int, n_gpu: int, xfer_ns: int, policy: insp_policy | None = None):
+        self.n_cpu, self.n_gpu, self.xfer_ns = n_cpu, n_gpu, xfer_ns
+        self.handle = _lib.insp_machine_create(n_cpu, n_gpu, xfer_ns, policy)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.insp_machine_destroy(h)
+            self.handle = None
+
+
+@dataclass
+class Schedule:
+    worker: "object"
+    start: "object"
+    end: "object"
+    makespan: "object"
+
+
+class DagBatch:
+    """DAGs resident in device memory.  `src` provides the batch arrays
+    (task_base, edge_base, row_ptr, col_idx, type, n_types, type_cost,
+    task_cost) as numpy arrays; see insp_batch_load_csr."""
+
+    def __init__(self, machine: Machine, src):
+        self.machine = machine
+        self.ndag = int(src.ndag)
+        tc = None if src.task_cost is None else _np(src.task_cost, np.int64)
+        self.handle = _lib.insp_batch_load_csr(
+            machine.handle, self.ndag, _np(src.task_base, np.int64), _np(src.edge_base, np.int64),
+            _np(src.row_ptr, np.int32), _np(src.col_idx, np.int32), _np(src.type, np.uint8), int(src.n_types),
+            _np(src.type_cost, np.int64), tc)
+        self.ndag, self.n_tasks, self.n_edges = _lib.insp_batch_info(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.insp_batch_destroy(h)
+            self.handle = None
+
+    # torch tensors on the current CUDA device
+    def _out(self, n, dtype):
+        import torch
+        return torch.empty(max(n, 1), dtype=dtype, device="cuda")[:n]
+
+    def attributes(self, unit_time_ns=None, stream=None):
+        """(ia, ie) int32 CUDA tensors; unit_time_ns: None, or int64 array per DAG."""
+        import torch
+        ia = self._out(self.n_tasks, torch.int32)
+        ie = self._out(self.n_tasks, torch.int32)
+        ut = None if unit_time_ns is None else _np(unit_time_ns, np.int64)
+        _lib.insp_attributes_batch(self.handle, ut, ia, ie, stream or torch.cuda.current_stream())
+        return ia, ie
+
+    def simulate(self, ia, ie, stream=None, per_dag: bool = False) -> Schedule:
+        import torch
+        sch = Schedule(self._out(self.n_tasks, torch.int32), self._out(self.n_tasks, torch.int64),
+                       self._out(self.n_tasks, torch.int64), self._out(self.ndag, torch.int64))
+        f = _lib.insp_simulate_per_dag if per_dag else _lib.insp_simulate_batch
+        f(self.handle, ia, ie, sch.worker, sch.start, sch.end, sch.makespan, stream or torch.cuda.current_stream())
+        return sch
+
+    def status(self) -> np.ndarray:
+        st = np.zeros(max(self.ndag, 1), np.int32)
+        _lib.insp_batch_status(self.handle, st)
+        return st[:self.ndag]

@@ -1,0 +1,178 @@
+"""ctypes binding of libinspirit.so: the C ABI of include/inspirit.h, one Python
+function per C entry point with the same name.  Arguments are marshalled
+(numpy arrays and torch tensors become raw pointers); nothing is computed here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+INSP_OK, INSP_EINVAL, INSP_ENOTTOPO, INSP_ENOMEM, INSP_ECUDA, INSP_ETIMEOUT, INSP_EOVERFLOW = range(7)
+INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO, INSP_POLICY_LEARNED = 0, 1, 2
+ERROR_NAMES = {0: "INSP_OK", 1: "INSP_EINVAL", 2: "INSP_ENOTTOPO", 3: "INSP_ENOMEM", 4: "INSP_ECUDA",
+               5: "INSP_ETIMEOUT", 6: "INSP_EOVERFLOW"}
+
+_vp = ctypes.c_void_p
+_i32, _i64 = ctypes.c_int32, ctypes.c_int64
+
+
+class insp_policy(ctypes.Structure):
+    _fields_ = [("policy", _i32), ("task_window", _i32), ("s_inc", _i32), ("s_dec", _i32), ("dec_step", _i32),
+                ("c", _i32), ("k_inc_tasks", _i64), ("k_inc_ns", _i64)]
+
+
+class InspError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_PROTOS = {
+    "insp_last_error": (ctypes.c_char_p, []),
+    "insp_machine_create": (ctypes.c_int, [_i32, _i32, _i64, ctypes.POINTER(insp_policy), ctypes.POINTER(_vp)]),
+    "insp_machine_destroy": (None, [_vp]),
+    "insp_set_scorer": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "insp_dag_load_csr": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
+    "insp_batch_load_csr": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, ctypes.POINTER(_vp)]),
+    "insp_batch_destroy": (None, [_vp]),
+    "insp_dag_destroy": (None, [_vp]),
+    "insp_attributes": (ctypes.c_int, [_vp, _i64, _vp, _vp, _vp]),
+    "insp_attributes_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "insp_simulate": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_simulate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
+    "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+}
+
+
+def so_path() -> str:
+    return _build.SO
+
+
+def lib():
+    """Load libinspirit.so (compiling it first if the sources are newer).
+    Raises if the CUDA library cannot be built or loaded: there is no fallback."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libinspirit.so missing at {path}")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in _PROTOS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def symbols() -> list[str]:
+    return list(_PROTOS)
+
+
+def last_error() -> str:
+    return lib().insp_last_error().decode()
+
+
+def check(rc: int) -> None:
+    if rc != INSP_OK:
+        raise InspError(rc, last_error())
+
+
+def ptr(x):
+    """Raw pointer of a numpy array, torch tensor or None."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if hasattr(x, "ctypes"):
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+# ------------------------------------------------------ same-name wrappers
+def insp_machine_create(n_cpu: int, n_gpu: int, xfer_ns: int, policy: insp_policy | None = None):
+    h = _vp()
+    check(lib().insp_machine_create(n_cpu, n_gpu, xfer_ns, None if policy is None else ctypes.byref(policy),
+                                    ctypes.byref(h)))
+    return h
+
+
+def insp_machine_destroy(m) -> None:
+    lib().insp_machine_destroy(m)
+
+
+def insp_set_scorer(m, bf16_weights) -> None:
+    check(lib().insp_set_scorer(m, ptr(bf16_weights), bf16_weights.nbytes if hasattr(bf16_weights, "nbytes")
+                                else bf16_weights.numel() * bf16_weights.element_size()))
+
+
+def insp_dag_load_csr(m, n, row_ptr, col_idx, type, n_types, type_cost, task_cost):
+    h = _vp()
+    check(lib().insp_dag_load_csr(m, n, ptr(row_ptr), ptr(col_idx), ptr(type), n_types, ptr(type_cost),
+                                  ptr(task_cost), ctypes.byref(h)))
+    return h
+
+
+def insp_batch_load_csr(m, ndag, task_base, edge_base, row_ptr, col_idx, type, n_types, type_cost, task_cost):
+    h = _vp()
+    check(lib().insp_batch_load_csr(m, ndag, ptr(task_base), ptr(edge_base), ptr(row_ptr), ptr(col_idx), ptr(type),
+                                    n_types, ptr(type_cost), ptr(task_cost), ctypes.byref(h)))
+    return h
+
+
+def insp_batch_destroy(b) -> None:
+    lib().insp_batch_destroy(b)
+
+
+def insp_dag_destroy(d) -> None:
+    lib().insp_dag_destroy(d)
+
+
+def insp_attributes(d, unit_time_ns: int, ia, ie, stream=None) -> None:
+    check(lib().insp_attributes(d, unit_time_ns, ptr(ia), ptr(ie), stream_ptr(stream)))
+
+
+def insp_attributes_batch(b, unit_time_ns, ia, ie, stream=None) -> None:
+    check(lib().insp_attributes_batch(b, ptr(unit_time_ns), ptr(ia), ptr(ie), stream_ptr(stream)))
+
+
+def insp_simulate(d, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    check(lib().insp_simulate(d, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                              stream_ptr(stream)))
+
+
+def insp_simulate_batch(b, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    check(lib().insp_simulate_batch(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                                    stream_ptr(stream)))
+
+
+def insp_simulate_per_dag(b, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    check(lib().insp_simulate_per_dag(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                                      stream_ptr(stream)))
+
+
+def insp_batch_status(b, status=None) -> int:
+    return int(lib().insp_batch_status(b, ptr(status)))
+
+
+def insp_batch_info(b) -> tuple[int, int, int]:
+    nd, nt, ne = _i32(), _i64(), _i64()
+    check(lib().insp_batch_info(b, ctypes.byref(nd), ctypes.byref(nt), ctypes.byref(ne)))
+    return nd.value, nt.value, ne.value

@@ -1,0 +1,561 @@
+// Host runtime behind the C ABI of include/inspirit.h: object lifetimes,
+// device residency of the DAGs, scratch sizing, launch configuration and
+// host/device pointer staging.  All scheduling arithmetic runs in the kernels.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+#define INSP_API extern "C" __attribute__((visibility("default")))
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CU(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) return fail(INSP_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device buffer owned by the library.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {
+        if (n <= bytes && p) return INSP_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return fail(INSP_ENOMEM, "cudaMalloc(" + std::to_string(n) + " bytes): " + cudaGetErrorString(e));
+        }
+        bytes = n;
+        return INSP_OK;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DeviceInfo {
+    int sms = 0;
+    int occ_sim = 0, occ_ia = 0, occ_ie = 0;
+};
+
+int device_info(DeviceInfo &di) {
+    int dev = 0;
+    CU(cudaGetDevice(&dev));
+    CU(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
+    di.occ_sim = insp::sim_occupancy();
+    di.occ_ia = insp::ia_occupancy();
+    di.occ_ie = insp::ie_occupancy();
+    if (di.occ_sim < 1 || di.occ_ia < 1 || di.occ_ie < 1) return fail(INSP_ECUDA, "occupancy query failed");
+    return INSP_OK;
+}
+
+}  // namespace
+
+struct insp_machine {
+    int32_t n_cpu = 0, n_gpu = 0;
+    int64_t xfer = 0;
+    insp_policy pol{};
+    bool has_scorer = false;
+};
+
+struct insp_batch {
+    insp_machine mach;
+    int32_t ndag = 0, n_types = 1;
+    int64_t n_total = 0, m_total = 0;
+    std::vector<int64_t> h_task_base, h_edge_base;
+    DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
+    DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
+    bool has_task_cost = false;
+    int32_t max_n = 0, max_span_h = 0, W = 1;
+    int64_t max_unit_def = 1, n_items = 0;
+    // scratch
+    DBuf st_a, st_b, p_idw, p_seq, p_ia, p_ie, p_dr, p_cost, nl;  // simulation
+    DBuf ia_bits, ia_done;                                         // inspiring ability
+    DBuf ie_rec, ie_acc;                                           // inspiring efficiency
+    int64_t ia_slot_words = 0, ie_rec_stride = 0;
+    int grid_sim = 1, grid_ia = 1, grid_ie = 1;
+    int32_t ia_epoch = 0;
+    uint32_t ie_tag = 1;
+    // staging for host pointers
+    DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;
+    cudaStream_t last_stream = nullptr;
+
+    insp::DevBatch dev() const {
+        insp::DevBatch B;
+        B.ndag = ndag;
+        B.n_types = n_types;
+        B.task_base = task_base.as<int64_t>();
+        B.edge_base = edge_base.as<int64_t>();
+        B.row_ptr = row_ptr.as<int32_t>();
+        B.col_idx = col_idx.as<int32_t>();
+        B.type = type.as<uint8_t>();
+        B.type_cost = type_cost.as<int64_t>();
+        B.task_cost = has_task_cost ? task_cost.as<int64_t>() : nullptr;
+        return B;
+    }
+};
+
+namespace {
+
+int copy_in(DBuf &dst, const void *src, size_t bytes) {
+    int rc = dst.alloc(bytes);
+    if (rc) return rc;
+    if (bytes) CU(cudaMemcpy(dst.p, src, bytes, cudaMemcpyDefault));
+    return INSP_OK;
+}
+
+int alloc_scratch(insp_batch *b) {
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    const int64_t N = std::max<int64_t>(b->n_total, 1);
+    // simulation: per task release state, pool spill, released-task spill
+    if ((rc = b->st_a.alloc(N * sizeof(int2))) || (rc = b->st_b.alloc(N * sizeof(longlong2))) ||
+        (rc = b->p_idw.alloc(N * 4)) || (rc = b->p_seq.alloc(N * 4)) || (rc = b->p_ia.alloc(N * 4)) ||
+        (rc = b->p_ie.alloc(N * 4)) || (rc = b->p_dr.alloc(N * 8)) || (rc = b->p_cost.alloc(N * 8)) ||
+        (rc = b->nl.alloc(N * 4)))
+        return rc;
+    b->grid_sim = std::max(1, std::min(di.sms * di.occ_sim, (b->ndag + insp::sim_warps() - 1) / insp::sim_warps()));
+    // inspiring ability: one bitset slot per CTA (rows of max_n tasks x ceil(max_n/32) words)
+    int64_t slot = 0;
+    for (int d = 0; d < b->ndag; ++d) {
+        int64_t n = b->h_task_base[d + 1] - b->h_task_base[d];
+        slot = std::max(slot, n * ((n + 31) / 32));
+    }
+    b->ia_slot_words = std::max<int64_t>(slot, 1);
+    const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
+    int64_t gia = std::min<int64_t>(int64_t(di.sms) * di.occ_ia, std::max(b->ndag, 1));
+    gia = std::max<int64_t>(1, std::min<int64_t>(gia, budget / (b->ia_slot_words * 4)));
+    b->grid_ia = int(gia);
+    if ((rc = b->ia_bits.alloc(size_t(gia) * b->ia_slot_words * 4)) || (rc = b->ia_done.alloc(N * 4))) return rc;
+    CU(cudaMemset(b->ia_done.p, 0, N * 4));
+    b->ia_epoch = 0;
+    // inspiring efficiency: per warp a record per task of the largest DAG and a W x 32 ring
+    b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
+    const int ie_warps_per_cta = insp::ie_threads() / 32;
+    int64_t gie = std::min<int64_t>(int64_t(di.sms) * di.occ_ie,
+                                    (std::max<int64_t>(b->n_items, 1) + ie_warps_per_cta - 1) / ie_warps_per_cta);
+    const int64_t per_warp = b->ie_rec_stride * 16 + int64_t(b->W) * 32 * 8;
+    gie = std::max<int64_t>(1, std::min<int64_t>(gie, budget / (per_warp * ie_warps_per_cta)));
+    b->grid_ie = int(gie);
+    const int64_t warps = gie * ie_warps_per_cta;
+    if ((rc = b->ie_rec.alloc(size_t(warps) * b->ie_rec_stride * 16)) ||
+        (rc = b->ie_acc.alloc(size_t(warps) * b->W * 32 * 8)))
+        return rc;
+    CU(cudaMemset(b->ie_rec.p, 0, size_t(warps) * b->ie_rec_stride * 16));
+    b->ie_tag = 1;
+    return INSP_OK;
+}
+
+// Stage a caller array into a device buffer when it lives on the host.
+template <typename T>
+int stage_in(DBuf &buf, const T *src, int64_t count, cudaStream_t s, const T *&dev) {
+    if (is_device_ptr(src)) { dev = src; return INSP_OK; }
+    int rc = buf.alloc(std::max<int64_t>(count, 1) * sizeof(T));
+    if (rc) return rc;
+    if (count) CU(cudaMemcpyAsync(buf.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+    dev = buf.as<T>();
+    return INSP_OK;
+}
+
+template <typename T>
+int stage_out(DBuf &buf, T *dst, int64_t count, T *&dev, bool &staged) {
+    if (is_device_ptr(dst)) { dev = dst; staged = false; return INSP_OK; }
+    int rc = buf.alloc(std::max<int64_t>(count, 1) * sizeof(T));
+    if (rc) return rc;
+    dev = buf.as<T>();
+    staged = true;
+    return INSP_OK;
+}
+
+int first_status(insp_batch *b, std::vector<int32_t> &st) {
+    st.assign(std::max(b->ndag, 0), 0);
+    if (b->ndag) CU(cudaMemcpy(st.data(), b->status.p, size_t(b->ndag) * 4, cudaMemcpyDeviceToHost));
+    for (int d = 0; d < b->ndag; ++d)
+        if (st[d] != INSP_OK) {
+            const char *what = st[d] == INSP_ETIMEOUT ? "a bounded device wait gave up" : "device-side error";
+            return fail(st[d], "DAG " + std::to_string(d) + ": " + what);
+        }
+    return INSP_OK;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+INSP_API const char *insp_last_error(void) { return g_err.c_str(); }
+
+INSP_API int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy,
+                                 insp_machine **out) {
+    if (!out) return fail(INSP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_cpu < 0 || n_gpu < 0 || n_cpu + n_gpu < 1 || n_cpu + n_gpu > insp::MAX_WORKERS)
+        return fail(INSP_EINVAL, "need 1 <= n_cpu + n_gpu <= 64 workers");
+    if (xfer_ns < 0 || xfer_ns > insp::TIME_BOUND) return fail(INSP_EINVAL, "xfer_ns out of range");
+    insp_policy p{};
+    if (policy) p = *policy;
+    if (p.policy < INSP_POLICY_INSPIRIT || p.policy > INSP_POLICY_LEARNED) return fail(INSP_EINVAL, "unknown policy");
+    if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
+        p.k_inc_ns < 0)
+        return fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");
+    if (p.policy == INSP_POLICY_LEARNED)
+        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer; install one with insp_set_scorer");
+    auto *m = new (std::nothrow) insp_machine;
+    if (!m) return fail(INSP_ENOMEM, "host allocation");
+    m->n_cpu = n_cpu;
+    m->n_gpu = n_gpu;
+    m->xfer = xfer_ns;
+    m->pol = p;
+    *out = m;
+    return INSP_OK;
+}
+
+INSP_API void insp_machine_destroy(insp_machine *m) { delete m; }
+
+INSP_API int insp_set_scorer(insp_machine *m, const uint16_t *w, size_t nbytes) {
+    (void)m; (void)w; (void)nbytes;
+    return fail(INSP_EINVAL, "learned scorer not available in this build");
+}
+
+INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *task_base, const int64_t *edge_base,
+                                 const int32_t *row_ptr, const int32_t *col_idx, const uint8_t *type,
+                                 int32_t n_types, const int64_t *type_cost, const int64_t *task_cost,
+                                 insp_batch **out) {
+    if (!out) return fail(INSP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!m) return fail(INSP_EINVAL, "machine is NULL");
+    if (ndag < 0 || !task_base || !edge_base) return fail(INSP_EINVAL, "bad ndag or base arrays");
+    if (n_types < 1 || n_types > 64) return fail(INSP_EINVAL, "n_types must be in 1..64");
+    if (!type_cost && !task_cost) return fail(INSP_EINVAL, "need type_cost or task_cost");
+    auto *b = new (std::nothrow) insp_batch;
+    if (!b) return fail(INSP_ENOMEM, "host allocation");
+    auto bail = [&](int rc) { delete b; return rc; };
+    b->mach = *m;
+    b->ndag = ndag;
+    b->n_types = n_types;
+    b->h_task_base.resize(ndag + 1);
+    b->h_edge_base.resize(ndag + 1);
+    if (cudaMemcpy(b->h_task_base.data(), task_base, (ndag + 1) * 8, cudaMemcpyDefault) != cudaSuccess ||
+        cudaMemcpy(b->h_edge_base.data(), edge_base, (ndag + 1) * 8, cudaMemcpyDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(INSP_ECUDA, "reading task_base / edge_base"));
+    }
+    if (b->h_task_base[0] != 0 || b->h_edge_base[0] != 0) return bail(fail(INSP_EINVAL, "bases must start at 0"));
+    for (int d = 0; d < ndag; ++d) {
+        int64_t n = b->h_task_base[d + 1] - b->h_task_base[d], e = b->h_edge_base[d + 1] - b->h_edge_base[d];
+        if (n < 0 || e < 0) return bail(fail(INSP_EINVAL, "bases must be non-decreasing"));
+        if (n > insp::MAX_DAG_TASKS) return bail(fail(INSP_EINVAL, "a DAG has more than 2^24-1 tasks"));
+        if (e > 0x7fffffffLL) return bail(fail(INSP_EINVAL, "a DAG has more than 2^31-1 edges"));
+        b->max_n = std::max<int32_t>(b->max_n, int32_t(n));
+    }
+    b->n_total = b->h_task_base[ndag];
+    b->m_total = b->h_edge_base[ndag];
+    if (b->n_total > 0 && (!row_ptr || !type)) return bail(fail(INSP_EINVAL, "row_ptr and type are required"));
+    if (b->m_total > 0 && !col_idx) return bail(fail(INSP_EINVAL, "col_idx is required"));
+    int rc;
+    if ((rc = copy_in(b->task_base, b->h_task_base.data(), (ndag + 1) * 8)) ||
+        (rc = copy_in(b->edge_base, b->h_edge_base.data(), (ndag + 1) * 8)) ||
+        (rc = copy_in(b->row_ptr, row_ptr, (b->n_total + ndag) * 4)) ||
+        (rc = copy_in(b->col_idx, col_idx, b->m_total * 4)) || (rc = copy_in(b->type, type, b->n_total)))
+        return bail(rc);
+    if (type_cost) {
+        if ((rc = copy_in(b->type_cost, type_cost, size_t(ndag) * n_types * 16))) return bail(rc);
+    } else if ((rc = b->type_cost.alloc(16))) {
+        return bail(rc);
+    }
+    if (task_cost) {
+        if ((rc = copy_in(b->task_cost, task_cost, b->n_total * 16))) return bail(rc);
+        b->has_task_cost = true;
+    } else if (!type_cost) {
+        return bail(fail(INSP_EINVAL, "need type_cost or task_cost"));
+    }
+    if ((rc = b->indeg0.alloc(std::max<int64_t>(b->n_total, 1) * 4)) ||
+        (rc = b->unit_time_def.alloc(std::max(ndag, 1) * 8)) || (rc = b->unit_time_user.alloc(std::max(ndag, 1) * 8)) ||
+        (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(64)))
+        return bail(rc);
+    if (cudaMemset(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4) != cudaSuccess ||
+        cudaMemset(b->max_span.p, 0, 4) != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "memset"));
+    DeviceInfo di;
+    if ((rc = device_info(di))) return bail(rc);
+    insp::DevBatch B = b->dev();
+    const int grid = std::max(1, std::min(ndag, di.sms * 8));
+    if (ndag > 0) {
+        insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
+                              b->max_span.as<int32_t>(), grid, 0);
+        insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, 0);
+    }
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "validation kernels failed"));
+    std::vector<int32_t> st;
+    if ((rc = first_status(b, st))) {
+        g_err = "DAG validation failed: " + g_err;
+        return bail(rc);
+    }
+    if (cudaMemcpy(&b->max_span_h, b->max_span.p, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "reading max span"));
+    std::vector<int64_t> ut(std::max(ndag, 1), 1);
+    if (ndag && cudaMemcpy(ut.data(), b->unit_time_def.p, ndag * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "reading unit times"));
+    b->max_unit_def = *std::max_element(ut.begin(), ut.end());
+    // window of the efficiency sweep: a power of two above every edge span
+    b->W = 1;
+    while (b->W <= b->max_span_h) b->W <<= 1;
+    // DAG order for the persistent kernels: descending size (longest first)
+    std::vector<int32_t> order(ndag);
+    for (int d = 0; d < ndag; ++d) order[d] = d;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (b->h_task_base[a + 1] - b->h_task_base[a]) > (b->h_task_base[c + 1] - b->h_task_base[c]);
+    });
+    std::vector<int64_t> items(ndag + 1, 0);
+    for (int d = 0; d < ndag; ++d) items[d + 1] = items[d] + (b->h_task_base[d + 1] - b->h_task_base[d] + 31) / 32;
+    b->n_items = items[ndag];
+    if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4)) ||
+        (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)))
+        return bail(rc);
+    if ((rc = alloc_scratch(b))) return bail(rc);
+    *out = b;
+    return INSP_OK;
+}
+
+INSP_API int insp_dag_load_csr(insp_machine *m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
+                               const uint8_t *type, int32_t n_types, const int64_t *type_cost,
+                               const int64_t *task_cost, insp_dag **out) {
+    if (!out) return fail(INSP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || n > insp::MAX_DAG_TASKS) return fail(INSP_EINVAL, "n out of range");
+    if (!row_ptr) return fail(INSP_EINVAL, "row_ptr is NULL");
+    int32_t m_edges = 0;
+    if (cudaMemcpy(&m_edges, row_ptr + n, 4, cudaMemcpyDefault) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(INSP_ECUDA, "reading row_ptr[n]");
+    }
+    if (m_edges < 0) return fail(INSP_EINVAL, "row_ptr[n] < 0");
+    int64_t tb[2] = {0, n}, eb[2] = {0, m_edges};
+    std::vector<uint8_t> zeros;
+    if (!type) {
+        zeros.assign(std::max(n, 1), 0);
+        type = zeros.data();
+    }
+    return insp_batch_load_csr(m, 1, tb, eb, row_ptr, col_idx, type, n_types, type_cost, task_cost, out);
+}
+
+INSP_API void insp_batch_destroy(insp_batch *b) {
+    if (b && b->last_stream) cudaStreamSynchronize(b->last_stream);
+    delete b;
+}
+INSP_API void insp_dag_destroy(insp_dag *d) { insp_batch_destroy(d); }
+
+INSP_API int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    if (ndag) *ndag = b->ndag;
+    if (n_tasks) *n_tasks = b->n_total;
+    if (n_edges) *n_edges = b->m_total;
+    return INSP_OK;
+}
+
+INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
+                                   void *stream) {
+    if (!b || !ia || !ie) return fail(INSP_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    int rc;
+    const int64_t N = b->n_total;
+    int32_t *d_ia, *d_ie;
+    bool st_ia, st_ie;
+    if ((rc = stage_out(b->s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(b->s_ie, ie, N, d_ie, st_ie))) return rc;
+    const int64_t *ut = b->unit_time_def.as<int64_t>();
+    bool wide = b->max_unit_def >= 0x7fffffffLL;
+    if (unit_time_ns) {
+        if (is_device_ptr(unit_time_ns)) {
+            CU(cudaMemcpyAsync(b->unit_time_user.p, unit_time_ns, size_t(b->ndag) * 8, cudaMemcpyDeviceToDevice, s));
+            wide = true;
+        } else {
+            std::vector<int64_t> h(unit_time_ns, unit_time_ns + b->ndag);
+            std::vector<int64_t> def(std::max(b->ndag, 1));
+            bool need_def = false;
+            for (auto v : h) need_def |= v <= 0;
+            if (need_def && b->ndag)
+                CU(cudaMemcpy(def.data(), b->unit_time_def.p, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost));
+            int64_t mx = 1;
+            for (int d = 0; d < b->ndag; ++d) {
+                if (h[d] <= 0) h[d] = def[d];
+                mx = std::max(mx, h[d]);
+            }
+            wide = mx >= 0x7fffffffLL;
+            if (b->ndag)
+                CU(cudaMemcpyAsync(b->unit_time_user.p, h.data(), size_t(b->ndag) * 8, cudaMemcpyHostToDevice, s));
+            if (b->ndag) CU(cudaStreamSynchronize(s));  // h is a local vector
+        }
+        ut = b->unit_time_user.as<int64_t>();
+    }
+    if (b->ndag == 0) return INSP_OK;
+    CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
+    CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
+    b->ia_epoch += 1;
+    if (b->ia_epoch == 0x7fffffff) {
+        CU(cudaMemsetAsync(b->ia_done.p, 0, std::max<int64_t>(N, 1) * 4, s));
+        b->ia_epoch = 1;
+    }
+    if (uint64_t(b->ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
+        const int64_t warps = int64_t(b->grid_ie) * (insp::ie_threads() / 32);
+        CU(cudaMemsetAsync(b->ie_rec.p, 0, size_t(warps) * b->ie_rec_stride * 16, s));
+        b->ie_tag = 1;
+    }
+    insp::DevBatch B = b->dev();
+    int32_t *ctr = b->counters.as<int32_t>();
+    insp::launch_ia(B, b->order.as<int32_t>(), ctr + 0, b->ia_bits.as<uint32_t>(), b->ia_slot_words,
+                    b->ia_done.as<int32_t>(), b->ia_epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
+    insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, b->ie_rec.as<uint4>(), b->ie_rec_stride,
+                    b->ie_acc.p, b->W, wide, b->ie_tag, d_ie, b->grid_ie, s);
+    b->ie_tag += uint32_t(b->n_items);
+    CU(cudaGetLastError());
+    if (st_ia || st_ie) {
+        if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
+        if (st_ie) CU(cudaMemcpyAsync(ie, d_ie, N * 4, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<int32_t> st;
+        return first_status(b, st);
+    }
+    return INSP_OK;
+}
+
+INSP_API int insp_attributes(insp_dag *d, int64_t unit_time_ns, int32_t *ia, int32_t *ie, void *stream) {
+    if (!d) return fail(INSP_EINVAL, "dag is NULL");
+    if (unit_time_ns <= 0) return insp_attributes_batch(d, nullptr, ia, ie, stream);
+    std::vector<int64_t> t(std::max(d->ndag, 1), unit_time_ns);
+    return insp_attributes_batch(d, t.data(), ia, ie, stream);
+}
+
+namespace {
+
+int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                  int64_t *end, int64_t *makespan, void *stream, bool per_dag) {
+    if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    const int64_t N = b->n_total;
+    int rc;
+    const int32_t *d_ia, *d_ie;
+    if ((rc = stage_in(b->s_ia, ia, N, s, d_ia)) || (rc = stage_in(b->s_ie, ie, N, s, d_ie))) return rc;
+    int32_t *d_worker;
+    int64_t *d_start, *d_end, *d_mk;
+    bool sw, ss, se, sm;
+    if ((rc = stage_out(b->s_worker, worker, N, d_worker, sw)) || (rc = stage_out(b->s_start, start, N, d_start, ss)) ||
+        (rc = stage_out(b->s_end, end, N, d_end, se)) || (rc = stage_out(b->s_makespan, makespan, b->ndag, d_mk, sm)))
+        return rc;
+    if (b->ndag > 0) {
+        CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
+        CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
+        insp::SimArgs A{};
+        A.B = b->dev();
+        A.n_cpu = b->mach.n_cpu;
+        A.n_gpu = b->mach.n_gpu;
+        A.xfer = b->mach.xfer;
+        A.policy = b->mach.pol.policy;
+        A.task_window = b->mach.pol.task_window;
+        A.s_inc = b->mach.pol.s_inc;
+        A.s_dec = b->mach.pol.s_dec;
+        A.dec_step = b->mach.pol.dec_step;
+        A.c = b->mach.pol.c;
+        A.k_inc_tasks = b->mach.pol.k_inc_tasks;
+        A.k_inc_ns = b->mach.pol.k_inc_ns;
+        A.unit_time_def = b->unit_time_def.as<int64_t>();
+        A.indeg0 = b->indeg0.as<int32_t>();
+        A.ia = d_ia;
+        A.ie = d_ie;
+        A.worker = d_worker;
+        A.start = d_start;
+        A.end = d_end;
+        A.makespan = d_mk;
+        A.status = b->status.as<int32_t>();
+        A.st_a = b->st_a.as<int2>();
+        A.st_b = b->st_b.as<longlong2>();
+        A.p_idw = b->p_idw.as<int32_t>();
+        A.p_seq = b->p_seq.as<int32_t>();
+        A.p_ia = b->p_ia.as<int32_t>();
+        A.p_ie = b->p_ie.as<int32_t>();
+        A.p_dr = b->p_dr.as<int64_t>();
+        A.p_cost = b->p_cost.as<int64_t>();
+        A.nl = b->nl.as<int32_t>();
+        A.order = b->order.as<int32_t>();
+        A.counter = b->counters.as<int32_t>() + 8;
+        if (per_dag) {
+            for (int d = 0; d < b->ndag; ++d) {
+                A.single_dag = d;
+                insp::launch_sim_single(A, s);
+            }
+        } else {
+            A.single_dag = -1;
+            insp::launch_sim(A, b->grid_sim, s);
+        }
+        CU(cudaGetLastError());
+    }
+    if (sw || ss || se || sm) {
+        if (sw) CU(cudaMemcpyAsync(worker, d_worker, N * 4, cudaMemcpyDeviceToHost, s));
+        if (ss) CU(cudaMemcpyAsync(start, d_start, N * 8, cudaMemcpyDeviceToHost, s));
+        if (se) CU(cudaMemcpyAsync(end, d_end, N * 8, cudaMemcpyDeviceToHost, s));
+        if (sm) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<int32_t> st;
+        return first_status(b, st);
+    }
+    return INSP_OK;
+}
+
+}  // namespace
+
+INSP_API int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
+                                 int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
+    return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                           int64_t *end, int64_t *makespan, void *stream) {
+    return simulate_impl(d, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
+                                   int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
+    return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, true);
+}
+
+INSP_API int insp_batch_status(insp_batch *b, int32_t *status) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    CU(cudaStreamSynchronize(b->last_stream));
+    std::vector<int32_t> st;
+    int rc = first_status(b, st);
+    if (status) std::copy(st.begin(), st.end(), status);
+    return rc;
+}

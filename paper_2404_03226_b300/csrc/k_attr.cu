@@ -1,0 +1,230 @@
+// Task attributes of Sec. 4.2 / Sec. 4.3.
+//
+// Inspiring ability, IA(v) = |strict descendants of v|.  Reverse sweep over a
+// DAG in descending id (ids are topological): desc(v) = union over successors
+// s of ({s} + desc(s)), kept as one bitset row per task in global scratch.  A
+// CTA owns one DAG at a time; its warps claim tasks in descending id and each
+// waits (bounded) until the rows of its successors are published.
+//
+// Inspiring efficiency, IE_T(v) = |{u != v : every path v ~> u, weighted by GPU
+// costs with both ends included, weighs <= T}|.  A warp owns 32 consecutive
+// sources (lane j <-> v0 + j) and sweeps ids upward from v0 -- the "sliding
+// window" of Sec. 4.3 -- keeping per task a reach mask (sources whose cone
+// holds it), an over mask (sources for which some path to it already exceeds
+// T) and, in a ring buffer of W >= max edge span + 1 slots, the running max of
+// its in-cone predecessors' path weights per source.  The sweep stops after
+// the last task that received an in-window contribution.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace insp {
+
+// --------------------------------------------------------- inspiring ability
+constexpr int IA_WARPS = 8;
+constexpr int IA_R = 4;  // words per lane per chunk (4 x 32 x 32 = 4096 ids)
+
+__global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t *counter,
+                                                      uint32_t *bits, int64_t slot_words, int32_t *done,
+                                                      int32_t epoch, int32_t *ia_out, int32_t *status) {
+    __shared__ int32_t s_dag;
+    __shared__ int32_t s_next;
+    __shared__ int32_t s_abort;  // a wait gave up: later waits of this DAG return at once
+    const int lane = threadIdx.x & 31;
+    uint32_t *slot = bits + int64_t(blockIdx.x) * slot_words;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int k = atomicAdd(counter, 1);
+            int d = k < B.ndag ? order[k] : -1;
+            s_dag = d;
+            s_next = d >= 0 ? int32_t(B.task_base[d + 1] - B.task_base[d]) - 1 : -1;
+            s_abort = 0;
+        }
+        __syncthreads();
+        const int d = s_dag;
+        if (d < 0) return;
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        const int32_t NW = (n + 31) >> 5;
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        bool timed_out = false;
+        for (;;) {
+            int32_t v = 0;
+            if (lane == 0) v = atomicSub(&s_next, 1);
+            v = __shfl_sync(FULL, v, 0);
+            if (v < 0) break;
+            const int32_t lo = rp[v], deg = rp[v + 1] - lo;
+            // wait until every successor's row is published (bounded)
+            for (int32_t i = lane; i < deg; i += 32) {
+                const int32_t s = col[lo + i];
+                int it = 0;
+                while (ld_volatile(done + tb + s) != epoch) {
+                    if (++it > SPIN_LIMIT || ld_volatile(&s_abort)) {
+                        timed_out = true;
+                        st_volatile(&s_abort, 1);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __syncwarp();
+            __threadfence_block();
+            const int32_t wlo = (v + 1) >> 5;
+            uint32_t *row_v = slot + int64_t(v) * NW;
+            int32_t count = 0;
+            for (int32_t cw = wlo; cw < NW; cw += 32 * IA_R) {
+                uint32_t acc[IA_R];
+#pragma unroll
+                for (int r = 0; r < IA_R; ++r) acc[r] = 0;
+                for (int32_t i = 0; i < deg; ++i) {
+                    const int32_t s = col[lo + i];
+                    const int32_t ws = (s + 1) >> 5;
+                    const uint32_t *row_s = slot + int64_t(s) * NW;
+#pragma unroll
+                    for (int r = 0; r < IA_R; ++r) {
+                        const int32_t w = cw + lane + 32 * r;
+                        if (w >= ws && w < NW) acc[r] |= row_s[w];
+                        if (w == (s >> 5)) acc[r] |= 1u << (s & 31);
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < IA_R; ++r) {
+                    const int32_t w = cw + lane + 32 * r;
+                    if (w < NW) {
+                        row_v[w] = acc[r];
+                        count += __popc(acc[r]);
+                    }
+                }
+            }
+            count = __reduce_add_sync(FULL, count);
+            __threadfence_block();
+            __syncwarp();
+            if (lane == 0) {
+                ia_out[tb + v] = count;
+                st_volatile(done + tb + v, epoch);
+            }
+        }
+        timed_out = __syncthreads_or(timed_out);
+        if (timed_out && threadIdx.x == 0) status[d] = INSP_ETIMEOUT;
+    }
+}
+
+// ------------------------------------------------------ inspiring efficiency
+// Per-task record of the sweep: {tag, reach mask, over mask, unused}.  A record
+// whose tag differs from the current work item's is empty (no reset needed).
+template <typename V>
+__global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base, int64_t n_items, int32_t *counter,
+                                            const int64_t *unit_time, uint4 *rec, int64_t rec_stride, V *acc,
+                                            int32_t W, uint32_t tag_base, int32_t *ie_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_id = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    uint4 *my_rec = rec + warp_id * rec_stride;
+    V *my_acc = acc + warp_id * int64_t(W) * 32;
+    const int32_t wmask = W - 1;
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= n_items) return;
+        const int d = upper_index(item_base, B.ndag + 1, item);
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        const int32_t v0 = int32_t(item - item_base[d]) * 32;
+        const int32_t n_src = min(32, n - v0);
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        const int64_t T = unit_time[d];
+        const uint32_t tag = tag_base + uint32_t(item);
+        int32_t cnt = 0;
+        int32_t hi = v0 + n_src - 1;
+        for (int32_t x = v0; x <= hi; ++x) {
+            const uint4 r = my_rec[x];
+            const uint32_t reach = (r.x == tag) ? r.y : 0u;
+            const uint32_t over = (r.x == tag) ? r.z : 0u;
+            const uint32_t src = (x - v0 < n_src) ? (1u << (x - v0)) : 0u;
+            const uint32_t pmask = reach | src;
+            if (pmask == 0) continue;
+            const int64_t c = task_cost(B, d, tb + x, 1);
+            bool under = false;
+            int64_t L = 0;
+            if ((src >> lane) & 1u) {
+                L = c;
+                under = (L <= T);
+            } else if (((reach >> lane) & 1u) && !((over >> lane) & 1u)) {
+                L = int64_t(my_acc[(x & wmask) * 32 + lane]) + c;
+                under = (L <= T);
+                cnt += under;
+            }
+            const uint32_t umask = __ballot_sync(FULL, under);
+            const uint32_t omask = pmask & ~umask;
+            const int32_t elo = rp[x], ehi = rp[x + 1];
+            for (int32_t base = elo; base < ehi; base += 32) {
+                const int32_t i = base + lane;
+                int32_t s = 0;
+                uint32_t old_reach = 0, old_over = 0;
+                if (i < ehi) {
+                    s = col[i];
+                    uint4 q = my_rec[s];
+                    if (q.x != tag) q = make_uint4(tag, 0u, 0u, 0u);
+                    old_reach = q.y;
+                    old_over = q.z;
+                    q.y |= pmask;
+                    q.z |= omask;
+                    my_rec[s] = q;
+                }
+                if (umask) {
+                    const int k = min(32, ehi - base);
+                    for (int j = 0; j < k; ++j) {
+                        const int32_t sj = __shfl_sync(FULL, s, j);
+                        const uint32_t orj = __shfl_sync(FULL, old_reach, j);
+                        const uint32_t ooj = __shfl_sync(FULL, old_over, j);
+                        if (under && !((ooj >> lane) & 1u)) {
+                            V *a = my_acc + (sj & wmask) * 32 + lane;
+                            if ((orj >> lane) & 1u) {
+                                if (V(L) > *a) *a = V(L);
+                            } else {
+                                *a = V(L);
+                            }
+                        }
+                        hi = max(hi, sj);
+                    }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane < n_src) ie_out[tb + v0 + lane] = cnt;
+        __syncwarp();
+    }
+}
+
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
+               int32_t *done, int32_t epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s) {
+    k_ia<<<grid, IA_WARPS * 32, 0, s>>>(B, order, counter, bits, slot_words, done, epoch, ia, status);
+}
+
+void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
+               const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
+               uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s) {
+    if (wide)
+        k_ie<int64_t><<<grid, 256, 0, s>>>(B, item_base, n_items, counter, unit_time, rec, rec_stride,
+                                           (int64_t *)acc, W, tag_base, ie);
+    else
+        k_ie<int32_t><<<grid, 256, 0, s>>>(B, item_base, n_items, counter, unit_time, rec, rec_stride,
+                                           (int32_t *)acc, W, tag_base, ie);
+}
+
+int ia_threads() { return IA_WARPS * 32; }
+int ie_threads() { return 256; }
+int ia_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ia, IA_WARPS * 32, 0) != cudaSuccess) return 0;
+    return nb;
+}
+int ie_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie<int64_t>, 256, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+}  // namespace insp

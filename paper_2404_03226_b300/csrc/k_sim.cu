@@ -1,0 +1,395 @@
+// The list-scheduling run of INSPIRIT (Sec. 2.1 push/pop, Sec. 4.1, Sec. 4.4),
+// one warp per DAG.
+//
+// Lane l owns workers l and l + 32: their busy-until time, queued work,
+// running task and queue count live in registers.  The ready tasks of all
+// workers form one pool (Nready = pool size): the first POOL_C entries in
+// shared memory, the rest spilled to the DAG's slice of a global pool.  Per
+// task the warp keeps in global scratch the remaining in-degree and the two
+// latest completion times of its predecessors on distinct memory nodes, which
+// give the data-arrival time on any worker in O(1).
+//
+// Event loop (all lanes in lockstep, every decision warp-uniform):
+//   completions at `now` release successors (lanes over the CSR row);
+//   released tasks are pushed in ascending id (a P-way merge of the per
+//   completion runs), each to the worker of minimum expected finish
+//   (argmin of (finish << 6 | worker) by redux);
+//   idle workers pop in ascending id: the Nready controller picks the mode
+//   and an argmax over the pool of a 64-bit key (mode key, then lowest id)
+//   selects the task.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace insp {
+
+constexpr int SIM_WARPS = 8;
+constexpr int POOL_C = 64;   // pool entries per warp in shared memory
+constexpr int NL_C = 128;    // released-task buffer per warp in shared memory
+constexpr int NODE_NONE = 0xff;
+
+enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4 };
+enum { ST_INC = 0, ST_DEC = 1 };
+
+struct WarpSmem {
+    int32_t idw[POOL_C];  // task id | worker << 24
+    int32_t seq[POOL_C];
+    int32_t ia[POOL_C];
+    int32_t ie[POOL_C];
+    int64_t dr[POOL_C];   // data arrival time on the queued worker
+    int64_t cost[POOL_C]; // cost on the queued worker
+    int32_t newly[NL_C];
+    int32_t run_end[MAX_WORKERS];
+    int64_t tcost[MAX_TYPES_SMEM * 2];
+};
+
+struct Pool {
+    WarpSmem *sm;
+    int32_t *g_idw, *g_seq, *g_ia, *g_ie;
+    int64_t *g_dr, *g_cost;
+    __device__ __forceinline__ int32_t idw(int i) const { return i < POOL_C ? sm->idw[i] : g_idw[i - POOL_C]; }
+    __device__ __forceinline__ int32_t seq(int i) const { return i < POOL_C ? sm->seq[i] : g_seq[i - POOL_C]; }
+    __device__ __forceinline__ int32_t ia(int i) const { return i < POOL_C ? sm->ia[i] : g_ia[i - POOL_C]; }
+    __device__ __forceinline__ int32_t ie(int i) const { return i < POOL_C ? sm->ie[i] : g_ie[i - POOL_C]; }
+    __device__ __forceinline__ int64_t dr(int i) const { return i < POOL_C ? sm->dr[i] : g_dr[i - POOL_C]; }
+    __device__ __forceinline__ int64_t cost(int i) const { return i < POOL_C ? sm->cost[i] : g_cost[i - POOL_C]; }
+    __device__ __forceinline__ void set(int i, int32_t idw_, int32_t seq_, int32_t ia_, int32_t ie_, int64_t dr_,
+                                        int64_t cost_) const {
+        if (i < POOL_C) {
+            sm->idw[i] = idw_; sm->seq[i] = seq_; sm->ia[i] = ia_; sm->ie[i] = ie_; sm->dr[i] = dr_; sm->cost[i] = cost_;
+        } else {
+            int j = i - POOL_C;
+            g_idw[j] = idw_; g_seq[j] = seq_; g_ia[j] = ia_; g_ie[j] = ie_; g_dr[j] = dr_; g_cost[j] = cost_;
+        }
+    }
+    // copy entry `from` into slot `to`, lanes 0..5 one field each
+    __device__ __forceinline__ void move(int from, int to, int lane) const {
+        if (lane == 0) { int32_t v = idw(from); if (to < POOL_C) sm->idw[to] = v; else g_idw[to - POOL_C] = v; }
+        if (lane == 1) { int32_t v = seq(from); if (to < POOL_C) sm->seq[to] = v; else g_seq[to - POOL_C] = v; }
+        if (lane == 2) { int32_t v = ia(from); if (to < POOL_C) sm->ia[to] = v; else g_ia[to - POOL_C] = v; }
+        if (lane == 3) { int32_t v = ie(from); if (to < POOL_C) sm->ie[to] = v; else g_ie[to - POOL_C] = v; }
+        if (lane == 4) { int64_t v = dr(from); if (to < POOL_C) sm->dr[to] = v; else g_dr[to - POOL_C] = v; }
+        if (lane == 5) { int64_t v = cost(from); if (to < POOL_C) sm->cost[to] = v; else g_cost[to - POOL_C] = v; }
+    }
+};
+
+// Nready controller (Sec. 4.4 pseudocode), warp-uniform state.
+struct Ctrl {
+    int64_t peak, prev_n, prev_t, count;
+    int32_t mode, state;
+};
+
+__device__ __forceinline__ void ctrl_step(Ctrl &S, int64_t cur, int64_t now, int32_t tw, int32_t s_inc,
+                                          int32_t s_dec, int32_t dec_step, int32_t c, int64_t kt, int64_t kns) {
+    if (cur > S.peak) { S.peak = cur; S.count = 0; }
+    int64_t moved = cur - S.prev_n;
+    if (moved < 0) moved = -moved;
+    if (moved < tw) return;
+    S.state = (cur >= S.peak - dec_step) ? ST_INC : ST_DEC;
+    if (S.state == ST_INC) {
+        const int64_t growth = cur - S.prev_n, elapsed = now - S.prev_t;
+        if (growth >= s_inc) {
+            if (elapsed == 0) {
+                S.mode = MODE_ABILITY;
+            } else {
+                const __int128 lhs = (__int128)growth * kns, rhs = (__int128)kt * elapsed;
+                S.mode = lhs < rhs ? MODE_EFI : (lhs > rhs ? MODE_ABILITY : MODE_FIFO);
+            }
+        } else {
+            S.mode = MODE_FIFO;
+        }
+    } else {
+        const int64_t stage = S.peak - int64_t(s_dec) * S.count;
+        const int64_t next = S.peak - int64_t(s_dec) * (S.count + 1);
+        if (cur > stage) {
+            S.mode = MODE_ABILITY;
+        } else if (cur <= next + c) {
+            S.mode = MODE_EFI_LOC;
+            if (cur <= next) S.count += 1;
+        } else {
+            S.mode = MODE_FIFO;
+        }
+    }
+    S.prev_n = cur;
+    S.prev_t = now;
+}
+
+__device__ __forceinline__ int32_t node_of(int32_t w, int32_t n_cpu) { return w < n_cpu ? 0 : 1 + (w - n_cpu); }
+
+__global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
+    __shared__ WarpSmem smem_all[SIM_WARPS];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    WarpSmem *sm = &smem_all[wib];
+    const DevBatch &B = A.B;
+    const int32_t P = A.n_cpu + A.n_gpu, n_cpu = A.n_cpu;
+    const int64_t xfer = A.xfer;
+    const bool smem_types = (A.B.task_cost == nullptr) && (B.n_types <= MAX_TYPES_SMEM);
+
+    for (int32_t iter = 0;; ++iter) {
+        int d;
+        if (A.single_dag >= 0) {
+            if (iter > 0 || blockIdx.x != 0 || wib != 0) return;
+            d = A.single_dag;
+        } else {
+            int k = 0;
+            if (lane == 0) k = atomicAdd(A.counter, 1);
+            k = __shfl_sync(FULL, k, 0);
+            if (k >= B.ndag) return;
+            d = A.order[k];
+        }
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        int2 *st_a = A.st_a + tb;
+        longlong2 *st_b = A.st_b + tb;
+        const int32_t *g_ia = A.ia + tb, *g_ie = A.ie + tb;
+        Pool pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
+        int32_t *nl_g = A.nl + tb;
+
+        // resolved policy parameters (zero = default for P workers and the DAG's default T)
+        const int32_t tw = A.task_window > 0 ? A.task_window : P;
+        const int32_t s_inc = A.s_inc > 0 ? A.s_inc : P;
+        const int32_t s_dec = A.s_dec > 0 ? A.s_dec : P;
+        const int32_t dec_step = A.dec_step > 0 ? A.dec_step : P;
+        const int32_t cslack = A.c > 0 ? A.c : (P / 2 > 1 ? P / 2 : 1);
+        const int64_t kt = A.k_inc_tasks > 0 ? A.k_inc_tasks : P;
+        const int64_t kns = A.k_inc_ns > 0 ? A.k_inc_ns : A.unit_time_def[d];
+        const bool fifo_policy = (A.policy == INSP_POLICY_FIFO);
+
+        // per-DAG init: cost table, per-task release state
+        if (smem_types) {
+            for (int i = lane; i < B.n_types * 2; i += 32) sm->tcost[i] = B.type_cost[int64_t(d) * B.n_types * 2 + i];
+        }
+        for (int32_t t = lane; t < n; t += 32) {
+            st_a[t] = make_int2(A.indeg0[tb + t], NODE_NONE);
+            st_b[t] = make_longlong2(NEG_TIME, NEG_TIME);
+        }
+        __syncwarp();
+
+        auto cost_of = [&](int32_t t, int kind) -> int64_t {
+            if (smem_types) return sm->tcost[int(B.type[tb + t]) * 2 + kind];
+            return task_cost(B, d, tb + t, kind);
+        };
+
+        // lane-owned worker state, workers w0 = lane and w1 = lane + 32
+        const int32_t w0 = lane, w1 = lane + 32;
+        int64_t busy0 = 0, busy1 = 0, qc0 = 0, qc1 = 0;
+        int32_t run0 = -1, run1 = -1, qn0 = 0, qn1 = 0;
+        int32_t nready = 0, seq = 0, done = 0;
+        int64_t now = 0;
+        Ctrl ctl{0, 0, 0, 0, MODE_FIFO, ST_INC};
+
+        // push(t): earliest expected finish over all workers (DMDA with transfer)
+        auto push = [&](int32_t t) {
+            const int2 a = st_a[t];
+            const longlong2 b = st_b[t];
+            const int32_t tia = g_ia[t], tie = g_ie[t];
+            const int64_t cc = cost_of(t, 0), cg = cost_of(t, 1);
+            uint64_t k0 = ~0ull, k1 = ~0ull;
+            int64_t dr0 = 0, dr1 = 0;
+            if (w0 < P) {
+                const int32_t nd = node_of(w0, n_cpu);
+                dr0 = a.y == NODE_NONE ? 0 : (nd == a.y ? max(b.x, b.y + xfer) : b.x + xfer);
+                const int64_t avail = max(now, busy0) + qc0;
+                const int64_t ef = max(avail, dr0) + (w0 < n_cpu ? cc : cg);
+                k0 = (uint64_t(ef) << 6) | uint64_t(w0);
+            }
+            if (w1 < P) {
+                const int32_t nd = node_of(w1, n_cpu);
+                dr1 = a.y == NODE_NONE ? 0 : (nd == a.y ? max(b.x, b.y + xfer) : b.x + xfer);
+                const int64_t avail = max(now, busy1) + qc1;
+                const int64_t ef = max(avail, dr1) + (w1 < n_cpu ? cc : cg);
+                k1 = (uint64_t(ef) << 6) | uint64_t(w1);
+            }
+            const uint64_t kmin = warp_min_u64(k0 < k1 ? k0 : k1);
+            const int32_t ws = int32_t(kmin & 63);
+            if (lane == (ws & 31)) {
+                const bool hi = ws >= 32;
+                const int64_t c = ws < n_cpu ? cc : cg;
+                if (hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
+                pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
+            }
+            seq += 1;
+            nready += 1;
+            __syncwarp();
+        };
+
+        // pop(w): controller judgement, then argmax of the mode's key over w's entries.
+        // Returns false (no fault) if w has no entry, which would be a bookkeeping error.
+        auto pop = [&](int32_t w) -> bool {
+            const int64_t cur = nready;
+            int32_t mode = MODE_FIFO;
+            if (!fifo_policy) {
+                ctrl_step(ctl, cur, now, tw, s_inc, s_dec, dec_step, cslack, kt, kns);
+                mode = ctl.mode;
+            }
+            uint64_t best = 0;
+            int32_t bi = -1;
+            for (int32_t i = lane; i < nready; i += 32) {
+                const int32_t e = pool.idw(i);
+                if ((e >> 24) != w) continue;
+                const uint32_t id = uint32_t(e & 0xffffff);
+                uint64_t key;
+                if (mode == MODE_FIFO) {
+                    key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.seq(i)));
+                } else {
+                    const uint64_t tie_lo = uint64_t(0x7fffffffu - id);
+                    uint64_t hi_part;
+                    if (mode == MODE_ABILITY) hi_part = uint64_t(uint32_t(pool.ia(i))) << 31;
+                    else if (mode == MODE_EFI) hi_part = uint64_t(uint32_t(pool.ie(i))) << 31;
+                    else hi_part = (uint64_t(pool.dr(i) <= now) << 62) | (uint64_t(uint32_t(pool.ie(i))) << 31);
+                    key = (1ull << 63) | hi_part | tie_lo;
+                }
+                if (key > best) { best = key; bi = i; }
+            }
+            const uint64_t wbest = warp_max_u64(best);
+            const uint32_t wl = __ballot_sync(FULL, best == wbest && bi >= 0);
+            if (wl == 0) return false;
+            const int32_t src_lane = __ffs(wl) - 1;
+            const int32_t idx = __shfl_sync(FULL, bi, src_lane);
+            const int32_t t = pool.idw(idx) & 0xffffff;
+            const int64_t dr = pool.dr(idx), c = pool.cost(idx);
+            __syncwarp();
+            const int32_t last = nready - 1;
+            if (idx != last) pool.move(last, idx, lane);
+            nready -= 1;
+            const int64_t s = max(now, dr), e = s + c;
+            if (lane == (w & 31)) {
+                if (w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; }
+                else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; }
+            }
+            if (lane == 0) {
+                A.worker[tb + t] = w;
+                A.start[tb + t] = s;
+                A.end[tb + t] = e;
+            }
+            __syncwarp();
+            return true;
+        };
+
+        auto dispatch = [&]() -> bool {
+            const uint32_t m0 = __ballot_sync(FULL, w0 < P && run0 < 0 && qn0 > 0);
+            const uint32_t m1 = __ballot_sync(FULL, w1 < P && run1 < 0 && qn1 > 0);
+            bool ok = true;
+            for (uint32_t m = m0; m && ok; m &= m - 1) ok = pop(__ffs(m) - 1);
+            for (uint32_t m = m1; m && ok; m &= m - 1) ok = pop(32 + __ffs(m) - 1);
+            return ok;
+        };
+
+        // initial pushes: tasks without predecessors, ascending id
+        for (int32_t base = 0; base < n; base += 32) {
+            const int32_t t = base + lane;
+            const uint32_t m = __ballot_sync(FULL, t < n && A.indeg0[tb + t] == 0);
+            for (uint32_t mm = m; mm; mm &= mm - 1) push(base + __ffs(mm) - 1);
+        }
+        bool bad = !dispatch();
+
+        int64_t guard = 0;
+        while (!bad && done < n) {
+            if (++guard > 2 * int64_t(n) + 2) { bad = true; break; }
+            // next event: earliest completion
+            const int64_t e0 = (w0 < P && run0 >= 0) ? busy0 : INT64_MAX;
+            const int64_t e1 = (w1 < P && run1 >= 0) ? busy1 : INT64_MAX;
+            now = warp_min_i64(min(e0, e1));
+            if (now == INT64_MAX) { bad = true; break; }
+            const uint32_t c0 = __ballot_sync(FULL, w0 < P && run0 >= 0 && busy0 == now);
+            const uint32_t c1 = __ballot_sync(FULL, w1 < P && run1 >= 0 && busy1 == now);
+            // release successors of every completed task; one run of released ids per completion
+            int32_t nl = 0, nruns = 0;
+            for (int half = 0; half < 2; ++half) {
+                for (uint32_t m = half ? c1 : c0; m; m &= m - 1) {
+                    const int32_t wl = __ffs(m) - 1;
+                    const int32_t w = wl + 32 * half;
+                    const int32_t p = __shfl_sync(FULL, half ? run1 : run0, wl);
+                    const int32_t nd = node_of(w, n_cpu);
+                    const int32_t lo = rp[p], hi = rp[p + 1];
+                    for (int32_t base = lo; base < hi; base += 32) {
+                        const int32_t i = base + lane;
+                        bool ready = false;
+                        int32_t s = 0;
+                        if (i < hi) {
+                            s = col[i];
+                            int2 a = st_a[s];
+                            longlong2 b = st_b[s];
+                            a.x -= 1;
+                            if (a.y == nd) {
+                                b.x = now;
+                            } else if (now > b.x) {
+                                b.y = b.x;
+                                a.y = nd;
+                                b.x = now;
+                            } else {
+                                b.y = now;
+                            }
+                            st_a[s] = a;
+                            st_b[s] = b;
+                            ready = (a.x == 0);
+                        }
+                        __syncwarp();  // the next row may release the same successor from another lane
+                        const uint32_t rm = __ballot_sync(FULL, ready);
+                        if (ready) {
+                            const int32_t pos = nl + __popc(rm & ((1u << lane) - 1));
+                            if (pos < NL_C) sm->newly[pos] = s; else nl_g[pos - NL_C] = s;
+                        }
+                        nl += __popc(rm);
+                    }
+                    if (lane == 0) sm->run_end[nruns] = nl;
+                    nruns += 1;
+                }
+            }
+            if (c0 & (1u << lane)) run0 = -1;
+            if (c1 & (1u << lane)) run1 = -1;
+            done += __popc(c0) + __popc(c1);
+            __syncwarp();
+            // push released tasks in ascending id: merge of the sorted runs
+            if (nl > 0) {
+                int32_t runs_nonempty = 0;
+                for (int r = 0; r < nruns; ++r) {
+                    const int32_t b0 = r ? sm->run_end[r - 1] : 0;
+                    runs_nonempty += sm->run_end[r] > b0;
+                }
+                if (runs_nonempty <= 1) {
+                    for (int32_t k = 0; k < nl; ++k) push(k < NL_C ? sm->newly[k] : nl_g[k - NL_C]);
+                } else {
+                    // lane r owns run r (and r + 32): cursor and end
+                    int32_t cur0 = 0, end0 = 0, cur1 = 0, end1 = 0;
+                    if (lane < nruns) { cur0 = lane ? sm->run_end[lane - 1] : 0; end0 = sm->run_end[lane]; }
+                    if (lane + 32 < nruns) { cur1 = sm->run_end[lane + 31]; end1 = sm->run_end[lane + 32]; }
+                    __syncwarp();
+                    for (int32_t k = 0; k < nl; ++k) {
+                        const uint32_t h0 = cur0 < end0 ? uint32_t(cur0 < NL_C ? sm->newly[cur0] : nl_g[cur0 - NL_C])
+                                                        : 0xffffffffu;
+                        const uint32_t h1 = cur1 < end1 ? uint32_t(cur1 < NL_C ? sm->newly[cur1] : nl_g[cur1 - NL_C])
+                                                        : 0xffffffffu;
+                        const uint32_t hm = __reduce_min_sync(FULL, min(h0, h1));
+                        if (h0 == hm) cur0 += 1;
+                        else if (h1 == hm) cur1 += 1;
+                        push(int32_t(hm));
+                    }
+                }
+            }
+            if (!dispatch()) bad = true;
+        }
+        if (lane == 0) {
+            A.makespan[d] = (n > 0 && !bad) ? now : 0;
+            if (bad) A.status[d] = INSP_ETIMEOUT;
+        }
+        __syncwarp();
+    }
+}
+
+void launch_sim(const SimArgs &A, int grid, cudaStream_t s) {
+    k_sim<<<grid, SIM_WARPS * 32, 0, s>>>(A);
+}
+// The unbatched form: one launch, one warp, one DAG.
+void launch_sim_single(const SimArgs &A, cudaStream_t s) { k_sim<<<1, 32, 0, s>>>(A); }
+int sim_threads() { return SIM_WARPS * 32; }
+int sim_warps() { return SIM_WARPS; }
+int sim_occupancy() {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim, SIM_WARPS * 32, 0) != cudaSuccess) return 0;
+    return nb;
+}
+
+}  // namespace insp

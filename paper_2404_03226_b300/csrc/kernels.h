@@ -1,0 +1,52 @@
+// Launch interface between the host runtime (insp_api.cu) and the kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace insp {
+
+struct SimArgs {
+    DevBatch B;
+    int32_t n_cpu, n_gpu;
+    int64_t xfer;
+    int32_t policy, task_window, s_inc, s_dec, dec_step, c;
+    int64_t k_inc_tasks, k_inc_ns;
+    const int64_t *unit_time_def;  // per DAG default unit time (k_inc default)
+    const int32_t *indeg0;
+    const int32_t *ia, *ie;
+    int32_t *worker;
+    int64_t *start, *end, *makespan;
+    int32_t *status;
+    // scratch, indexed by global task id
+    int2 *st_a;         // {remaining in-degree, node of the latest predecessor completion}
+    longlong2 *st_b;    // {latest completion time, latest on another node}
+    int32_t *p_idw, *p_seq, *p_ia, *p_ie;  // pool spill
+    int64_t *p_dr, *p_cost;
+    int32_t *nl;        // released-task spill
+    // work distribution
+    const int32_t *order;  // DAGs by descending size
+    int32_t *counter;
+    int32_t single_dag;    // >= 0: only that DAG, one warp
+};
+
+void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
+                     int grid, cudaStream_t s);
+void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s);
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
+               int32_t *done, int32_t epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s);
+void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
+               const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
+               uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s);
+void launch_sim(const SimArgs &A, int grid, cudaStream_t s);
+void launch_sim_single(const SimArgs &A, cudaStream_t s);
+int ia_threads();
+int ie_threads();
+int sim_threads();
+int sim_warps();
+int sim_occupancy();
+int ia_occupancy();
+int ie_occupancy();
+
+}  // namespace insp

@@ -1,0 +1,52 @@
+"""The C-ABI library loads on a machine without a GPU and exports every
+entry point that include/inspirit.h declares (no compute calls here)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    hdr = open(os.path.join(ROOT, "include", "inspirit.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"\b(insp_[a-z_0-9]+)\s*\(", hdr)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("insp_machine_create", "insp_dag_load_csr", "insp_attributes", "insp_simulate",
+                 "insp_batch_load_csr", "insp_attributes_batch", "insp_simulate_batch", "insp_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2404_03226_b300 import _lib
+    L = _lib.lib()
+    for name in _declared():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.so_path()], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (insp_[a-z_0-9]+)", out))
+    assert set(_declared()) <= exported
+    # the binding wraps every declared entry point under the same name
+    assert set(_declared()) <= set(_lib.symbols())
+
+
+def test_last_error_is_empty_string_initially():
+    from paper_2404_03226_b300 import _lib
+    assert isinstance(_lib.last_error(), str)
+
+
+def test_machine_argument_errors_without_gpu():
+    from paper_2404_03226_b300 import _lib
+    with pytest.raises(_lib.InspError) as e:
+        _lib.insp_machine_create(0, 0, 10)
+    assert e.value.code == _lib.INSP_EINVAL
+    with pytest.raises(_lib.InspError):
+        _lib.insp_machine_create(40, 40, 10)
+    with pytest.raises(_lib.InspError):
+        _lib.insp_machine_create(1, 1, -5)
+    h = _lib.insp_machine_create(8, 2, 20000)
+    _lib.insp_machine_destroy(h)

@@ -1,0 +1,175 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle: bit-exact
+inspiring ability / efficiency, worker, start, end and makespan."""
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from helpers import compare_dag, edge_case_dags, gpu_run, valid
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("policy", ["inspirit", "fifo"])
+def test_cholesky8(policy):
+    b = inputs.cholesky8()
+    m = inputs.MACHINE_CHOLESKY8
+    g = gpu_run(b, m, policy)
+    assert (g["status"] == 0).all()
+    compare_dag(b, 0, g, m, policy)
+
+
+@pytest.mark.parametrize("policy", ["inspirit", "fifo"])
+def test_layered_small_sizes(policy):
+    """Layered DAGs spanning several 32-source blocks, ragged tails."""
+    b = inputs.layered(48, cfg=90, n_min=1, n_max=300)
+    m = inputs.MACHINE_LAYERED
+    g = gpu_run(b, m, policy)
+    assert (g["status"] == 0).all()
+    for d in range(b.ndag):
+        compare_dag(b, d, g, m, policy)
+
+
+@pytest.mark.parametrize("machine", [inputs.Machine(1, 0, 0), inputs.Machine(0, 1, 5), inputs.Machine(3, 2, 7),
+                                     inputs.Machine(32, 8, 20000), inputs.Machine(60, 4, 1000)])
+def test_edge_case_dags(machine):
+    dags = edge_case_dags()
+    b = inputs.concat_dags(dags)
+    for policy in ("inspirit", "fifo"):
+        g = gpu_run(b, machine, policy)
+        assert (g["status"] == 0).all()
+        for d in range(b.ndag):
+            compare_dag(b, d, g, machine, policy)
+
+
+def test_empty_dags_in_batch():
+    dags = [inputs.make_dag(0, [], [], []), inputs.make_dag(3, [(0, 1)], [1, 2, 3], [3, 2, 1]),
+            inputs.make_dag(0, [], [], [])]
+    b = inputs.concat_dags(dags)
+    m = inputs.Machine(2, 1, 4)
+    g = gpu_run(b, m)
+    assert list(g["makespan"][[0, 2]]) == [0, 0]
+    compare_dag(b, 1, g, m)
+
+
+@pytest.mark.parametrize("kind,N", [(inputs.KIND_CHOLESKY, 16), (inputs.KIND_LU, 8), (inputs.KIND_QR, 8)])
+def test_tiled_per_task_costs(kind, N):
+    b = inputs.tiled(kind, N, 3, cfg=91)
+    m = inputs.MACHINE_TILED
+    g = gpu_run(b, m)
+    assert (g["status"] == 0).all()
+    for d in range(b.ndag):
+        compare_dag(b, d, g, m)
+
+
+def test_explicit_unit_times_narrow_and_wide():
+    b = inputs.layered(12, cfg=92, n_min=20, n_max=400)
+    m = inputs.MACHINE_LAYERED
+    rng = np.random.default_rng(0)
+    for T in (rng.integers(1, 200_000, b.ndag), np.full(b.ndag, 3_000_000_000)):
+        g = gpu_run(b, m, unit_time=T)
+        for d in range(b.ndag):
+            compare_dag(b, d, g, m, unit_time=int(T[d]))
+
+
+def test_per_dag_launch_matches_batched():
+    b = inputs.layered(16, cfg=93, n_max=600)
+    m = inputs.MACHINE_LAYERED
+    g1 = gpu_run(b, m)
+    g2 = gpu_run(b, m, per_dag=True)
+    for k in ("ia", "ie", "worker", "start", "end", "makespan"):
+        np.testing.assert_array_equal(g1[k], g2[k])
+
+
+def test_full_layered_workload_sampled():
+    """All 4096 layered DAGs in the batched launch: every schedule valid and
+    bounded, a sample (largest, smallest, spread) bit-exact vs the oracle."""
+    b = inputs.layered4096()
+    m = inputs.MACHINE_LAYERED
+    g = gpu_run(b, m)
+    assert (g["status"] == 0).all()
+    sizes = b.sizes()
+    order = np.argsort(-sizes, kind="stable")
+    sample = list(order[:3]) + list(order[-2:]) + list(range(0, b.ndag, 512))
+    for d in sample:
+        compare_dag(b, int(d), g, m)
+    for d in range(0, b.ndag, 7):
+        assert valid(b, d, g, m) == (0, -1)
+    # repeat: deterministic
+    g2 = gpu_run(b, m)
+    np.testing.assert_array_equal(g["makespan"], g2["makespan"])
+    np.testing.assert_array_equal(g["start"], g2["start"])
+
+
+def test_load_errors():
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    m = P.Machine(2, 1, 10)
+    good = inputs.make_dag(3, [(0, 1), (1, 2)], [1, 1, 1], [1, 1, 1])
+    cases = []
+    back = inputs.Dag(2, np.array([0, 0, 1], np.int32), np.array([0], np.int32), np.zeros(2, np.uint8),
+                      np.ones(2, np.int64), np.ones(2, np.int64))
+    cases.append((back, _lib.INSP_ENOTTOPO))
+    dup = inputs.Dag(2, np.array([0, 2, 2], np.int32), np.array([1, 1], np.int32), np.zeros(2, np.uint8),
+                     np.ones(2, np.int64), np.ones(2, np.int64))
+    cases.append((dup, _lib.INSP_EINVAL))
+    zero = inputs.make_dag(3, [(0, 1)], [1, 0, 1], [1, 1, 1])
+    cases.append((zero, _lib.INSP_EINVAL))
+    oob = inputs.Dag(2, np.array([0, 1, 1], np.int32), np.array([5], np.int32), np.zeros(2, np.uint8),
+                     np.ones(2, np.int64), np.ones(2, np.int64))
+    cases.append((oob, _lib.INSP_EINVAL))
+    huge = inputs.make_dag(2, [], [1 << 53, (1 << 53) + 1], [1, 1])
+    cases.append((huge, _lib.INSP_EOVERFLOW))
+    for dag, code in cases:
+        assert oracle.check_dag(dag, 10) == code  # the oracle agrees on the code
+        with pytest.raises(_lib.InspError) as e:
+            P.DagBatch(m, inputs.concat_dags([good, dag]))
+        assert e.value.code == code
+    bad_type = inputs.concat_dags([good])
+    bad_type.task_cost = None
+    bad_type.type = np.array([0, 3, 0], np.uint8)
+    bad_type.type_cost = np.ones((1, 2, 2), np.int64)
+    bad_type.n_types = 2
+    with pytest.raises(_lib.InspError) as e:
+        P.DagBatch(m, bad_type)
+    assert e.value.code == _lib.INSP_EINVAL
+
+
+def test_host_pointer_path_matches_device_path():
+    """The C ABI with host arrays (staged by the library) gives the same result."""
+    from paper_2404_03226_b300 import _lib
+    import paper_2404_03226_b300 as P
+    b = inputs.layered(8, cfg=94, n_max=500)
+    m = inputs.MACHINE_LAYERED
+    g = gpu_run(b, m)
+    M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
+    B = P.DagBatch(M, b)
+    n = b.n_total
+    ia = np.zeros(n, np.int32); ie = np.zeros(n, np.int32)
+    _lib.insp_attributes_batch(B.handle, None, ia, ie)
+    w = np.zeros(n, np.int32); s = np.zeros(n, np.int64); e = np.zeros(n, np.int64); mk = np.zeros(b.ndag, np.int64)
+    _lib.insp_simulate_batch(B.handle, ia, ie, w, s, e, mk)
+    np.testing.assert_array_equal(ia, g["ia"]); np.testing.assert_array_equal(ie, g["ie"])
+    np.testing.assert_array_equal(w, g["worker"]); np.testing.assert_array_equal(mk, g["makespan"])
+
+
+def test_single_dag_entry_points():
+    from paper_2404_03226_b300 import _lib
+    import paper_2404_03226_b300 as P
+    d = inputs.cholesky8().dag(0)
+    m = inputs.MACHINE_CHOLESKY8
+    M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
+    h = _lib.insp_dag_load_csr(M.handle, d.n, d.row_ptr, d.col_idx, None, 1, None,
+                               np.ascontiguousarray(np.stack([d.c_cpu, d.c_gpu], 1)))
+    try:
+        ia = np.zeros(d.n, np.int32); ie = np.zeros(d.n, np.int32)
+        _lib.insp_attributes(h, 0, ia, ie)
+        w = np.zeros(d.n, np.int32); s = np.zeros(d.n, np.int64); e = np.zeros(d.n, np.int64)
+        mk = np.zeros(1, np.int64)
+        _lib.insp_simulate(h, ia, ie, w, s, e, mk)
+    finally:
+        _lib.insp_dag_destroy(h)
+    r = oracle.simulate(d, m)
+    np.testing.assert_array_equal(ia, r["ia"]); np.testing.assert_array_equal(ie, r["ie"])
+    np.testing.assert_array_equal(w, r["worker"]); np.testing.assert_array_equal(s, r["start"])
+    assert int(mk[0]) == r["makespan"]
