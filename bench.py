@@ -1,0 +1,390 @@
+#!/usr/bin/env python
+"""Benchmark: scheduled tasks per second of the INSPIRIT schedule evaluation
+(inspiring attributes + adaptive-priority list-scheduling run) on one B300.
+
+Workload: the 4096 random layered DAGs (n ~ U[50, 2000], layer width
+U[4, 64], edge probability U[0.1, 0.5] to the next U{1..3} layers, 8 task
+types, log-normal per-type costs) on 8 CPU + 2 GPU workers, 20 us transfer.
+A step is one pass of the whole path over the batch: inspiring ability,
+inspiring efficiency, and the simulation, with the DAGs resident in HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank evaluates its own 4096-DAG window (weak scaling).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "scheduled tasks/sec on 1 B300, batched vs per-DAG form; makespan exact vs oracle"
+UNIT = "tasks/s"
+WORKLOAD = ("4096 random layered DAGs (n~U[50,2000], width U[4,64], p U[0.1,0.5], span U{1,2,3}, 8 types, "
+            "log-normal costs) on 8 CPU + 2 GPU workers, 20 us transfer, INSPIRIT policy")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------- clocks
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, device: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(device)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+        self.t0 = self.t1 = None
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
+        if self.p is not None:
+            time.sleep(0.3)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(parts[0].split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                rows.append((ts, float(parts[2]), float(parts[3]), parts[6:10]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sel = [r for r in rows if self.t0 is None or (self.t0 - 1 <= r[0] <= (self.t1 or r[0]) + 1)] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in sel for i, v in enumerate(r[3]) if v.lower().startswith("active")})
+        return {"sm_mhz": float(np.median([r[1] for r in sel])), "sm_max_mhz": float(max(r[2] for r in sel)),
+                "reasons": reasons, "samples": len(sel)}
+
+
+# ---------------------------------------------------------------- roofline
+def algorithmic_bytes(batch):
+    """Minimal HBM bytes per launch of each kernel: inputs read once, outputs
+    written once (scratch excluded)."""
+    n, m, nd = batch.n_total, batch.m_total, batch.ndag
+    csr = 4 * (n + nd) + 4 * m  # row_ptr + col_idx
+    return {
+        "k_ia": csr + 4 * n,                          # ia written
+        "k_ie": csr + n + 4 * n,                      # type read, ie written
+        "k_sim": csr + n + 4 * n + 8 * n + 20 * n + 8 * nd,  # type, in-degree, ia+ie read; worker/start/end + makespan
+    }
+
+
+def traffic_from_profile(kernel: str):
+    """dram bytes per launch recorded by an ncu capture in profiles/, if the
+    kernel source has not changed since."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    rec = d.get(kernel)
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2404_03226_b300", "csrc", rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+        return None
+    return rec["bytes_per_launch_full"]
+
+
+# --------------------------------------------------------------------- arms
+def cpu_baseline(batch, machine, budget_tasks=300000):
+    """The oracle, as it stands, on the first DAGs of the workload (one core)."""
+    import oracle
+    tasks = 0
+    idx = []
+    for d in range(batch.ndag):
+        idx.append(d)
+        tasks += int(batch.task_base[d + 1] - batch.task_base[d])
+        if tasks >= budget_tasks:
+            break
+    dags = [batch.dag(d) for d in idx]
+    t0 = time.perf_counter()
+    for g in dags:
+        r = oracle.simulate(g, machine)
+        assert r["rc"] == 0
+    dt = time.perf_counter() - t0
+    return {"value": tasks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks), attributes + simulation, "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def run_reference(args, rank):
+    """The oracle arm: same metric on a bounded sample per step, host cores."""
+    import inputs
+    import oracle
+    if rank != 0:
+        return
+    batch = inputs.layered4096()
+    machine = inputs.MACHINE_LAYERED
+    budget = 25000
+    idx, tasks = [], 0
+    for d in range(batch.ndag):
+        idx.append(d)
+        tasks += int(batch.task_base[d + 1] - batch.task_base[d])
+        if tasks >= budget:
+            break
+    dags = [batch.dag(d) for d in idx]
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        for g in dags:
+            oracle.simulate(g, machine)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step = float(np.mean(times))
+    v = tasks / step
+    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+          "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks) per step, single-threaded"}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample_tasks": tasks},
+                      "cpu_baseline": cb,
+                      "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import inputs
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # weak scaling: each rank its own 4096 DAGs (--ndag: the first K of them, for profiling captures)
+    batch = inputs.layered4096(ndag=args.ndag, first=rank * 4096)
+    mach = inputs.MACHINE_LAYERED
+    machine = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns)
+    b = P.DagBatch(machine, batch)
+    n, ndag = b.n_tasks, b.ndag
+    stream = torch.cuda.current_stream(dev)
+    ia = torch.empty(n, dtype=torch.int32, device=dev)
+    ie = torch.empty(n, dtype=torch.int32, device=dev)
+    worker = torch.empty(n, dtype=torch.int32, device=dev)
+    start = torch.empty(n, dtype=torch.int64, device=dev)
+    end = torch.empty(n, dtype=torch.int64, device=dev)
+    mk = torch.empty(ndag, dtype=torch.int64, device=dev)
+
+    def step():
+        _lib.insp_attributes_batch(b.handle, None, ia, ie, stream)
+        _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if _lib.insp_batch_status(b.handle) != 0:
+        raise RuntimeError("device-side status not OK: " + _lib.last_error())
+
+    clocks = ClockSampler(local_rank)
+    time.sleep(0.6)  # let the sampler start
+    _lib.insp_batch_timing(b.handle, reset=True)
+    _lib.insp_batch_set_timing(b.handle, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.mark_start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks.mark_end()
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    _lib.insp_batch_set_timing(b.handle, False)
+    kms, klaunch = _lib.insp_batch_timing(b.handle, reset=True)
+    clk = clocks.stop()
+    if _lib.insp_batch_status(b.handle) != 0:
+        raise RuntimeError("device-side status not OK: " + _lib.last_error())
+
+    tasks_all, t_max = float(n) * args.steps, elapsed
+    if dist is not None:
+        t = torch.tensor([tasks_all, elapsed], dtype=torch.float64, device=dev)
+        s_ = t.clone()
+        dist.all_reduce(s_, op=dist.ReduceOp.SUM)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tasks_all, t_max = float(s_[0]), float(t[1])
+    value = tasks_all / t_max
+
+    # ---- roofline of the dominant kernel
+    names = ["k_ia", "k_ie", "k_sim"]
+    alg = algorithmic_bytes(batch)
+    per_launch_ms = {names[k]: kms[k] / max(klaunch[k], 1) for k in range(3)}
+    share = {names[k]: kms[k] / max(kms[:3].sum(), 1e-9) for k in range(3)}
+    dom = max(names, key=lambda k: share[k])
+    peak, peak_kind = load_peaks()
+    achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_from_profile(dom), "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
+                "kernel_ms": {k: round(v, 4) for k, v in per_launch_ms.items()},
+                "kernel_share": {k: round(v, 4) for k, v in share.items()},
+                "step_bytes": int(sum(alg.values())),
+                "step_frac": sum(alg.values()) / (t_max / args.steps) / 1e9 / peak}
+
+    # ---- per-DAG launch form on a sample (same kernels, one DAG per launch)
+    per_dag = None
+    if rank == 0 and not args.profile:
+        k_sample = 64
+        sub = batch.subset(range(k_sample))
+        dags, outs = [], []
+        for d in range(k_sample):
+            g = sub.dag(d)
+            h = _lib.insp_dag_load_csr(machine.handle, g.n, g.row_ptr, g.col_idx, None, 1, None,
+                                       np.ascontiguousarray(np.stack([g.c_cpu, g.c_gpu], 1)))
+            dags.append(h)
+            outs.append([torch.empty(max(g.n, 1), dtype=dt, device=dev) for dt in
+                         (torch.int32, torch.int32, torch.int32, torch.int64, torch.int64)] +
+                        [torch.empty(1, dtype=torch.int64, device=dev)])
+
+        def per_dag_pass():
+            for h, o in zip(dags, outs):
+                _lib.insp_attributes(h, 0, o[0], o[1], stream)
+                _lib.insp_simulate(h, o[0], o[1], o[2], o[3], o[4], o[5], stream)
+
+        per_dag_pass()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            per_dag_pass()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_pd = e0.elapsed_time(e1) / 1e3 / reps
+        sub_tasks = int(sub.n_total)
+        for h in dags:
+            _lib.insp_dag_destroy(h)
+        pd_value = sub_tasks / t_pd
+        per_dag = {"value": pd_value, "unit": UNIT, "sample_dags": k_sample, "sample_tasks": sub_tasks,
+                   "batched_over_per_dag": (n * args.steps / elapsed) / pd_value}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if rank == 0 and not args.profile:
+        def pinned(a):
+            t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            return t
+        h_tb, h_eb = pinned(batch.task_base), pinned(batch.edge_base)
+        h_rp, h_ci, h_ty = pinned(batch.row_ptr), pinned(batch.col_idx), pinned(batch.type)
+        h_tc = pinned(batch.type_cost)
+        o_w = torch.empty(n, dtype=torch.int32).pin_memory()
+        o_s = torch.empty(n, dtype=torch.int64).pin_memory()
+        o_e = torch.empty(n, dtype=torch.int64).pin_memory()
+        o_m = torch.empty(ndag, dtype=torch.int64).pin_memory()
+        h2d = sum(int(t.numel() * t.element_size()) for t in (h_tb, h_eb, h_rp, h_ci, h_ty, h_tc))
+        d2h = sum(int(t.numel() * t.element_size()) for t in (o_w, o_s, o_e, o_m))
+
+        def e2e_step():
+            h = _lib.insp_batch_load_csr(machine.handle, ndag, h_tb, h_eb, h_rp, h_ci, h_ty, batch.n_types, h_tc,
+                                         None)
+            try:
+                _lib.insp_attributes_batch(h, None, ia, ie, stream)
+                _lib.insp_simulate_batch(h, ia, ie, o_w, o_s, o_e, o_m, stream)  # host outputs: D2H + sync
+            finally:
+                _lib.insp_batch_destroy(h)
+
+        e2e_step()
+        k_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            e2e_step()
+        torch.cuda.synchronize()
+        t_e2e = (time.perf_counter() - t0) / k_e2e
+        assert np.array_equal(o_m.numpy(), mk.cpu().numpy())
+        e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step": t_e2e * 1e3, "steps": k_e2e}
+
+    cb = cpu_baseline(batch, mach) if (rank == 0 and world == 1 and not args.profile) else None
+
+    if rank == 0:
+        res = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD if ndag == 4096 else f"first {ndag} of: " + WORKLOAD, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
+                       "machine": "8 CPU + 2 GPU workers, xfer 20000 ns", "policy": "INSPIRIT (defaults)",
+                       "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
+                             f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+            "per_dag_form": per_dag,
+            "e2e": e2e,
+            "roofline": roofline,
+            "cpu_baseline": cb,
+            "clocks": clk,
+            "gpu_launches": int(klaunch[:3].sum()),
+        }
+        print(json.dumps(res), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ndag", type=int, default=4096, help="first K DAGs of the workload (profiling captures)")
+    ap.add_argument("--profile", action="store_true",
+                    help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -84,6 +84,8 @@ typedef struct insp_batch insp_dag;       /* a batch holding exactly one DAG */
  * may be NULL (all defaults).  Errors: INSP_EINVAL, INSP_ENOMEM. */
 int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy,
                         insp_machine **out);
+/* Destroy a machine after every batch loaded on it: a destroyed batch hands its
+ * kernel scratch back to its machine for reuse by the next load. */
 void insp_machine_destroy(insp_machine *m);
 
 /* Install the learned proposal scorer used by INSP_POLICY_LEARNED: an MLP
@@ -155,6 +157,15 @@ int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, i
  * batch (INSP_OK or INSP_ETIMEOUT), copied to the host array status[ndag].
  * Synchronises the batch's last stream.  Returns the first non-OK status. */
 int insp_batch_status(insp_batch *b, int32_t *status);
+
+/* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
+ * call on the batch records CUDA events on its stream around each kernel.
+ * insp_batch_timing waits for them and returns the summed milliseconds and
+ * launch counts since the last reset, per kernel: [0] inspiring ability,
+ * [1] inspiring efficiency, [2] batched simulation, [3] per-DAG simulation
+ * launches.  ms and launches may be NULL; reset != 0 clears the sums. */
+int insp_batch_set_timing(insp_batch *b, int32_t enable);
+int insp_batch_timing(insp_batch *b, double *ms, int64_t *launches, int32_t reset);
 
 /* Batch facts: number of DAGs, total tasks, total edges. */
 int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges);

@@ -201,8 +201,10 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
         tr = _Trace(_p(bufs["t"], _i64p), _p(bufs["nready"], _i32p), _p(bufs["mode"], _i32p),
                     _p(bufs["task"], _i32p), _p(bufs["worker"], _i32p), 0, feat_pop, feat_cap, 0,
                     _p(bufs["feat_task"], _i32p), _p(bufs["feat"], _i32p))
+    # k_inc's default is P tasks per the DAG's *default* unit time, whatever T the
+    # attributes used (0 lets orc_simulate take the default).
     rc = _L().orc_simulate(n, _p(rp, _i32p), _p(ci, _i32p), _p(cc, _i64p), _p(cg, _i64p), machine.n_cpu,
-                           machine.n_gpu, machine.xfer_ns, ctypes.byref(pol), T, _p(a, _i32p), _p(e, _i32p),
+                           machine.n_gpu, machine.xfer_ns, ctypes.byref(pol), 0, _p(a, _i32p), _p(e, _i32p),
                            None if w is None else _p(w, _i16p), None if fobj is None else ctypes.byref(fobj),
                            _p(worker, _i32p), _p(start, _i64p), _p(end, _i64p), _p(mk, _i64p),
                            None if tr is None else ctypes.byref(tr))

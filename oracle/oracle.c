@@ -415,6 +415,8 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
     int rc = orc_check_dag(n, row_ptr, col_idx, c_cpu, c_gpu, xfer);
     if (rc) return rc;
     if (pol_in->policy == POL_LEARNED && !mlp_w) return ORC_EINVAL;
+    /* unit_time only sets k_inc's default (P tasks per unit_time ns); <= 0
+     * selects the DAG's default unit time. */
     if (unit_time <= 0) unit_time = orc_default_unit_time(n, c_gpu);
     orc_policy pol;
     orc_resolve_policy(pol_in, P, unit_time, &pol);

@@ -48,6 +48,8 @@ _PROTOS = {
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "insp_batch_set_timing": (ctypes.c_int, [_vp, _i32]),
+    "insp_batch_timing": (ctypes.c_int, [_vp, _vp, _vp, _i32]),
 }
 
 
@@ -176,3 +178,17 @@ def insp_batch_info(b) -> tuple[int, int, int]:
     nd, nt, ne = _i32(), _i64(), _i64()
     check(lib().insp_batch_info(b, ctypes.byref(nd), ctypes.byref(nt), ctypes.byref(ne)))
     return nd.value, nt.value, ne.value
+
+
+def insp_batch_set_timing(b, enable: bool) -> None:
+    check(lib().insp_batch_set_timing(b, 1 if enable else 0))
+
+
+def insp_batch_timing(b, reset: bool = False):
+    """(ms[4], launches[4]) per kernel: inspiring ability, inspiring efficiency,
+    batched simulation, per-DAG simulation."""
+    import numpy as np
+    ms = np.zeros(4, np.float64)
+    n = np.zeros(4, np.int64)
+    check(lib().insp_batch_timing(b, ptr(ms), ptr(n), 1 if reset else 0))
+    return ms, n

@@ -2,6 +2,7 @@
 // device residency of the DAGs, scratch sizing, launch configuration and
 // host/device pointer staging.  All scheduling arithmetic runs in the kernels.
 #include <algorithm>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -39,8 +40,10 @@ struct DBuf {
         p = nullptr;
         bytes = 0;
     }
-    int alloc(size_t n) {
+    int alloc(size_t n, bool *fresh = nullptr) {
+        if (fresh) *fresh = false;
         if (n <= bytes && p) return INSP_OK;
+        if (fresh) *fresh = true;
         release();
         if (n == 0) n = 16;
         cudaError_t e = cudaMalloc(&p, n);
@@ -83,15 +86,32 @@ int device_info(DeviceInfo &di) {
 
 }  // namespace
 
+// Scratch of the kernels.  A batch borrows one set from its machine at load
+// and hands it back when destroyed, so reloading batches through the public
+// API reuses device memory instead of allocating it again.
+struct Scratch {
+    DBuf st_a, st_b, p_idw, p_seq, p_ia, p_ie, p_dr, p_cost, nl;  // simulation
+    DBuf ia_bits, ia_done;                                         // inspiring ability
+    DBuf ie_rec, ie_acc;                                           // inspiring efficiency
+    DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
+    int32_t ia_epoch = 0;   // done[] flags equal to the epoch are published in this call
+    uint32_t ie_tag = 1;    // records whose tag differs from the work item's are empty
+};
+
 struct insp_machine {
     int32_t n_cpu = 0, n_gpu = 0;
     int64_t xfer = 0;
     insp_policy pol{};
     bool has_scorer = false;
+    std::vector<std::unique_ptr<Scratch>> spare;
 };
 
+enum { TK_IA = 0, TK_IE = 1, TK_SIM = 2, TK_SIM_SINGLE = 3, TK_N = 4 };
+
 struct insp_batch {
-    insp_machine mach;
+    insp_machine *owner = nullptr;
+    insp_machine mach_params;
+    const insp_machine &mach = mach_params;
     int32_t ndag = 0, n_types = 1;
     int64_t n_total = 0, m_total = 0;
     std::vector<int64_t> h_task_base, h_edge_base;
@@ -100,17 +120,21 @@ struct insp_batch {
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;
-    // scratch
-    DBuf st_a, st_b, p_idw, p_seq, p_ia, p_ie, p_dr, p_cost, nl;  // simulation
-    DBuf ia_bits, ia_done;                                         // inspiring ability
-    DBuf ie_rec, ie_acc;                                           // inspiring efficiency
+    std::unique_ptr<Scratch> sc;
     int64_t ia_slot_words = 0, ie_rec_stride = 0;
     int grid_sim = 1, grid_ia = 1, grid_ie = 1;
-    int32_t ia_epoch = 0;
-    uint32_t ie_tag = 1;
-    // staging for host pointers
-    DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;
     cudaStream_t last_stream = nullptr;
+    // kernel timing (tracing aid)
+    bool timing = false;
+    struct Pending { int kind; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double ms[TK_N] = {0, 0, 0, 0};
+    int64_t launches[TK_N] = {0, 0, 0, 0};
+
+    ~insp_batch() {
+        for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
+    }
 
     insp::DevBatch dev() const {
         insp::DevBatch B;
@@ -140,12 +164,22 @@ int alloc_scratch(insp_batch *b) {
     DeviceInfo di;
     int rc = device_info(di);
     if (rc) return rc;
+    if (!b->sc) {
+        if (b->owner && !b->owner->spare.empty()) {
+            b->sc = std::move(b->owner->spare.back());
+            b->owner->spare.pop_back();
+        } else {
+            b->sc.reset(new (std::nothrow) Scratch);
+            if (!b->sc) return fail(INSP_ENOMEM, "host allocation");
+        }
+    }
+    Scratch &S = *b->sc;
     const int64_t N = std::max<int64_t>(b->n_total, 1);
     // simulation: per task release state, pool spill, released-task spill
-    if ((rc = b->st_a.alloc(N * sizeof(int2))) || (rc = b->st_b.alloc(N * sizeof(longlong2))) ||
-        (rc = b->p_idw.alloc(N * 4)) || (rc = b->p_seq.alloc(N * 4)) || (rc = b->p_ia.alloc(N * 4)) ||
-        (rc = b->p_ie.alloc(N * 4)) || (rc = b->p_dr.alloc(N * 8)) || (rc = b->p_cost.alloc(N * 8)) ||
-        (rc = b->nl.alloc(N * 4)))
+    if ((rc = S.st_a.alloc(N * sizeof(int2))) || (rc = S.st_b.alloc(N * sizeof(longlong2))) ||
+        (rc = S.p_idw.alloc(N * 4)) || (rc = S.p_seq.alloc(N * 4)) || (rc = S.p_ia.alloc(N * 4)) ||
+        (rc = S.p_ie.alloc(N * 4)) || (rc = S.p_dr.alloc(N * 8)) || (rc = S.p_cost.alloc(N * 8)) ||
+        (rc = S.nl.alloc(N * 4)))
         return rc;
     b->grid_sim = std::max(1, std::min(di.sms * di.occ_sim, (b->ndag + insp::sim_warps() - 1) / insp::sim_warps()));
     // inspiring ability: one bitset slot per CTA (rows of max_n tasks x ceil(max_n/32) words)
@@ -159,9 +193,13 @@ int alloc_scratch(insp_batch *b) {
     int64_t gia = std::min<int64_t>(int64_t(di.sms) * di.occ_ia, std::max(b->ndag, 1));
     gia = std::max<int64_t>(1, std::min<int64_t>(gia, budget / (b->ia_slot_words * 4)));
     b->grid_ia = int(gia);
-    if ((rc = b->ia_bits.alloc(size_t(gia) * b->ia_slot_words * 4)) || (rc = b->ia_done.alloc(N * 4))) return rc;
-    CU(cudaMemset(b->ia_done.p, 0, N * 4));
-    b->ia_epoch = 0;
+    bool fresh = false;
+    if ((rc = S.ia_bits.alloc(size_t(gia) * b->ia_slot_words * 4)) || (rc = S.ia_done.alloc(N * 4, &fresh)))
+        return rc;
+    if (fresh) {
+        CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
+        S.ia_epoch = 0;
+    }
     // inspiring efficiency: per warp a record per task of the largest DAG and a W x 32 ring
     b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
     const int ie_warps_per_cta = insp::ie_threads() / 32;
@@ -171,13 +209,33 @@ int alloc_scratch(insp_batch *b) {
     gie = std::max<int64_t>(1, std::min<int64_t>(gie, budget / (per_warp * ie_warps_per_cta)));
     b->grid_ie = int(gie);
     const int64_t warps = gie * ie_warps_per_cta;
-    if ((rc = b->ie_rec.alloc(size_t(warps) * b->ie_rec_stride * 16)) ||
-        (rc = b->ie_acc.alloc(size_t(warps) * b->W * 32 * 8)))
-        return rc;
-    CU(cudaMemset(b->ie_rec.p, 0, size_t(warps) * b->ie_rec_stride * 16));
-    b->ie_tag = 1;
+    if ((rc = S.ie_rec.alloc(size_t(warps) * b->ie_rec_stride * 16, &fresh))) return rc;
+    if (fresh) {
+        CU(cudaMemset(S.ie_rec.p, 0, S.ie_rec.bytes));
+        S.ie_tag = 1;
+    }
+    if ((rc = S.ie_acc.alloc(size_t(warps) * b->W * 32 * 8))) return rc;
     return INSP_OK;
 }
+
+// Events around one kernel launch when timing is enabled.
+struct TimedLaunch {
+    insp_batch *b;
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, e = nullptr;
+    TimedLaunch(insp_batch *b_, int kind_, cudaStream_t s_) : b(b_), kind(kind_), s(s_) {
+        if (b->timing && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&e) == cudaSuccess)
+            cudaEventRecord(a, s);
+    }
+    ~TimedLaunch() {
+        b->launches[kind] += 1;
+        if (a && e) {
+            cudaEventRecord(e, s);
+            b->pending.push_back({kind, a, e});
+        }
+    }
+};
 
 // Stage a caller array into a device buffer when it lives on the host.
 template <typename T>
@@ -261,7 +319,12 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     auto *b = new (std::nothrow) insp_batch;
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
-    b->mach = *m;
+    b->owner = m;
+    b->mach_params.n_cpu = m->n_cpu;
+    b->mach_params.n_gpu = m->n_gpu;
+    b->mach_params.xfer = m->xfer;
+    b->mach_params.pol = m->pol;
+    b->mach_params.has_scorer = m->has_scorer;
     b->ndag = ndag;
     b->n_types = n_types;
     b->h_task_base.resize(ndag + 1);
@@ -394,7 +457,8 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     const int64_t N = b->n_total;
     int32_t *d_ia, *d_ie;
     bool st_ia, st_ie;
-    if ((rc = stage_out(b->s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(b->s_ie, ie, N, d_ie, st_ie))) return rc;
+    Scratch &S = *b->sc;
+    if ((rc = stage_out(S.s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(S.s_ie, ie, N, d_ie, st_ie))) return rc;
     const int64_t *ut = b->unit_time_def.as<int64_t>();
     bool wide = b->max_unit_def >= 0x7fffffffLL;
     if (unit_time_ns) {
@@ -423,23 +487,28 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     if (b->ndag == 0) return INSP_OK;
     CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
     CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
-    b->ia_epoch += 1;
-    if (b->ia_epoch == 0x7fffffff) {
-        CU(cudaMemsetAsync(b->ia_done.p, 0, std::max<int64_t>(N, 1) * 4, s));
-        b->ia_epoch = 1;
+    S.ia_epoch += 1;
+    if (S.ia_epoch == 0x7fffffff) {
+        CU(cudaMemsetAsync(S.ia_done.p, 0, S.ia_done.bytes, s));
+        S.ia_epoch = 1;
     }
-    if (uint64_t(b->ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
-        const int64_t warps = int64_t(b->grid_ie) * (insp::ie_threads() / 32);
-        CU(cudaMemsetAsync(b->ie_rec.p, 0, size_t(warps) * b->ie_rec_stride * 16, s));
-        b->ie_tag = 1;
+    if (uint64_t(S.ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
+        CU(cudaMemsetAsync(S.ie_rec.p, 0, S.ie_rec.bytes, s));
+        S.ie_tag = 1;
     }
     insp::DevBatch B = b->dev();
     int32_t *ctr = b->counters.as<int32_t>();
-    insp::launch_ia(B, b->order.as<int32_t>(), ctr + 0, b->ia_bits.as<uint32_t>(), b->ia_slot_words,
-                    b->ia_done.as<int32_t>(), b->ia_epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
-    insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, b->ie_rec.as<uint4>(), b->ie_rec_stride,
-                    b->ie_acc.p, b->W, wide, b->ie_tag, d_ie, b->grid_ie, s);
-    b->ie_tag += uint32_t(b->n_items);
+    {
+        TimedLaunch tl(b, TK_IA, s);
+        insp::launch_ia(B, b->order.as<int32_t>(), ctr + 0, S.ia_bits.as<uint32_t>(), b->ia_slot_words,
+                        S.ia_done.as<int32_t>(), S.ia_epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
+    }
+    {
+        TimedLaunch tl(b, TK_IE, s);
+        insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
+                        b->ie_rec_stride, S.ie_acc.p, b->W, wide, S.ie_tag, d_ie, b->grid_ie, s);
+    }
+    S.ie_tag += uint32_t(b->n_items);
     CU(cudaGetLastError());
     if (st_ia || st_ie) {
         if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
@@ -468,12 +537,13 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
     const int64_t N = b->n_total;
     int rc;
     const int32_t *d_ia, *d_ie;
-    if ((rc = stage_in(b->s_ia, ia, N, s, d_ia)) || (rc = stage_in(b->s_ie, ie, N, s, d_ie))) return rc;
+    Scratch &S = *b->sc;
+    if ((rc = stage_in(S.s_ia, ia, N, s, d_ia)) || (rc = stage_in(S.s_ie, ie, N, s, d_ie))) return rc;
     int32_t *d_worker;
     int64_t *d_start, *d_end, *d_mk;
     bool sw, ss, se, sm;
-    if ((rc = stage_out(b->s_worker, worker, N, d_worker, sw)) || (rc = stage_out(b->s_start, start, N, d_start, ss)) ||
-        (rc = stage_out(b->s_end, end, N, d_end, se)) || (rc = stage_out(b->s_makespan, makespan, b->ndag, d_mk, sm)))
+    if ((rc = stage_out(S.s_worker, worker, N, d_worker, sw)) || (rc = stage_out(S.s_start, start, N, d_start, ss)) ||
+        (rc = stage_out(S.s_end, end, N, d_end, se)) || (rc = stage_out(S.s_makespan, makespan, b->ndag, d_mk, sm)))
         return rc;
     if (b->ndag > 0) {
         CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
@@ -500,24 +570,26 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         A.end = d_end;
         A.makespan = d_mk;
         A.status = b->status.as<int32_t>();
-        A.st_a = b->st_a.as<int2>();
-        A.st_b = b->st_b.as<longlong2>();
-        A.p_idw = b->p_idw.as<int32_t>();
-        A.p_seq = b->p_seq.as<int32_t>();
-        A.p_ia = b->p_ia.as<int32_t>();
-        A.p_ie = b->p_ie.as<int32_t>();
-        A.p_dr = b->p_dr.as<int64_t>();
-        A.p_cost = b->p_cost.as<int64_t>();
-        A.nl = b->nl.as<int32_t>();
+        A.st_a = S.st_a.as<int2>();
+        A.st_b = S.st_b.as<longlong2>();
+        A.p_idw = S.p_idw.as<int32_t>();
+        A.p_seq = S.p_seq.as<int32_t>();
+        A.p_ia = S.p_ia.as<int32_t>();
+        A.p_ie = S.p_ie.as<int32_t>();
+        A.p_dr = S.p_dr.as<int64_t>();
+        A.p_cost = S.p_cost.as<int64_t>();
+        A.nl = S.nl.as<int32_t>();
         A.order = b->order.as<int32_t>();
         A.counter = b->counters.as<int32_t>() + 8;
         if (per_dag) {
             for (int d = 0; d < b->ndag; ++d) {
                 A.single_dag = d;
+                TimedLaunch tl(b, TK_SIM_SINGLE, s);
                 insp::launch_sim_single(A, s);
             }
         } else {
             A.single_dag = -1;
+            TimedLaunch tl(b, TK_SIM, s);
             insp::launch_sim(A, b->grid_sim, s);
         }
         CU(cudaGetLastError());
@@ -558,4 +630,29 @@ INSP_API int insp_batch_status(insp_batch *b, int32_t *status) {
     int rc = first_status(b, st);
     if (status) std::copy(st.begin(), st.end(), status);
     return rc;
+}
+
+INSP_API int insp_batch_set_timing(insp_batch *b, int32_t enable) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    b->timing = enable != 0;
+    return INSP_OK;
+}
+
+INSP_API int insp_batch_timing(insp_batch *b, double *ms, int64_t *launches, int32_t reset) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    for (auto &p : b->pending) {
+        CU(cudaEventSynchronize(p.b));
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, p.a, p.b));
+        b->ms[p.kind] += t;
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    b->pending.clear();
+    for (int k = 0; k < TK_N; ++k) {
+        if (ms) ms[k] = b->ms[k];
+        if (launches) launches[k] = b->launches[k];
+        if (reset) { b->ms[k] = 0; b->launches[k] = 0; }
+    }
+    return INSP_OK;
 }
