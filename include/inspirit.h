@@ -170,6 +170,37 @@ int insp_batch_timing(insp_batch *b, double *ms, int64_t *launches, int32_t rese
 /* Batch facts: number of DAGs, total tasks, total edges. */
 int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges);
 
+/* ------------------------------------------------ no-allocation entry point
+ * insp_simulate_noalloc -- the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory: code running inside a framework
+ * whose allocator owns all of the GPU's memory (a stray cudaMalloc may fail or
+ * fragment it) and latency-critical loops that cannot afford the implicit
+ * synchronisation of cudaMalloc / cudaFree.
+ *
+ * Same result as insp_dag_load_csr + insp_simulate on one DAG with the same
+ * arguments (validation included), but it allocates nothing: its scratch is
+ * a fixed array of INSP_NOALLOC_SCRATCH_BYTES reserved in every GPU that loads
+ * the library, held until the process exits.  The caller passes device
+ * pointers only (a host pointer gives INSP_EINVAL): row_ptr[n+1], col_idx,
+ * type[n], type_cost[n_types][2] or task_cost[n][2], ia[n], ie[n] (from
+ * insp_attributes or the caller's own) and the outputs worker[n], start[n],
+ * end[n], makespan[1].  n above INSP_NOALLOC_MAX_TASKS gives INSP_EINVAL.
+ * policy may be NULL; INSP_POLICY_LEARNED is not accepted.
+ *
+ * The first call on a device looks up the array's device address on that
+ * device; make that first call before any stream capture.  Every call reuses
+ * the same array (it keeps the previous call's contents and clears what must
+ * start at zero), so calls whose work overlaps on the GPU -- two streams or
+ * two host threads -- race and must be serialised by the caller.  The call is
+ * synchronous: it waits for `stream` before returning the final status. */
+#define INSP_NOALLOC_MAX_TASKS 65536
+#define INSP_NOALLOC_SCRATCH_BYTES 4194560
+int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const uint8_t *type,
+                          int32_t n_types, const int64_t *type_cost, const int64_t *task_cost, int32_t n_cpu,
+                          int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy, const int32_t *ia,
+                          const int32_t *ie, int32_t *worker, int64_t *start, int64_t *end, int64_t *makespan,
+                          void *stream);
+
 /* Thread-local description of the last error on the calling thread ("" if none). */
 const char *insp_last_error(void);
 

@@ -50,6 +50,8 @@ _PROTOS = {
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "insp_batch_set_timing": (ctypes.c_int, [_vp, _i32]),
     "insp_batch_timing": (ctypes.c_int, [_vp, _vp, _vp, _i32]),
+    "insp_simulate_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _i32, _i64,
+                                             ctypes.POINTER(insp_policy), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
 
 
@@ -192,3 +194,16 @@ def insp_batch_timing(b, reset: bool = False):
     n = np.zeros(4, np.int64)
     check(lib().insp_batch_timing(b, ptr(ms), ptr(n), 1 if reset else 0))
     return ms, n
+
+
+INSP_NOALLOC_MAX_TASKS = 65536
+
+
+def insp_simulate_noalloc(n, row_ptr, col_idx, type, n_types, type_cost, task_cost, n_cpu, n_gpu, xfer_ns,
+                          policy, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    """The single-DAG simulation that allocates no device memory (all arrays
+    must be device tensors the caller owns); see include/inspirit.h."""
+    check(lib().insp_simulate_noalloc(n, ptr(row_ptr), ptr(col_idx), ptr(type), n_types, ptr(type_cost),
+                                      ptr(task_cost), n_cpu, n_gpu, xfer_ns,
+                                      None if policy is None else ctypes.byref(policy), ptr(ia), ptr(ie),
+                                      ptr(worker), ptr(start), ptr(end), ptr(makespan), stream_ptr(stream)))

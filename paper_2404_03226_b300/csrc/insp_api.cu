@@ -271,6 +271,11 @@ int first_status(insp_batch *b, std::vector<int32_t> &st) {
 
 }  // namespace
 
+namespace insp {
+// Lets other translation units of the library report through insp_last_error.
+void set_last_error(const std::string &msg) { g_err = msg; }
+}  // namespace insp
+
 // ===================================================================== ABI
 INSP_API const char *insp_last_error(void) { return g_err.c_str(); }
 
