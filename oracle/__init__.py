@@ -70,7 +70,7 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
             tmp = _SO + f".tmp{os.getpid()}"
-            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC])
+            subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-o", tmp, _SRC, "-lm"])
             os.replace(tmp, _SO)
     return _SO
 
@@ -95,6 +95,10 @@ def _L():
                                      ctypes.POINTER(_Force), _i32p, _i64p, _i64p, _i64p, ctypes.POINTER(_Trace)]
         lib.orc_validate.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int64, _i32p, _i64p, _i64p, ctypes.c_int64, _i32p]
+        _dp = ctypes.POINTER(ctypes.c_double)
+        lib.orc_mlp_loss_grad.restype = ctypes.c_double
+        lib.orc_mlp_loss_grad.argtypes = [ctypes.c_int32] * 3 + [_dp, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp]
+        lib.orc_adamw.argtypes = [ctypes.c_int32, _dp, _dp, _dp, _dp, ctypes.c_int32] + [ctypes.c_double] * 5
         lib.orc_optimum.restype = ctypes.c_int64
         lib.orc_optimum.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_int64, ctypes.c_int64]
@@ -244,3 +248,31 @@ def simulate_batch(batch, machine, policy: Policy | None = None, idx=None, unit_
     for d in (range(batch.ndag) if idx is None else idx):
         res.append(simulate(batch.dag(int(d)), machine, policy, unit_time))
     return res
+
+
+def mlp_nweights_dims(inp: int, h1: int, h2: int) -> int:
+    return inp * h1 + h1 + h1 * h2 + h2 + h2 + 1
+
+
+def mlp_loss_grad(w, x, target, dims=(16, 64, 64), mode: int = 1):
+    """(loss, grad) of the scorer's training loss in fp64; mode 0 smooth, 1
+    quantisation-aware with straight-through estimators (see oracle.c)."""
+    _dp = ctypes.POINTER(ctypes.c_double)
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    t = np.ascontiguousarray(target, np.float64)
+    g = np.zeros_like(w)
+    n = t.size
+    loss = _L().orc_mlp_loss_grad(dims[0], dims[1], dims[2], w.ctypes.data_as(_dp), mode, n, x.ctypes.data_as(_dp),
+                                  t.ctypes.data_as(_dp), g.ctypes.data_as(_dp))
+    return float(loss), g
+
+
+def adamw(w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
+    """One AdamW step in place (fp64)."""
+    _dp = ctypes.POINTER(ctypes.c_double)
+    for a in (w, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    _L().orc_adamw(w.size, w.ctypes.data_as(_dp), m.ctypes.data_as(_dp), v.ctypes.data_as(_dp),
+                   g.ctypes.data_as(_dp), t, lr, b1, b2, eps, wd)

@@ -23,7 +23,8 @@
  *  orc_validate  an independent check of a schedule's feasibility.
  *  orc_optimum   exhaustive optimum makespan for tiny DAGs.
  *  orc_mlp_*     integer restatement of the learned proposal scorer (fixed
- *                grid BF16 weights; see the scorer section below).
+ *                grid BF16 weights; see the scorer section below) and an
+ *                fp64 restatement of its training loss, gradient and AdamW.
  *
  * Readings where the paper is silent (each is also listed in the design
  * notes): self excluded from IA; IE counts a descendant only if every path to
@@ -36,6 +37,7 @@
  * moved by at least task_window since the last judgement, the count of
  * downward steps resets when a new peak is seen.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -693,4 +695,106 @@ EXPORT int64_t orc_optimum(int32_t n, const int32_t *row_ptr, const int32_t *col
                   upper_bound > 0 ? upper_bound + 1 : INT64_MAX, worker, indeg, end, free_at};
     bb(&S, 0, 0);
     return S.best;
+}
+
+/* ------------------------------------------------------ scorer training */
+/*
+ * fp64 restatement of the scorer's training loss and gradient, for checking
+ * the training kernels.  Network in -> h1 -> h2 -> 1, weights laid out as
+ * W1[in][h1], b1[h1], W2[h1][h2], b2[h2], W3[h2], b3[1] (real values).
+ * Loss = mean over samples of (y - target)^2.
+ *
+ * mode 0 (smooth): h = min(max(z, 0), 255), derivative 1 on 0 < z < 255.
+ * mode 1 (quantisation-aware, the inference network): the forward pass uses
+ *   w_q = clamp(round(64 w), -128, 128) / 64 and h = min(floor(max(z, 0)), 255),
+ *   i.e. exactly orc_mlp_score / 64 for the rounded weights; the backward pass
+ *   uses straight-through estimators: d w_q / d w = 1 when |64 w| <= 128.5,
+ *   else 0; d h / d z = 1 when 0 < z < 256, else 0 (round: half away from zero).
+ */
+static double q_weight(double w) {
+    double k = w * 64.0;
+    k = k >= 0 ? (double)(int64_t)(k + 0.5) : -(double)(int64_t)(-k + 0.5);
+    if (k > 128) k = 128;
+    if (k < -128) k = -128;
+    return k / 64.0;
+}
+static int q_pass(double w) { double k = w * 64.0; return k <= 128.5 && k >= -128.5; }
+
+EXPORT double orc_mlp_loss_grad(int32_t in, int32_t h1, int32_t h2, const double *w, int32_t mode, int32_t n,
+                                const double *x, const double *target, double *grad) {
+    const int32_t nw = in * h1 + h1 + h1 * h2 + h2 + h2 + 1;
+    const double *W1 = w, *B1 = W1 + in * h1, *W2 = B1 + h1, *B2 = W2 + h1 * h2, *W3 = B2 + h2, *B3 = W3 + h2;
+    double *gW1 = grad, *gB1 = gW1 + in * h1, *gW2 = gB1 + h1, *gB2 = gW2 + h1 * h2, *gW3 = gB2 + h2, *gB3 = gW3 + h2;
+    double *wq = (double *)malloc(sizeof(double) * (size_t)nw);
+    double *z1 = (double *)malloc(sizeof(double) * (size_t)h1), *a1 = (double *)malloc(sizeof(double) * (size_t)h1);
+    double *z2 = (double *)malloc(sizeof(double) * (size_t)h2), *a2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    double *d1 = (double *)malloc(sizeof(double) * (size_t)h1), *d2 = (double *)malloc(sizeof(double) * (size_t)h2);
+    if (!wq || !z1 || !a1 || !z2 || !a2 || !d1 || !d2) return -1.0;
+    for (int32_t i = 0; i < nw; ++i) { wq[i] = mode ? q_weight(w[i]) : w[i]; grad[i] = 0.0; }
+    const double *Q1 = wq, *QB1 = Q1 + in * h1, *Q2 = QB1 + h1, *QB2 = Q2 + h1 * h2, *Q3 = QB2 + h2, *QB3 = Q3 + h2;
+    (void)W1; (void)B1; (void)W2; (void)B2; (void)W3; (void)B3;
+    double loss = 0.0;
+    for (int32_t s = 0; s < n; ++s) {
+        const double *xs = x + (size_t)s * in;
+        for (int32_t j = 0; j < h1; ++j) {
+            double z = QB1[j];
+            for (int32_t i = 0; i < in; ++i) z += Q1[i * h1 + j] * xs[i];
+            z1[j] = z;
+            double h = z > 0 ? z : 0;
+            if (mode) h = (double)(int64_t)h;
+            a1[j] = h > 255 ? 255 : h;
+        }
+        for (int32_t j = 0; j < h2; ++j) {
+            double z = QB2[j];
+            for (int32_t i = 0; i < h1; ++i) z += Q2[i * h2 + j] * a1[i];
+            z2[j] = z;
+            double h = z > 0 ? z : 0;
+            if (mode) h = (double)(int64_t)h;
+            a2[j] = h > 255 ? 255 : h;
+        }
+        double y = QB3[0];
+        for (int32_t i = 0; i < h2; ++i) y += Q3[i] * a2[i];
+        const double e = y - target[s];
+        loss += e * e;
+        const double dy = 2.0 * e / n;
+        const double hi = mode ? 256.0 : 255.0;
+        gB3[0] += dy;
+        for (int32_t i = 0; i < h2; ++i) {
+            gW3[i] += dy * a2[i];
+            d2[i] = (z2[i] > 0 && z2[i] < hi) ? dy * Q3[i] : 0.0;
+            gB2[i] += d2[i];
+        }
+        for (int32_t i = 0; i < h1; ++i) {
+            double g = 0.0;
+            for (int32_t j = 0; j < h2; ++j) {
+                gW2[i * h2 + j] += a1[i] * d2[j];
+                g += Q2[i * h2 + j] * d2[j];
+            }
+            d1[i] = (z1[i] > 0 && z1[i] < hi) ? g : 0.0;
+            gB1[i] += d1[i];
+        }
+        for (int32_t i = 0; i < in; ++i)
+            for (int32_t j = 0; j < h1; ++j) gW1[i * h1 + j] += xs[i] * d1[j];
+    }
+    if (mode)
+        for (int32_t i = 0; i < nw; ++i)
+            if (!q_pass(w[i])) grad[i] = 0.0;
+    free(wq); free(z1); free(a1); free(z2); free(a2); free(d1); free(d2);
+    return loss / n;
+}
+
+/* One AdamW step (decoupled weight decay, Loshchilov and Hutter, ICLR 2019),
+ * step counter t >= 1: m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+ * w -= lr (m / (1-b1^t) / (sqrt(v / (1-b2^t)) + eps) + wd w). */
+EXPORT void orc_adamw(int32_t nw, double *w, double *m, double *v, const double *g, int32_t t, double lr,
+                      double b1, double b2, double eps, double wd) {
+    double c1 = 1.0, c2 = 1.0;
+    for (int32_t i = 0; i < t; ++i) { c1 *= b1; c2 *= b2; }
+    c1 = 1.0 - c1;
+    c2 = 1.0 - c2;
+    for (int32_t i = 0; i < nw; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        w[i] -= lr * ((m[i] / c1) / (sqrt(v[i] / c2) + eps) + wd * w[i]);
+    }
 }

@@ -122,6 +122,7 @@ struct insp_batch {
     int64_t max_unit_def = 1, n_items = 0;
     std::unique_ptr<Scratch> sc;
     int64_t ia_slot_words = 0, ie_rec_stride = 0;
+    bool ie_global_ready = false;
     int grid_sim = 1, grid_ia = 1, grid_ie = 1;
     cudaStream_t last_stream = nullptr;
     // kernel timing (tracing aid)
@@ -159,6 +160,8 @@ int copy_in(DBuf &dst, const void *src, size_t bytes) {
     if (bytes) CU(cudaMemcpy(dst.p, src, bytes, cudaMemcpyDefault));
     return INSP_OK;
 }
+
+int alloc_ie_global(insp_batch *b);
 
 int alloc_scratch(insp_batch *b) {
     DeviceInfo di;
@@ -200,21 +203,34 @@ int alloc_scratch(insp_batch *b) {
         CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
         S.ia_epoch = 0;
     }
-    // inspiring efficiency: per warp a record per task of the largest DAG and a W x 32 ring
+    // inspiring efficiency: window sweep scratch
     b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
+    return alloc_ie_global(b);
+}
+
+// Scratch of the global-memory inspiring-efficiency sweep: per warp one record
+// per task of the largest DAG and a W x 32 ring of int64 path weights.
+int alloc_ie_global(insp_batch *b) {
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    Scratch &S = *b->sc;
     const int ie_warps_per_cta = insp::ie_threads() / 32;
+    const int64_t budget = int64_t(24) << 30;
     int64_t gie = std::min<int64_t>(int64_t(di.sms) * di.occ_ie,
                                     (std::max<int64_t>(b->n_items, 1) + ie_warps_per_cta - 1) / ie_warps_per_cta);
     const int64_t per_warp = b->ie_rec_stride * 16 + int64_t(b->W) * 32 * 8;
     gie = std::max<int64_t>(1, std::min<int64_t>(gie, budget / (per_warp * ie_warps_per_cta)));
     b->grid_ie = int(gie);
     const int64_t warps = gie * ie_warps_per_cta;
+    bool fresh = false;
     if ((rc = S.ie_rec.alloc(size_t(warps) * b->ie_rec_stride * 16, &fresh))) return rc;
     if (fresh) {
         CU(cudaMemset(S.ie_rec.p, 0, S.ie_rec.bytes));
         S.ie_tag = 1;
     }
     if ((rc = S.ie_acc.alloc(size_t(warps) * b->W * 32 * 8))) return rc;
+    b->ie_global_ready = true;
     return INSP_OK;
 }
 
@@ -497,6 +513,7 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
         CU(cudaMemsetAsync(S.ia_done.p, 0, S.ia_done.bytes, s));
         S.ia_epoch = 1;
     }
+    if (!b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
     if (uint64_t(S.ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
         CU(cudaMemsetAsync(S.ie_rec.p, 0, S.ie_rec.bytes, s));
         S.ie_tag = 1;

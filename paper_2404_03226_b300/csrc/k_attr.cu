@@ -21,7 +21,6 @@ namespace insp {
 
 // --------------------------------------------------------- inspiring ability
 constexpr int IA_WARPS = 8;
-constexpr int IA_R = 4;  // words per lane per chunk (4 x 32 x 32 = 4096 ids)
 
 __global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t *counter,
                                                       uint32_t *bits, int64_t slot_words, int32_t *done,
@@ -70,31 +69,33 @@ __global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t 
             }
             __syncwarp();
             __threadfence_block();
+            // Words wlo..NW-1 of the row are needed.  The warp splits into
+            // 32/g groups of g lanes (g = words per chunk, a power of two);
+            // groups OR different successors, then combine by shuffle-xor.
             const int32_t wlo = (v + 1) >> 5;
+            const int32_t span_w = NW - wlo;
+            int32_t g = 32;
+            if (span_w < 32) {
+                g = 1;
+                while (g < span_w) g <<= 1;
+            }
+            const int32_t G = 32 / g, grp = lane / g, wl = lane % g;
             uint32_t *row_v = slot + int64_t(v) * NW;
             int32_t count = 0;
-            for (int32_t cw = wlo; cw < NW; cw += 32 * IA_R) {
-                uint32_t acc[IA_R];
-#pragma unroll
-                for (int r = 0; r < IA_R; ++r) acc[r] = 0;
-                for (int32_t i = 0; i < deg; ++i) {
+            for (int32_t cw = wlo; cw < NW; cw += g) {
+                const int32_t w = cw + wl;
+                uint32_t acc = 0;
+#pragma unroll 4
+                for (int32_t i = grp; i < deg; i += G) {
                     const int32_t s = col[lo + i];
                     const int32_t ws = (s + 1) >> 5;
-                    const uint32_t *row_s = slot + int64_t(s) * NW;
-#pragma unroll
-                    for (int r = 0; r < IA_R; ++r) {
-                        const int32_t w = cw + lane + 32 * r;
-                        if (w >= ws && w < NW) acc[r] |= row_s[w];
-                        if (w == (s >> 5)) acc[r] |= 1u << (s & 31);
-                    }
+                    if (w >= ws && w < NW) acc |= slot[int64_t(s) * NW + w];
+                    if (w == (s >> 5)) acc |= 1u << (s & 31);
                 }
-#pragma unroll
-                for (int r = 0; r < IA_R; ++r) {
-                    const int32_t w = cw + lane + 32 * r;
-                    if (w < NW) {
-                        row_v[w] = acc[r];
-                        count += __popc(acc[r]);
-                    }
+                for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
+                if (grp == 0 && w < NW) {
+                    row_v[w] = acc;
+                    count += __popc(acc);
                 }
             }
             count = __reduce_add_sync(FULL, count);
