@@ -54,7 +54,8 @@ extern "C" {
 /* ---------------------------------------------------------------- policy */
 #define INSP_POLICY_INSPIRIT 0 /* adaptive priority by the Nready controller (default) */
 #define INSP_POLICY_FIFO 1     /* DMDA without priorities: pop in push order (Sec. 2.1) */
-#define INSP_POLICY_LEARNED 2  /* controller runs, but the pop takes the learned scorer's best candidate */
+#define INSP_POLICY_LEARNED 2  /* controller runs, but the pop takes the learned scorer's best candidate
+                                  (highest score, ties to the lowest id); needs insp_set_scorer */
 
 /* Controller parameters of Sec. 4.4 (the paper gives no values).  A zero
  * field takes its default for P = n_cpu + n_gpu workers and the DAG's default
@@ -157,6 +158,55 @@ int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, i
  * batch (INSP_OK or INSP_ETIMEOUT), copied to the host array status[ndag].
  * Synchronises the batch's last stream.  Returns the first non-OK status. */
 int insp_batch_status(insp_batch *b, int32_t *status);
+
+/* ------------------------------------------------ learned proposal scorer
+ * No counterpart in the paper: a small network that can replace the adaptive
+ * priority's pick (INSP_POLICY_LEARNED), trained on rollouts of this
+ * simulator.  All pointers below are device pointers (INSP_EINVAL otherwise).
+ *
+ * insp_scorer_eval: scores of n candidates, feat[n][16] int32 features (each
+ *   clamped to [0, 255]) -> score[n] int64 in units of 1/64, with the scorer
+ *   installed on m; the same tensor-core tile the learned pop uses.
+ *
+ * insp_simulate_rollout: insp_simulate_batch plus rollout controls, each
+ *   optional (NULL): at pop number force_pop[d] (0-based count of pops in DAG
+ *   d) take task force_task[d] if it is queued on the popping worker; at pop
+ *   number feat_pop[d] write the 16 features of up to feat_cap candidates of
+ *   that worker's queue, oldest push first, to feat[d][feat_cap][16], their
+ *   task ids to feat_task[d][feat_cap] and the count to feat_n[d].  The
+ *   features are: bit lengths of IA and IE, min(255 * IE / max(IA, 1), 255),
+ *   bit lengths of the CPU and GPU costs, min(16 * cpu / gpu, 255), worker is a
+ *   GPU, data already local, bit length of the remaining data wait, of Nready,
+ *   of the worker's queue length, the controller mode (0 FIFO, 1 ability,
+ *   2 efficiency, 3 efficiency + locality) and state (0 ascending,
+ *   1 descending), bit lengths of the peak, of the out-degree and of the number
+ *   of pushes since the task was pushed.
+ *
+ * insp_scorer_train_grad: FP32 loss and gradient of an in -> h1 -> h2 -> 1
+ *   network (in <= 32, h1, h2 <= 64; weights w laid out W1[in][h1], b1[h1],
+ *   W2[h1][h2], b2[h2], W3[h2], b3) on n samples x[n][in] with targets[n]:
+ *   loss = mean (y - target)^2.  mode 0: smooth network (h = clamp(z, 0, 255));
+ *   mode 1: quantisation-aware -- the forward pass is the installed-scorer
+ *   network (weights rounded to k/64 with |k| <= 128, h = min(floor(max(z,0)),
+ *   255)) and gradients pass straight through the rounding and the floor.
+ *   work: caller scratch of n * (2*h1 + 2*h2 + 2) floats; grad[nw], loss[1].
+ *   Gradients are reduced over samples in a fixed order (deterministic).
+ *
+ * insp_adamw: one AdamW step (decoupled weight decay), step t >= 1, in place
+ *   on w, m, v with gradient g.
+ *
+ * insp_scorer_quantize: BF16 bit patterns of clamp(round(64 w), -128, 128)/64
+ *   (ties away from zero), ready for insp_set_scorer. */
+int insp_scorer_eval(insp_machine *m, const int32_t *feat, int64_t n, int64_t *score, void *stream);
+int insp_simulate_rollout(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                          int64_t *end, int64_t *makespan, const int32_t *force_pop, const int32_t *force_task,
+                          const int32_t *feat_pop, int32_t feat_cap, int32_t *feat_task, int32_t *feat,
+                          int32_t *feat_n, void *stream);
+int insp_scorer_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                           const float *x, const float *target, float *work, float *grad, float *loss, void *stream);
+int insp_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t t, float lr, float b1, float b2,
+               float eps, float wd, void *stream);
+int insp_scorer_quantize(int64_t nw, const float *w, uint16_t *bf16_out, void *stream);
 
 /* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
  * call on the batch records CUDA events on its stream around each kernel.

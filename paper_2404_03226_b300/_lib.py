@@ -50,6 +50,13 @@ _PROTOS = {
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "insp_batch_set_timing": (ctypes.c_int, [_vp, _i32]),
     "insp_batch_timing": (ctypes.c_int, [_vp, _vp, _vp, _i32]),
+    "insp_scorer_eval": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
+    "insp_simulate_rollout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp,
+                                             _vp, _vp]),
+    "insp_scorer_train_grad": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_adamw": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                  ctypes.c_float, ctypes.c_float, _vp]),
+    "insp_scorer_quantize": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
     "insp_simulate_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _i32, _i64,
                                              ctypes.POINTER(insp_policy), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
@@ -207,3 +214,27 @@ def insp_simulate_noalloc(n, row_ptr, col_idx, type, n_types, type_cost, task_co
                                       ptr(task_cost), n_cpu, n_gpu, xfer_ns,
                                       None if policy is None else ctypes.byref(policy), ptr(ia), ptr(ie),
                                       ptr(worker), ptr(start), ptr(end), ptr(makespan), stream_ptr(stream)))
+
+
+def insp_scorer_eval(m, feat, n, score, stream=None) -> None:
+    check(lib().insp_scorer_eval(m, ptr(feat), n, ptr(score), stream_ptr(stream)))
+
+
+def insp_simulate_rollout(b, ia, ie, worker, start, end, makespan, force_pop=None, force_task=None, feat_pop=None,
+                          feat_cap=0, feat_task=None, feat=None, feat_n=None, stream=None) -> None:
+    check(lib().insp_simulate_rollout(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                                      ptr(force_pop), ptr(force_task), ptr(feat_pop), feat_cap, ptr(feat_task),
+                                      ptr(feat), ptr(feat_n), stream_ptr(stream)))
+
+
+def insp_scorer_train_grad(inp, h1, h2, w, mode, n, x, target, work, grad, loss, stream=None) -> None:
+    check(lib().insp_scorer_train_grad(inp, h1, h2, ptr(w), mode, n, ptr(x), ptr(target), ptr(work), ptr(grad),
+                                       ptr(loss), stream_ptr(stream)))
+
+
+def insp_adamw(nw, w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0, stream=None) -> None:
+    check(lib().insp_adamw(nw, ptr(w), ptr(m), ptr(v), ptr(g), t, lr, b1, b2, eps, wd, stream_ptr(stream)))
+
+
+def insp_scorer_quantize(nw, w, out, stream=None) -> None:
+    check(lib().insp_scorer_quantize(nw, ptr(w), ptr(out), stream_ptr(stream)))

@@ -103,6 +103,7 @@ struct insp_machine {
     int64_t xfer = 0;
     insp_policy pol{};
     bool has_scorer = false;
+    DBuf scorer;  // insp::ScorerPacked in device memory
     std::vector<std::unique_ptr<Scratch>> spare;
 };
 
@@ -308,8 +309,6 @@ INSP_API int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, 
     if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
         p.k_inc_ns < 0)
         return fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");
-    if (p.policy == INSP_POLICY_LEARNED)
-        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer; install one with insp_set_scorer");
     auto *m = new (std::nothrow) insp_machine;
     if (!m) return fail(INSP_ENOMEM, "host allocation");
     m->n_cpu = n_cpu;
@@ -323,8 +322,82 @@ INSP_API int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, 
 INSP_API void insp_machine_destroy(insp_machine *m) { delete m; }
 
 INSP_API int insp_set_scorer(insp_machine *m, const uint16_t *w, size_t nbytes) {
-    (void)m; (void)w; (void)nbytes;
-    return fail(INSP_EINVAL, "learned scorer not available in this build");
+    if (!m || !w) return fail(INSP_EINVAL, "NULL argument");
+    if (nbytes != size_t(insp::MLP_NW) * 2) return fail(INSP_EINVAL, "expected 5313 BF16 weights (10626 bytes)");
+    // every value must be k / 64 with integer |k| <= 128
+    std::vector<float> v(insp::MLP_NW);
+    for (int i = 0; i < insp::MLP_NW; ++i) {
+        uint32_t bits = uint32_t(w[i]) << 16;
+        float f;
+        std::memcpy(&f, &bits, 4);
+        const float k = f * 64.0f;
+        if (!(k >= -128.0f && k <= 128.0f) || k != float(int(k)))
+            return fail(INSP_EINVAL, "weight " + std::to_string(i) + " is not k/64 with |k| <= 128");
+        v[i] = f;
+    }
+    // pack for the tensor-core tile (see mlp.cuh): transposed BF16 rows, FP32 biases
+    insp::ScorerPacked P;
+    std::memset(&P, 0, sizeof(P));
+    const uint16_t *W1 = w, *W2 = w + insp::MLP_IN * insp::MLP_H + insp::MLP_H;
+    const uint16_t *W3 = W2 + insp::MLP_H * insp::MLP_H + insp::MLP_H;
+    const float *B1 = v.data() + insp::MLP_IN * insp::MLP_H;
+    const float *B2 = B1 + insp::MLP_H + insp::MLP_H * insp::MLP_H;
+    const float *B3 = B2 + insp::MLP_H + insp::MLP_H;
+    for (int k = 0; k < insp::MLP_IN; ++k)
+        for (int n = 0; n < insp::MLP_H; ++n) P.w1t[n][k] = W1[k * insp::MLP_H + n];
+    for (int k = 0; k < insp::MLP_H; ++k)
+        for (int n = 0; n < insp::MLP_H; ++n) P.w2t[n][k] = W2[k * insp::MLP_H + n];
+    for (int k = 0; k < insp::MLP_H; ++k) P.w3t[0][k] = W3[k];
+    for (int n = 0; n < insp::MLP_H; ++n) { P.b1[n] = B1[n]; P.b2[n] = B2[n]; }
+    P.b3[0] = P.b3[1] = P.b3[2] = P.b3[3] = B3[0];
+    int rc = m->scorer.alloc(sizeof(P));
+    if (rc) return rc;
+    CU(cudaMemcpy(m->scorer.p, &P, sizeof(P), cudaMemcpyHostToDevice));
+    m->has_scorer = true;
+    return INSP_OK;
+}
+
+INSP_API int insp_scorer_eval(insp_machine *m, const int32_t *feat, int64_t n, int64_t *score, void *stream) {
+    if (!m || n < 0 || (n > 0 && (!feat || !score))) return fail(INSP_EINVAL, "bad argument");
+    if (!m->has_scorer) return fail(INSP_EINVAL, "no scorer installed (insp_set_scorer)");
+    if (n > 0 && (!is_device_ptr(feat) || !is_device_ptr(score))) return fail(INSP_EINVAL, "device pointers required");
+    if (n == 0) return INSP_OK;
+    insp::launch_scorer_eval(m->scorer.as<insp::ScorerPacked>(), feat, n, score, static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
+INSP_API int insp_scorer_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                                    const float *x, const float *target, float *work, float *grad, float *loss,
+                                    void *stream) {
+    if (in < 1 || in > 32 || h1 < 1 || h1 > 64 || h2 < 1 || h2 > 64 || n < 1 || (mode != 0 && mode != 1))
+        return fail(INSP_EINVAL, "need 1 <= in <= 32, 1 <= h1, h2 <= 64, n >= 1, mode 0 or 1");
+    const void *ptrs[] = {w, x, target, work, grad, loss};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    insp::launch_mlp_train_grad(in, h1, h2, w, mode, n, x, target, work, grad, loss,
+                                static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
+INSP_API int insp_adamw(int64_t nw, float *w, float *m_, float *v, const float *g, int32_t t, float lr, float b1,
+                        float b2, float eps, float wd, void *stream) {
+    if (nw < 1 || t < 1) return fail(INSP_EINVAL, "need nw >= 1 and step t >= 1");
+    const void *ptrs[] = {w, m_, v, g};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    insp::launch_adamw(nw, w, m_, v, g, t, lr, b1, b2, eps, wd, static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
+INSP_API int insp_scorer_quantize(int64_t nw, const float *w, uint16_t *bf16_out, void *stream) {
+    if (nw < 1) return fail(INSP_EINVAL, "need nw >= 1");
+    if (!is_device_ptr(w) || !is_device_ptr(bf16_out)) return fail(INSP_EINVAL, "device pointers required");
+    insp::launch_quantize(nw, w, bf16_out, static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return INSP_OK;
 }
 
 INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *task_base, const int64_t *edge_base,
@@ -551,9 +624,18 @@ INSP_API int insp_attributes(insp_dag *d, int64_t unit_time_ns, int32_t *ia, int
 
 namespace {
 
+struct Rollout {
+    const int32_t *force_pop = nullptr, *force_task = nullptr, *feat_pop = nullptr;
+    int32_t feat_cap = 0;
+    int32_t *feat_task = nullptr, *feat = nullptr, *feat_n = nullptr;
+};
+
 int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
-                  int64_t *end, int64_t *makespan, void *stream, bool per_dag) {
+                  int64_t *end, int64_t *makespan, void *stream, bool per_dag, const Rollout &ro = Rollout()) {
     if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
+    const bool learned = b->mach.pol.policy == INSP_POLICY_LEARNED;
+    if (learned && !(b->owner && b->owner->has_scorer))
+        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     b->last_stream = s;
     const int64_t N = b->n_total;
@@ -603,6 +685,14 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         A.nl = S.nl.as<int32_t>();
         A.order = b->order.as<int32_t>();
         A.counter = b->counters.as<int32_t>() + 8;
+        A.scorer = learned ? b->owner->scorer.as<insp::ScorerPacked>() : nullptr;
+        A.force_pop = ro.force_pop;
+        A.force_task = ro.force_task;
+        A.feat_pop = ro.feat_pop;
+        A.feat_cap = ro.feat_cap;
+        A.feat_task = ro.feat_task;
+        A.feat = ro.feat;
+        A.feat_n = ro.feat_n;
         if (per_dag) {
             for (int d = 0; d < b->ndag; ++d) {
                 A.single_dag = d;
@@ -612,7 +702,14 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         } else {
             A.single_dag = -1;
             TimedLaunch tl(b, TK_SIM, s);
-            insp::launch_sim(A, b->grid_sim, s);
+            int grid = b->grid_sim;
+            if (learned) {
+                DeviceInfo di;
+                if ((rc = device_info(di))) return rc;
+                const int occ = std::max(1, insp::sim_learned_occupancy());
+                grid = std::max(1, std::min(di.sms * occ, (b->ndag + insp::sim_warps() - 1) / insp::sim_warps()));
+            }
+            insp::launch_sim(A, grid, s);
         }
         CU(cudaGetLastError());
     }
@@ -638,6 +735,30 @@ INSP_API int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t
 INSP_API int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
                            int64_t *end, int64_t *makespan, void *stream) {
     return simulate_impl(d, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_simulate_rollout(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
+                                   int64_t *start, int64_t *end, int64_t *makespan, const int32_t *force_pop,
+                                   const int32_t *force_task, const int32_t *feat_pop, int32_t feat_cap,
+                                   int32_t *feat_task, int32_t *feat, int32_t *feat_n, void *stream) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    if ((force_pop == nullptr) != (force_task == nullptr)) return fail(INSP_EINVAL, "force_pop and force_task go together");
+    if (feat_pop && (feat_cap < 1 || !feat_task || !feat || !feat_n)) return fail(INSP_EINVAL, "feature capture needs outputs");
+    const void *ptrs[] = {ia, ie, worker, start, end, makespan};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    const void *opt[] = {force_pop, force_task, feat_pop, feat_task, feat, feat_n};
+    for (const void *q : opt)
+        if (q && !is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    Rollout ro;
+    ro.force_pop = force_pop;
+    ro.force_task = force_task;
+    ro.feat_pop = feat_pop;
+    ro.feat_cap = feat_pop ? feat_cap : 0;
+    ro.feat_task = feat_task;
+    ro.feat = feat;
+    ro.feat_n = feat_n;
+    return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false, ro);
 }
 
 INSP_API int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,

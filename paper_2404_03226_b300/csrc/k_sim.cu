@@ -115,11 +115,58 @@ __device__ __forceinline__ void ctrl_step(Ctrl &S, int64_t cur, int64_t now, int
 
 __device__ __forceinline__ int32_t node_of(int32_t w, int32_t n_cpu) { return w < n_cpu ? 0 : 1 + (w - n_cpu); }
 
+__device__ __forceinline__ int32_t bitlen64(int64_t x) { return x > 0 ? 64 - __clzll(x) : 0; }
+__device__ __forceinline__ int32_t clamp255(int64_t x) { return x < 0 ? 0 : (x > 255 ? 255 : int32_t(x)); }
+
+// The 16 integer features of a candidate at a pop (all in [0, 255]): inspiring
+// ability and efficiency (bit lengths and their ratio), CPU / GPU costs (bit
+// lengths and ratio), whether the popping worker is a GPU, data locality and
+// remaining wait, Nready, the worker's queue length, the controller's mode,
+// state and peak, the out-degree and the number of pushes since the task was
+// pushed.
+__device__ __forceinline__ void cand_features(int32_t *f, int32_t ia, int32_t ie, int64_t ccpu, int64_t cgpu,
+                                              int32_t is_gpu, int64_t dr, int64_t now, int64_t nready, int64_t qlen,
+                                              int32_t mode, int32_t state, int64_t peak, int32_t outdeg,
+                                              int64_t age) {
+    f[0] = clamp255(bitlen64(ia));
+    f[1] = clamp255(bitlen64(ie));
+    f[2] = clamp255(int64_t(ie) * 255 / (ia > 1 ? ia : 1));
+    f[3] = clamp255(bitlen64(ccpu));
+    f[4] = clamp255(bitlen64(cgpu));
+    f[5] = clamp255(16 * ccpu / cgpu);
+    f[6] = is_gpu;
+    f[7] = dr <= now;
+    f[8] = clamp255(bitlen64(dr > now ? dr - now : 0));
+    f[9] = clamp255(bitlen64(nready));
+    f[10] = clamp255(bitlen64(qlen));
+    f[11] = mode;
+    f[12] = state;
+    f[13] = clamp255(bitlen64(peak));
+    f[14] = clamp255(bitlen64(outdeg));
+    f[15] = clamp255(bitlen64(age));
+}
+
+// Per-warp shared memory of the learned pop: 32 candidate rows of 16 BF16
+// features and their pool indices.
+struct LearnSmem {
+    uint32_t tile[32 * 8];
+    int32_t cidx[32];
+};
+
+template <bool LEARNED>
 __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     __shared__ WarpSmem smem_all[SIM_WARPS];
+    extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WarpSmem *sm = &smem_all[wib];
+    ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn);
+    LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn + sizeof(ScorerPacked)) + wib;
+    if (LEARNED) {
+        for (int i = threadIdx.x; i < int(sizeof(ScorerPacked) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t *>(SP)[i] = reinterpret_cast<const uint32_t *>(A.scorer)[i];
+        __syncthreads();
+    }
     const DevBatch &B = A.B;
     const int32_t P = A.n_cpu + A.n_gpu, n_cpu = A.n_cpu;
     const int64_t xfer = A.xfer;
@@ -176,7 +223,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         const int32_t w0 = lane, w1 = lane + 32;
         int64_t busy0 = 0, busy1 = 0, qc0 = 0, qc1 = 0;
         int32_t run0 = -1, run1 = -1, qn0 = 0, qn1 = 0;
-        int32_t nready = 0, seq = 0, done = 0;
+        int32_t nready = 0, seq = 0, done = 0, npop = 0;
         int64_t now = 0;
         Ctrl ctl{0, 0, 0, 0, MODE_FIFO, ST_INC};
 
@@ -215,7 +262,14 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             __syncwarp();
         };
 
-        // pop(w): controller judgement, then argmax of the mode's key over w's entries.
+        // features of pool entry i as a candidate of worker w at this pop
+        auto features_of = [&](int32_t i, int32_t w, int64_t cur, int32_t qlen, int32_t *f) {
+            const int32_t t = pool.idw(i) & 0xffffff;
+            cand_features(f, pool.ia(i), pool.ie(i), cost_of(t, 0), cost_of(t, 1), w >= n_cpu, pool.dr(i), now, cur,
+                          qlen, ctl.mode, ctl.state, ctl.peak, rp[t + 1] - rp[t], int64_t(seq) - pool.seq(i));
+        };
+
+        // pop(w): controller judgement, then the pick (forced / learned / mode key).
         // Returns false (no fault) if w has no entry, which would be a bookkeeping error.
         auto pop = [&](int32_t w) -> bool {
             const int64_t cur = nready;
@@ -224,24 +278,102 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 ctrl_step(ctl, cur, now, tw, s_inc, s_dec, dec_step, cslack, kt, kns);
                 mode = ctl.mode;
             }
+            const int32_t qlen = __shfl_sync(FULL, w >= 32 ? qn1 : qn0, w & 31);
+            // rollouts: candidate features in push order
+            if (A.feat_pop != nullptr && npop == A.feat_pop[d]) {
+                int32_t last = -1, nd = 0;
+                for (int k = 0; k < A.feat_cap; ++k) {
+                    int32_t ms = 0x7fffffff, mi = -1;
+                    for (int32_t i = lane; i < nready; i += 32) {
+                        if ((pool.idw(i) >> 24) != w) continue;
+                        const int32_t sq = pool.seq(i);
+                        if (sq > last && sq < ms) { ms = sq; mi = i; }
+                    }
+                    const int32_t wm = int32_t(__reduce_min_sync(FULL, uint32_t(ms)));
+                    if (wm == 0x7fffffff) break;
+                    const uint32_t ol = __ballot_sync(FULL, ms == wm && mi >= 0);
+                    const int32_t i = __shfl_sync(FULL, mi, __ffs(ol) - 1);
+                    if (lane == 0) {
+                        int32_t f[16];
+                        features_of(i, w, cur, qlen, f);
+                        int32_t *o = A.feat + (int64_t(d) * A.feat_cap + k) * 16;
+                        for (int q = 0; q < 16; ++q) o[q] = f[q];
+                        A.feat_task[int64_t(d) * A.feat_cap + k] = pool.idw(i) & 0xffffff;
+                    }
+                    last = wm;
+                    nd += 1;
+                }
+                if (lane == 0) A.feat_n[d] = nd;
+                __syncwarp();
+            }
             uint64_t best = 0;
             int32_t bi = -1;
-            for (int32_t i = lane; i < nready; i += 32) {
-                const int32_t e = pool.idw(i);
-                if ((e >> 24) != w) continue;
-                const uint32_t id = uint32_t(e & 0xffffff);
-                uint64_t key;
-                if (mode == MODE_FIFO) {
-                    key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.seq(i)));
-                } else {
-                    const uint64_t tie_lo = uint64_t(0x7fffffffu - id);
-                    uint64_t hi_part;
-                    if (mode == MODE_ABILITY) hi_part = uint64_t(uint32_t(pool.ia(i))) << 31;
-                    else if (mode == MODE_EFI) hi_part = uint64_t(uint32_t(pool.ie(i))) << 31;
-                    else hi_part = (uint64_t(pool.dr(i) <= now) << 62) | (uint64_t(uint32_t(pool.ie(i))) << 31);
-                    key = (1ull << 63) | hi_part | tie_lo;
+            const bool forcing = A.force_pop != nullptr && npop == A.force_pop[d];
+            if (forcing) {
+                const int32_t ft = A.force_task[d];
+                for (int32_t i = lane; i < nready; i += 32) {
+                    const int32_t e = pool.idw(i);
+                    if ((e >> 24) == w && (e & 0xffffff) == ft) { best = 1; bi = i; }
                 }
-                if (key > best) { best = key; bi = i; }
+            }
+            if (__ballot_sync(FULL, bi >= 0) == 0) {
+                if (LEARNED) {
+                    // score w's candidates 32 at a time on the tensor cores
+                    for (int32_t base = 0; base < nready; base += 32) {
+                        const int32_t i = base + lane;
+                        const bool match = i < nready && (pool.idw(i) >> 24) == w;
+                        const uint32_t mm = __ballot_sync(FULL, match);
+                        if (!mm) continue;
+                        if (match) {
+                            const int r = __popc(mm & ((1u << lane) - 1));
+                            int32_t f[16];
+                            features_of(i, w, cur, qlen, f);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) LS->tile[r * 8 + c] = pack_bf16x2(float(f[2 * c]), float(f[2 * c + 1]));
+                            LS->cidx[r] = i;
+                        }
+                        __syncwarp();
+                        const int nc = __popc(mm);
+                        for (int mt = 0; mt < nc; mt += 16) {
+                            float s0, s1;
+                            mlp_score_tile(SP, LS->tile + mt * 8, lane, s0, s1);
+                            if ((lane & 3) == 0) {
+                                const int r0 = mt + (lane >> 2), r1 = r0 + 8;
+                                if (r0 < nc) {
+                                    const int32_t pi = LS->cidx[r0];
+                                    const uint64_t key = (1ull << 63) | (uint64_t(int64_t(s0 * 64.0f) + 0x80000000LL) << 31) |
+                                                         uint64_t(0x7fffffffu - uint32_t(pool.idw(pi) & 0xffffff));
+                                    if (key > best) { best = key; bi = pi; }
+                                }
+                                if (r1 < nc) {
+                                    const int32_t pi = LS->cidx[r1];
+                                    const uint64_t key = (1ull << 63) | (uint64_t(int64_t(s1 * 64.0f) + 0x80000000LL) << 31) |
+                                                         uint64_t(0x7fffffffu - uint32_t(pool.idw(pi) & 0xffffff));
+                                    if (key > best) { best = key; bi = pi; }
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                } else {
+                    for (int32_t i = lane; i < nready; i += 32) {
+                        const int32_t e = pool.idw(i);
+                        if ((e >> 24) != w) continue;
+                        const uint32_t id = uint32_t(e & 0xffffff);
+                        uint64_t key;
+                        if (mode == MODE_FIFO) {
+                            key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.seq(i)));
+                        } else {
+                            const uint64_t tie_lo = uint64_t(0x7fffffffu - id);
+                            uint64_t hi_part;
+                            if (mode == MODE_ABILITY) hi_part = uint64_t(uint32_t(pool.ia(i))) << 31;
+                            else if (mode == MODE_EFI) hi_part = uint64_t(uint32_t(pool.ie(i))) << 31;
+                            else hi_part = (uint64_t(pool.dr(i) <= now) << 62) | (uint64_t(uint32_t(pool.ie(i))) << 31);
+                            key = (1ull << 63) | hi_part | tie_lo;
+                        }
+                        if (key > best) { best = key; bi = i; }
+                    }
+                }
             }
             const uint64_t wbest = warp_max_u64(best);
             const uint32_t wl = __ballot_sync(FULL, best == wbest && bi >= 0);
@@ -254,6 +386,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             const int32_t last = nready - 1;
             if (idx != last) pool.move(last, idx, lane);
             nready -= 1;
+            npop += 1;
             const int64_t s = max(now, dr), e = s + c;
             if (lane == (w & 31)) {
                 if (w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; }
@@ -379,16 +512,37 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     }
 }
 
+constexpr size_t LEARN_SMEM = sizeof(ScorerPacked) + SIM_WARPS * sizeof(LearnSmem);
+
 void launch_sim(const SimArgs &A, int grid, cudaStream_t s) {
-    k_sim<<<grid, SIM_WARPS * 32, 0, s>>>(A);
+    if (A.policy == INSP_POLICY_LEARNED) {
+        cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+        k_sim<true><<<grid, SIM_WARPS * 32, LEARN_SMEM, s>>>(A);
+    } else {
+        k_sim<false><<<grid, SIM_WARPS * 32, 0, s>>>(A);
+    }
 }
 // The unbatched form: one launch, one warp, one DAG.
-void launch_sim_single(const SimArgs &A, cudaStream_t s) { k_sim<<<1, 32, 0, s>>>(A); }
+void launch_sim_single(const SimArgs &A, cudaStream_t s) {
+    if (A.policy == INSP_POLICY_LEARNED) {
+        cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+        k_sim<true><<<1, 32, LEARN_SMEM, s>>>(A);
+    } else {
+        k_sim<false><<<1, 32, 0, s>>>(A);
+    }
+}
 int sim_threads() { return SIM_WARPS * 32; }
 int sim_warps() { return SIM_WARPS; }
 int sim_occupancy() {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim, SIM_WARPS * 32, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<false>, SIM_WARPS * 32, 0) != cudaSuccess) return 0;
+    return nb;
+}
+int sim_learned_occupancy() {
+    int nb = 0;
+    cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<true>, SIM_WARPS * 32, LEARN_SMEM) != cudaSuccess)
+        return 0;
     return nb;
 }
 

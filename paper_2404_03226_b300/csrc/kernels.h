@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace insp {
 
@@ -29,6 +30,14 @@ struct SimArgs {
     const int32_t *order;  // DAGs by descending size
     int32_t *counter;
     int32_t single_dag;    // >= 0: only that DAG, one warp
+    // learned scorer (policy INSP_POLICY_LEARNED)
+    const ScorerPacked *scorer;
+    // rollouts: per DAG, at pop number force_pop[d] take task force_task[d] if it is
+    // in the popping worker's queue; at pop number feat_pop[d] record the features
+    // of up to feat_cap candidates of that queue in push order
+    const int32_t *force_pop, *force_task, *feat_pop;
+    int32_t feat_cap;
+    int32_t *feat_task, *feat, *feat_n;
 };
 
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
@@ -39,7 +48,16 @@ void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
                uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s);
+// learned scorer (k_mlp.cu)
+void launch_scorer_eval(const ScorerPacked *P, const int32_t *feat, int64_t n, int64_t *score, cudaStream_t s);
+void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                           const float *x, const float *target, float *work, float *grad, float *loss,
+                           cudaStream_t s);
+void launch_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t t, float lr, float b1, float b2,
+                  float eps, float wd, cudaStream_t s);
+void launch_quantize(int64_t nw, const float *w, uint16_t *out, cudaStream_t s);
 void launch_sim(const SimArgs &A, int grid, cudaStream_t s);
+int sim_learned_occupancy();
 void launch_sim_single(const SimArgs &A, cudaStream_t s);
 int ia_threads();
 int ie_threads();

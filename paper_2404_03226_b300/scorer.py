@@ -1,0 +1,168 @@
+"""Training driver of the learned proposal scorer (no counterpart in the paper).
+
+Rollouts come from the simulator itself (insp_simulate_rollout): for every
+training DAG a decision point (a pop) is drawn, the candidates of the popping
+worker's queue are recorded with their 16 features, and the run is repeated
+once per candidate with that candidate forced at the decision point.  A
+candidate's target is the relative makespan gain, in percent, of forcing it
+over the plain INSPIRIT run.  The MLP 16 -> 64 -> 64 -> 1 is trained on the
+GPU by the library's kernels (insp_scorer_train_grad in quantisation-aware
+mode, insp_adamw), then rounded to the BF16 grid (insp_scorer_quantize) and
+installed with insp_set_scorer.  The plain INSPIRIT priority stays the
+fallback: the learned policy is used only if its mean makespan on a
+validation split is no worse.
+
+torch is used for device buffers only; numpy only assembles labels.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+
+IN, H = 16, 64
+NW = IN * H + H + H * H + H + H + 1
+CAP = 8
+
+
+def _policy(kind: int) -> _lib.insp_policy:
+    p = _lib.insp_policy()
+    p.policy = kind
+    return p
+
+
+@dataclass
+class Rollouts:
+    feat: np.ndarray     # [N, 16] int32
+    target: np.ndarray   # [N] float32, % makespan gain of forcing the candidate
+    dag: np.ndarray      # [N] index of the DAG the row came from
+
+
+def collect_rollouts(batch, machine, seed: int, cap: int = CAP) -> Rollouts:
+    """One decision point per DAG of `batch` (an inputs.Batch-like object)."""
+    import torch
+    from . import DagBatch, Machine
+    M = Machine(machine.n_cpu, machine.n_gpu, machine.xfer_ns, _policy(_lib.INSP_POLICY_INSPIRIT))
+    B = DagBatch(M, batch)
+    nd, n = B.ndag, B.n_tasks
+    dev = torch.device("cuda")
+    ia, ie = B.attributes()
+    sizes = np.diff(np.asarray(batch.task_base))
+    rng = np.random.default_rng(seed)
+    pop = np.floor(rng.random(nd) * np.maximum(sizes, 1)).astype(np.int32)
+    d_pop = torch.from_numpy(pop).to(dev)
+    worker = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+    start = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    end = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+    mk0 = torch.empty(nd, dtype=torch.int64, device=dev)
+    ftask = torch.full((nd, cap), -1, dtype=torch.int32, device=dev)
+    feat = torch.zeros((nd, cap, IN), dtype=torch.int32, device=dev)
+    fn = torch.zeros(nd, dtype=torch.int32, device=dev)
+    _lib.insp_simulate_rollout(B.handle, ia, ie, worker, start, end, mk0, None, None, d_pop, cap, ftask, feat, fn)
+    mks = []
+    for r in range(cap):
+        mk = torch.empty(nd, dtype=torch.int64, device=dev)
+        force_task = ftask[:, r].contiguous()
+        _lib.insp_simulate_rollout(B.handle, ia, ie, worker, start, end, mk, d_pop, force_task)
+        mks.append(mk)
+    torch.cuda.synchronize()
+    if _lib.insp_batch_status(B.handle) != 0:
+        raise RuntimeError("rollout simulation failed: " + _lib.last_error())
+    mk0 = mk0.cpu().numpy().astype(np.float64)
+    fn = fn.cpu().numpy()
+    feat = feat.cpu().numpy()
+    mk = np.stack([m.cpu().numpy() for m in mks], 1).astype(np.float64)
+    rows_f, rows_t, rows_d = [], [], []
+    for d in np.nonzero(fn >= 2)[0]:
+        k = int(fn[d])
+        rows_f.append(feat[d, :k])
+        rows_t.append((mk0[d] - mk[d, :k]) / mk0[d] * 100.0)
+        rows_d.append(np.full(k, d))
+    if not rows_f:
+        return Rollouts(np.zeros((0, IN), np.int32), np.zeros(0, np.float32), np.zeros(0, np.int64))
+    return Rollouts(np.concatenate(rows_f).astype(np.int32), np.concatenate(rows_t).astype(np.float32),
+                    np.concatenate(rows_d))
+
+
+def init_weights(seed: int) -> np.ndarray:
+    """Small random weights with positive biases (floor activations need
+    positive pre-activations to pass gradients)."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(NW, np.float32)
+    o = 0
+    w[o:o + IN * H] = rng.normal(0, 0.08, IN * H); o += IN * H
+    w[o:o + H] = 2.0; o += H
+    w[o:o + H * H] = rng.normal(0, 0.06, H * H); o += H * H
+    w[o:o + H] = 2.0; o += H
+    w[o:o + H] = rng.normal(0, 0.05, H); o += H
+    w[o] = 0.0
+    return w
+
+
+def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3, seed: int = 0,
+          w0: np.ndarray | None = None, log=None):
+    """Quantisation-aware training on the GPU; returns (fp32 master weights,
+    BF16 grid weights as uint16, per-epoch mean loss)."""
+    import torch
+    dev = torch.device("cuda")
+    n = len(roll.target)
+    x = torch.from_numpy(roll.feat.astype(np.float32)).to(dev)
+    y = torch.from_numpy(roll.target.astype(np.float32)).to(dev)
+    w = torch.from_numpy(init_weights(seed) if w0 is None else w0.astype(np.float32)).to(dev)
+    m = torch.zeros_like(w)
+    v = torch.zeros_like(w)
+    g = torch.zeros_like(w)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    bs = min(batch, n)
+    work = torch.empty(bs * (2 * H + 2 * H + 2), dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(seed + 1)
+    t = 0
+    hist = []
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).to(dev)
+        losses = []
+        for s0 in range(0, n - bs + 1, bs):
+            idx = perm[s0:s0 + bs]
+            xb = x[idx].contiguous()
+            yb = y[idx].contiguous()
+            _lib.insp_scorer_train_grad(IN, H, H, w, 1, bs, xb, yb, work, g, loss)
+            t += 1
+            _lib.insp_adamw(NW, w, m, v, g, t, lr)
+            losses.append(loss)
+        ep_loss = float(torch.stack(losses).mean()) if losses else float("nan")
+        hist.append(ep_loss)
+        if log:
+            log(f"epoch {ep}: loss {ep_loss:.4f}")
+    q = torch.empty(NW, dtype=torch.int16, device=dev)
+    _lib.insp_scorer_quantize(NW, w, q)
+    torch.cuda.synchronize()
+    return w.cpu().numpy(), q.cpu().numpy().view(np.uint16), hist
+
+
+def evaluate(batch, machine, bf16_weights) -> dict:
+    """Mean makespan of the plain INSPIRIT priority and of the learned scorer
+    on `batch`; the policy to ship is the learned one only if it is no worse."""
+    import torch
+    from . import DagBatch, Machine
+    res = {}
+    for name, kind in (("inspirit", _lib.INSP_POLICY_INSPIRIT), ("learned", _lib.INSP_POLICY_LEARNED)):
+        M = Machine(machine.n_cpu, machine.n_gpu, machine.xfer_ns, _policy(kind))
+        if kind == _lib.INSP_POLICY_LEARNED:
+            _lib.insp_set_scorer(M.handle, np.ascontiguousarray(bf16_weights, np.uint16))
+        B = DagBatch(M, batch)
+        ia, ie = B.attributes()
+        s = B.simulate(ia, ie)
+        torch.cuda.synchronize()
+        if _lib.insp_batch_status(B.handle) != 0:
+            raise RuntimeError(_lib.last_error())
+        res[name] = s.makespan.cpu().numpy()
+    mean_plain = float(res["inspirit"].mean())
+    mean_learned = float(res["learned"].mean())
+    return {"mean_makespan_inspirit": mean_plain, "mean_makespan_learned": mean_learned,
+            "gain_pct": (mean_plain - mean_learned) / mean_plain * 100.0,
+            "wins": int((res["learned"] < res["inspirit"]).sum()),
+            "losses": int((res["learned"] > res["inspirit"]).sum()),
+            "policy": "learned" if mean_learned <= mean_plain else "inspirit (fallback)",
+            "makespan_inspirit": res["inspirit"], "makespan_learned": res["learned"]}
