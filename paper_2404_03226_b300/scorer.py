@@ -5,7 +5,9 @@ training DAG a decision point (a pop) is drawn, the candidates of the popping
 worker's queue are recorded with their 16 features, and the run is repeated
 once per candidate with that candidate forced at the decision point.  A
 candidate's target is the relative makespan gain, in percent, of forcing it
-over the plain INSPIRIT run.  The MLP 16 -> 64 -> 64 -> 1 is trained on the
+over the plain INSPIRIT run, centred on the mean over that decision's
+candidates (the scorer ranks candidates of one pop, so only their relative
+gains matter).  The MLP 16 -> 64 -> 64 -> 1 is trained on the
 GPU by the library's kernels (insp_scorer_train_grad in quantisation-aware
 mode, insp_adamw), then rounded to the BF16 grid (insp_scorer_quantize) and
 installed with insp_set_scorer.  The plain INSPIRIT priority stays the
@@ -77,8 +79,9 @@ def collect_rollouts(batch, machine, seed: int, cap: int = CAP) -> Rollouts:
     rows_f, rows_t, rows_d = [], [], []
     for d in np.nonzero(fn >= 2)[0]:
         k = int(fn[d])
+        gain = (mk0[d] - mk[d, :k]) / mk0[d] * 100.0
         rows_f.append(feat[d, :k])
-        rows_t.append((mk0[d] - mk[d, :k]) / mk0[d] * 100.0)
+        rows_t.append(gain - gain.mean())
         rows_d.append(np.full(k, d))
     if not rows_f:
         return Rollouts(np.zeros((0, IN), np.int32), np.zeros(0, np.float32), np.zeros(0, np.int64))
@@ -166,3 +169,76 @@ def evaluate(batch, machine, bf16_weights) -> dict:
             "losses": int((res["learned"] > res["inspirit"]).sum()),
             "policy": "learned" if mean_learned <= mean_plain else "inspirit (fallback)",
             "makespan_inspirit": res["inspirit"], "makespan_learned": res["learned"]}
+
+
+TRAINED = __import__("os").path.join(__import__("os").path.dirname(__file__), "scorer_k.txt")
+
+
+def load_trained(path: str = TRAINED) -> tuple[np.ndarray, str]:
+    """(BF16 bit patterns, shipped policy) of the scorer trained by main()."""
+    policy = "learned"
+    with open(path) as f:
+        for line in f:
+            if line.startswith("# policy shipped:"):
+                policy = line.split(":", 1)[1].strip()
+            elif line.strip() and not line.startswith("#"):
+                k = np.array([int(t) for t in line.split()], np.int64)
+    f32 = (k.astype(np.float64) / 64.0).astype(np.float32)
+    return (f32.view(np.uint32) >> 16).astype(np.uint16), policy
+
+
+def main(argv=None) -> None:
+    """Train on rollouts of layered DAGs and evaluate on held-out ones:
+    python -m paper_2404_03226_b300.scorer --train 100000 --eval 4096 --out FILE"""
+    import argparse
+    import json
+    import sys
+    import time
+    import os
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import inputs  # seeded workload generators (repository root)
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=100000)
+    ap.add_argument("--val", type=int, default=2048)
+    ap.add_argument("--eval", type=int, default=4096)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--chunk", type=int, default=8192)
+    ap.add_argument("--decisions", type=int, default=4, help="decision points drawn per training DAG")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--lr", type=float, default=5e-4)
+    ap.add_argument("--out", default="")
+    a = ap.parse_args(argv)
+    m = inputs.MACHINE_LAYERED
+    t0 = time.time()
+    parts = []
+    for first in range(0, a.train, a.chunk):
+        b = inputs.layered(min(a.chunk, a.train - first), cfg=4, first=first)
+        for r in range(a.decisions):
+            parts.append(collect_rollouts(b, m, seed=(a.seed + first) * 16 + r))
+    roll = Rollouts(np.concatenate([p.feat for p in parts]), np.concatenate([p.target for p in parts]),
+                    np.concatenate([p.dag for p in parts]))
+    t1 = time.time()
+    w, q, hist = train(roll, epochs=a.epochs, lr=a.lr, seed=a.seed, log=lambda s: print(s, file=sys.stderr))
+    t2 = time.time()
+    val = evaluate(inputs.layered(a.val, cfg=4, first=1 << 19), m, q)       # seed set A, not trained on
+    held = evaluate(inputs.layered(a.eval, cfg=4, first=1 << 20), m, q)     # seed set B
+    use = "learned" if val["mean_makespan_learned"] <= val["mean_makespan_inspirit"] else "inspirit (fallback)"
+    rep = {"train_dags": a.train, "rollout_rows": int(len(roll.target)), "epochs": a.epochs,
+           "loss_first": hist[0], "loss_last": hist[-1], "rollout_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 1),
+           "validation": {k: v for k, v in val.items() if not k.startswith("makespan_")},
+           "policy_shipped": use,
+           "held_out": {k: v for k, v in held.items() if not k.startswith("makespan_")},
+           "held_out_gain_pct_of_shipped": held["gain_pct"] if use == "learned" else 0.0}
+    print(json.dumps(rep))
+    if a.out:
+        k = np.round((q.astype(np.uint32) << 16).view(np.float32) * 64).astype(np.int64)
+        with open(a.out, "w") as f:
+            f.write("# learned scorer, grid numerators k (weight = k/64), layout W1[16][64] b1 W2[64][64] b2 W3[64] b3\n")
+            f.write(f"# python -m paper_2404_03226_b300.scorer --train {a.train} --val {a.val} --eval {a.eval} "
+                    f"--epochs {a.epochs} --decisions {a.decisions} --lr {a.lr} --seed {a.seed}\n")
+            f.write(f"# policy shipped: {use}\n")
+            f.write(" ".join(str(int(x)) for x in k) + "\n")
+
+
+if __name__ == "__main__":
+    main()

@@ -200,3 +200,20 @@ def test_small_training_run_and_fallback():
     res = scorer.evaluate(held, m, q)
     chosen = res["mean_makespan_learned"] if res["policy"] == "learned" else res["mean_makespan_inspirit"]
     assert chosen <= res["mean_makespan_inspirit"]
+
+
+def test_shipped_scorer_on_held_out_dags():
+    """The trained scorer shipped with the library (layered workload, 100k
+    training DAGs) against plain INSPIRIT on the 4096 held-out DAGs: when the
+    learned policy is shipped it must not lose on average; otherwise the plain
+    priority is the fallback."""
+    from paper_2404_03226_b300 import scorer
+    bits, shipped = scorer.load_trained()
+    held = inputs.layered(4096, cfg=4, first=1 << 20)
+    res = scorer.evaluate(held, inputs.MACHINE_LAYERED, bits)
+    print(f"held-out gain of the learned scorer: {res['gain_pct']:.3f}% "
+          f"(wins {res['wins']}, losses {res['losses']}), shipped: {shipped}")
+    if shipped == "learned":
+        assert res["mean_makespan_learned"] <= res["mean_makespan_inspirit"]
+    else:
+        assert shipped.startswith("inspirit")
