@@ -118,6 +118,10 @@ struct insp_batch {
     std::vector<int64_t> h_task_base, h_edge_base;
     DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
+    DBuf pr_ptr, pcol;      // predecessor lists (pull form of the efficiency sweep)
+    int grid_ie_pull = 0;   // > 0: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
+    DBuf ie_ring;           // per-warp rings of the pull sweep (global, L2-resident)
+    DBuf item_dag;          // DAG of every 32-source work item
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;
@@ -204,9 +208,10 @@ int alloc_scratch(insp_batch *b) {
         CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
         S.ia_epoch = 0;
     }
-    // inspiring efficiency: window sweep scratch
+    // inspiring efficiency: global-memory sweep scratch unless the pull form applies
+    // (allocated later if a call needs the global form)
     b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
-    return alloc_ie_global(b);
+    return b->grid_ie_pull > 0 ? INSP_OK : alloc_ie_global(b);
 }
 
 // Scratch of the global-memory inspiring-efficiency sweep: per warp one record
@@ -498,9 +503,38 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     std::vector<int64_t> items(ndag + 1, 0);
     for (int d = 0; d < ndag; ++d) items[d + 1] = items[d] + (b->h_task_base[d + 1] - b->h_task_base[d] + 31) / 32;
     b->n_items = items[ndag];
+    std::vector<int32_t> idag(std::max<int64_t>(b->n_items, 1));
+    for (int d = 0; d < ndag; ++d)
+        for (int64_t k = items[d]; k < items[d + 1]; ++k) idag[k] = d;
     if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4)) ||
-        (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)))
+        (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)) ||
+        (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)))
         return bail(rc);
+    // pull form of the efficiency sweep when its window ring fits shared memory
+    if (b->W <= insp::IE_PULL_MAX_W && ndag > 0) {
+        const int occ = insp::ie_pull_occupancy();
+        if (occ > 0) {
+            DBuf cursor;
+            if ((rc = b->pr_ptr.alloc((b->n_total + ndag) * 4)) || (rc = b->pcol.alloc(std::max<int64_t>(b->m_total, 1) * 4)) ||
+                (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
+                return bail(rc);
+            insp::launch_reverse_csr(B, b->indeg0.as<int32_t>(), b->pr_ptr.as<int32_t>(), cursor.as<int32_t>(),
+                                     b->pcol.as<int32_t>(), grid, 0);
+            if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
+                return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
+            // rings of all warps stay L2-resident: ~64 MB of rings at most
+            const int wpc = insp::ie_pull_warps();
+            const int64_t ring = insp::ie_pull_ring_bytes(b->W);
+            const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(64) << 20) / (ring * wpc));
+            b->grid_ie_pull = int(std::max<int64_t>(
+                1, std::min({int64_t(di.sms) * occ, (b->n_items + wpc - 1) / wpc, l2_ctas})));
+            if ((rc = b->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring))) return bail(rc);
+            // row W of every ring is the all -1 row predecessors older than the sources read
+            std::vector<int32_t> h(size_t(b->grid_ie_pull) * wpc * (ring / 4), -1);
+            if (cudaMemcpy(b->ie_ring.p, h.data(), h.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return bail(fail(INSP_ECUDA, "initialising window rings"));
+        }
+    }
     if ((rc = alloc_scratch(b))) return bail(rc);
     *out = b;
     return INSP_OK;
@@ -586,8 +620,9 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
         CU(cudaMemsetAsync(S.ia_done.p, 0, S.ia_done.bytes, s));
         S.ia_epoch = 1;
     }
-    if (!b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
-    if (uint64_t(S.ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
+    const bool pull = !wide && b->grid_ie_pull > 0;
+    if (!pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
+    if (!pull && uint64_t(S.ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
         CU(cudaMemsetAsync(S.ie_rec.p, 0, S.ie_rec.bytes, s));
         S.ie_tag = 1;
     }
@@ -600,10 +635,15 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     }
     {
         TimedLaunch tl(b, TK_IE, s);
-        insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
-                        b->ie_rec_stride, S.ie_acc.p, b->W, wide, S.ie_tag, d_ie, b->grid_ie, s);
+        if (pull)
+            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
+                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, b->ie_ring.as<int32_t>(),
+                                 d_ie, b->grid_ie_pull, s);
+        else
+            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
+                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, S.ie_tag, d_ie, b->grid_ie, s);
     }
-    S.ie_tag += uint32_t(b->n_items);
+    if (!pull) S.ie_tag += uint32_t(b->n_items);
     CU(cudaGetLastError());
     if (st_ia || st_ie) {
         if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));

@@ -1,0 +1,219 @@
+// Inspiring efficiency (Sec. 4.2 / Sec. 4.3), "pull" form of the window sweep.
+//
+// A warp owns 32 consecutive sources (lane j <-> v0 + j) and visits every task
+// u = v0, v0+1, ... in id order (a topological order).  Each lane keeps, per
+// task, one value in a shared-memory ring of W slots (W a power of two above
+// every edge span, so every predecessor of u is still in the ring):
+//     -1         u is not in the source's cone,
+//     L in 1..T  u is in the cone and every path from the source to u weighs L
+//                or less (L = the longest path weight, GPU costs, both ends),
+//     OVER       u is in the cone but some path weighs more than T.
+// These codes are ordered so that a plain max over predecessors combines them:
+//     val_j(u) = source ? (c(u) <= T ? c(u) : OVER)
+//              : m = max over predecessors q >= v0 of val_j(q);
+//                m < 0 ? -1 : (m == OVER ? OVER : (m + c(u) <= T ? m + c(u) : OVER))
+// and IE(v_j) counts the tasks whose value lands in 1..T (the source excluded).
+// The sweep stops after the last task that received an in-window value from a
+// predecessor (tracked through each in-window task's largest successor id).
+// Predecessor lists (built at ingest) and GPU costs of the next 32 tasks are
+// staged into shared memory with coalesced loads.  The ring is a per-warp
+// slice of global memory sized to stay in L2 (a shared-memory ring was measured
+// slower: at 33 KB per warp it caps residency at 6 warps per SM); each lane
+// only reads its own column, i.e. its own earlier writes.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace insp {
+
+constexpr int PULL_WARPS = 4;
+constexpr int PCH = 32;      // tasks per staged chunk
+constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
+constexpr int32_t OVER = 0x7fffffff;
+
+// ring of W + 1 rows of 32 values (row W is all -1: where predecessors older
+// than the sources point)
+__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W + 1) * 32 * 4; }
+// per warp shared memory: the chunk staging
+constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) / 16 * 16;
+
+__global__ void __launch_bounds__(PULL_WARPS * 32)
+    k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
+              const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
+              int32_t *gring, int32_t *ie_out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const int32_t wmask = W - 1;
+    unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
+    int32_t *__restrict__ val = gring + (int64_t(blockIdx.x) * PULL_WARPS + wib) * (ie_ring_bytes(W) / 4);
+    int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
+    int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
+    int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
+    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row offset of each predecessor (row W if < v0)
+    val[W * 32 + lane] = -1;
+
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= n_items) return;
+        const int d = item_dag[item];
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        const int32_t v0 = int32_t(item - item_base[d]) * 32;
+        const int32_t n_src = min(32, n - v0);
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        const int32_t *pp = pr_ptr + tb + d;
+        const int32_t *pc = pcol + eb;
+        const int64_t T = unit_time[d];
+
+        int32_t cnt = 0;
+        int32_t hi = v0 + n_src - 1;
+        int32_t uc = -1, e0 = 0;  // first task and first predecessor edge of the staged chunk
+        for (int32_t u = v0; u <= hi; ++u) {
+            if (uc < 0 || u - uc >= PCH) {
+                __syncwarp();
+                uc = u;
+                const int32_t t = min(u + lane, n);
+                c_pp[lane] = pp[t];
+                if (lane == 0) c_pp[PCH] = pp[min(u + PCH, n)];
+                if (u + lane < n) {
+                    const int64_t cg = task_cost(B, d, tb + u + lane, 1);
+                    c_cost[lane] = int32_t(cg > T ? T + 1 : cg);
+                    const int32_t r0 = rp[u + lane], r1 = rp[u + lane + 1];
+                    c_msucc[lane] = r1 > r0 ? col[r1 - 1] : -1;
+                }
+                __syncwarp();
+                e0 = c_pp[0];
+                const int32_t ne = min(c_pp[PCH] - e0, PCOL);
+                // all loads of the chunk first, then the conversions and stores
+                int32_t qv[PCOL / 32];
+#pragma unroll
+                for (int r = 0; r < PCOL / 32; ++r) {
+                    const int32_t i = lane + 32 * r;
+                    qv[r] = i < ne ? __ldg(pc + e0 + i) : 0;
+                }
+#pragma unroll
+                for (int r = 0; r < PCOL / 32; ++r) {
+                    const int32_t i = lane + 32 * r;
+                    if (i < ne) c_off[i] = (qv[r] >= v0 ? (qv[r] & wmask) : W) * 32;
+                }
+                __syncwarp();
+            }
+            const int32_t k = u - uc;
+            const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
+            int32_t m0 = -1, m1 = -1;
+            if (hi_p <= PCOL) {
+                // full rounds of 8 predecessor values in flight, then a short tail
+                int32_t e = lo;
+                for (; e + 8 <= hi_p; e += 8) {
+                    int32_t pv[8];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) pv[r] = val[c_off[e + r] + lane];
+#pragma unroll
+                    for (int r = 0; r < 8; r += 2) {
+                        m0 = max(m0, pv[r]);
+                        m1 = max(m1, pv[r + 1]);
+                    }
+                }
+                for (; e < hi_p; ++e) m0 = max(m0, val[c_off[e] + lane]);
+            } else {
+                for (int32_t e = lo; e < hi_p; ++e) {
+                    const int32_t q = e < PCOL ? -2 : pc[e0 + e];
+                    const int32_t off = e < PCOL ? c_off[e] : (q >= v0 ? (q & wmask) : W) * 32;
+                    m0 = max(m0, val[off + lane]);
+                }
+            }
+            const int32_t m = max(m0, m1);
+            const int32_t c = c_cost[k];
+            int32_t v;
+            if (u - v0 == lane) {
+                v = (int64_t(c) <= T) ? c : OVER;
+            } else if (m < 0 || m == OVER) {
+                v = m;
+            } else {
+                const int64_t L = int64_t(m) + c;
+                v = L <= T ? int32_t(L) : OVER;
+                cnt += L <= T;
+            }
+            val[(u & wmask) * 32 + lane] = v;
+            if (__any_sync(FULL, v >= 0 && v != OVER)) hi = max(hi, c_msucc[k]);
+        }
+        if (lane < n_src) ie_out[tb + v0 + lane] = cnt;
+        __syncwarp();
+    }
+}
+
+// Predecessor lists of every DAG (CSR of the reversed edges, same layout as
+// row_ptr / col_idx): exclusive scan of the in-degrees, then a scatter.  Order
+// within a list is irrelevant to the max.  One CTA per DAG.
+__global__ void __launch_bounds__(256) k_reverse_csr(DevBatch B, const int32_t *indeg0, int32_t *pr_ptr,
+                                                     int32_t *cursor, int32_t *pcol) {
+    __shared__ int32_t s_scan[256];
+    __shared__ int32_t s_carry;
+    for (int d = blockIdx.x; d < B.ndag; d += gridDim.x) {
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        int32_t *pp = pr_ptr + tb + d;
+        if (threadIdx.x == 0) s_carry = 0;
+        __syncthreads();
+        for (int32_t base = 0; base < n; base += blockDim.x) {
+            const int32_t i = base + threadIdx.x;
+            const int32_t x = i < n ? indeg0[tb + i] : 0;
+            s_scan[threadIdx.x] = x;
+            __syncthreads();
+            for (int off = 1; off < int(blockDim.x); off <<= 1) {
+                const int32_t y = threadIdx.x >= unsigned(off) ? s_scan[threadIdx.x - off] : 0;
+                __syncthreads();
+                s_scan[threadIdx.x] += y;
+                __syncthreads();
+            }
+            const int32_t incl = s_scan[threadIdx.x];
+            if (i < n) {
+                pp[i] = s_carry + incl - x;
+                cursor[tb + i] = s_carry + incl - x;
+            }
+            __syncthreads();
+            if (threadIdx.x == blockDim.x - 1) s_carry += incl;
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) pp[n] = s_carry;
+        __syncthreads();
+        const int32_t *rp = B.row_ptr + tb + d;
+        for (int32_t u = threadIdx.x; u < n; u += blockDim.x)
+            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
+                const int32_t v = B.col_idx[eb + e];
+                const int32_t pos = atomicAdd(&cursor[tb + v], 1);
+                pcol[eb + pos] = u;
+            }
+        __syncthreads();
+    }
+}
+
+int ie_pull_warps() { return PULL_WARPS; }
+int64_t ie_pull_ring_bytes(int32_t W) { return ie_ring_bytes(W); }
+
+int ie_pull_occupancy() {
+    const int64_t bytes = IE_PULL_STAGE_BYTES * PULL_WARPS;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, PULL_WARPS * 32, size_t(bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nb;
+}
+
+void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
+                    const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
+                    int32_t *gring, int32_t *ie, int grid, cudaStream_t s) {
+    k_ie_pull<<<grid, PULL_WARPS * 32, size_t(IE_PULL_STAGE_BYTES * PULL_WARPS), s>>>(
+        B, pr_ptr, pcol, item_base, item_dag, n_items, counter, unit_time, W, gring, ie);
+}
+
+void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
+                        int grid, cudaStream_t s) {
+    k_reverse_csr<<<grid, 256, 0, s>>>(B, indeg0, pr_ptr, cursor, pcol);
+}
+
+}  // namespace insp

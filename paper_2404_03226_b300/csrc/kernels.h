@@ -48,6 +48,17 @@ void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
                uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s);
+// inspiring efficiency, pull form (k_ie_pull.cu)
+constexpr int32_t IE_PULL_MAX_W = 512;
+int ie_pull_warps();
+int64_t ie_pull_ring_bytes(int32_t W);
+int ie_pull_occupancy();
+// gring: per-warp rings of ie_pull_ring_bytes(W) in global memory (row W all -1)
+void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
+                    const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
+                    int32_t *gring, int32_t *ie, int grid, cudaStream_t s);
+void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
+                        int grid, cudaStream_t s);
 // learned scorer (k_mlp.cu)
 void launch_scorer_eval(const ScorerPacked *P, const int32_t *feat, int64_t n, int64_t *score, cudaStream_t s);
 void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
