@@ -208,12 +208,27 @@ int insp_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t
                float eps, float wd, void *stream);
 int insp_scorer_quantize(int64_t nw, const float *w, uint16_t *bf16_out, void *stream);
 
+/* One evaluation step as a CUDA graph.  insp_batch_record captures, on
+ * `stream` (not the legacy default stream), the kernels of
+ * insp_attributes_batch (default unit times) followed by insp_simulate_batch
+ * with the given device outputs, and keeps the instantiated graph in the batch
+ * (replacing an earlier one); it does not run the step.  insp_batch_replay
+ * launches the recorded step on `stream` -- the same results as the two calls,
+ * with one graph launch per step.  The output arrays must stay valid while the
+ * graph is used; calls on the batch must not overlap in time.
+ * Errors: INSP_EINVAL (host pointers, default stream, nothing recorded), INSP_ECUDA. */
+int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t *worker, int64_t *start, int64_t *end,
+                      int64_t *makespan, void *stream);
+int insp_batch_replay(insp_batch *b, void *stream);
+
 /* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
  * call on the batch records CUDA events on its stream around each kernel.
  * insp_batch_timing waits for them and returns the summed milliseconds and
  * launch counts since the last reset, per kernel: [0] inspiring ability,
  * [1] inspiring efficiency, [2] batched simulation, [3] per-DAG simulation
- * launches.  ms and launches may be NULL; reset != 0 clears the sums. */
+ * launches.  ms and launches may be NULL; reset != 0 clears the sums.  (Each
+ * attributes call also runs one single-thread step-counter kernel, not timed.)
+ * Steps replayed from a recorded graph are not timed. */
 int insp_batch_set_timing(insp_batch *b, int32_t enable);
 int insp_batch_timing(insp_batch *b, double *ms, int64_t *launches, int32_t reset);
 

@@ -57,6 +57,8 @@ _PROTOS = {
     "insp_adamw": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, ctypes.c_float, _vp]),
     "insp_scorer_quantize": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
+    "insp_batch_record": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_batch_replay": (ctypes.c_int, [_vp, _vp]),
     "insp_simulate_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _i32, _i64,
                                              ctypes.POINTER(insp_policy), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
@@ -238,3 +240,12 @@ def insp_adamw(nw, w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0, stream
 
 def insp_scorer_quantize(nw, w, out, stream=None) -> None:
     check(lib().insp_scorer_quantize(nw, ptr(w), ptr(out), stream_ptr(stream)))
+
+
+def insp_batch_record(b, ia, ie, worker, start, end, makespan, stream) -> None:
+    check(lib().insp_batch_record(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                                  stream_ptr(stream)))
+
+
+def insp_batch_replay(b, stream) -> None:
+    check(lib().insp_batch_replay(b, stream_ptr(stream)))

@@ -94,8 +94,7 @@ struct Scratch {
     DBuf ia_bits, ia_done;                                         // inspiring ability
     DBuf ie_rec, ie_acc;                                           // inspiring efficiency
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
-    int32_t ia_epoch = 0;   // done[] flags equal to the epoch are published in this call
-    uint32_t ie_tag = 1;    // records whose tag differs from the work item's are empty
+    DBuf step;              // insp::StepCounters (device-side epoch and record tags)
 };
 
 struct insp_machine {
@@ -136,8 +135,10 @@ struct insp_batch {
     std::vector<Pending> pending;
     double ms[TK_N] = {0, 0, 0, 0};
     int64_t launches[TK_N] = {0, 0, 0, 0};
+    cudaGraphExec_t graph = nullptr;  // recorded evaluation step (insp_batch_record)
 
     ~insp_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
     }
@@ -204,9 +205,11 @@ int alloc_scratch(insp_batch *b) {
     bool fresh = false;
     if ((rc = S.ia_bits.alloc(size_t(gia) * b->ia_slot_words * 4)) || (rc = S.ia_done.alloc(N * 4, &fresh)))
         return rc;
+    if (fresh) CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
+    if ((rc = S.step.alloc(sizeof(insp::StepCounters), &fresh))) return rc;
     if (fresh) {
-        CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
-        S.ia_epoch = 0;
+        const insp::StepCounters c0{0, 0, 1};  // epoch 0 is never published; tag 0 marks empty records
+        CU(cudaMemcpy(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice));
     }
     // inspiring efficiency: global-memory sweep scratch unless the pull form applies
     // (allocated later if a call needs the global form)
@@ -231,10 +234,7 @@ int alloc_ie_global(insp_batch *b) {
     const int64_t warps = gie * ie_warps_per_cta;
     bool fresh = false;
     if ((rc = S.ie_rec.alloc(size_t(warps) * b->ie_rec_stride * 16, &fresh))) return rc;
-    if (fresh) {
-        CU(cudaMemset(S.ie_rec.p, 0, S.ie_rec.bytes));
-        S.ie_tag = 1;
-    }
+    if (fresh) CU(cudaMemset(S.ie_rec.p, 0, S.ie_rec.bytes));
     if ((rc = S.ie_acc.alloc(size_t(warps) * b->W * 32 * 8))) return rc;
     b->ie_global_ready = true;
     return INSP_OK;
@@ -615,23 +615,16 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     if (b->ndag == 0) return INSP_OK;
     CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
     CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
-    S.ia_epoch += 1;
-    if (S.ia_epoch == 0x7fffffff) {
-        CU(cudaMemsetAsync(S.ia_done.p, 0, S.ia_done.bytes, s));
-        S.ia_epoch = 1;
-    }
     const bool pull = !wide && b->grid_ie_pull > 0;
     if (!pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
-    if (!pull && uint64_t(S.ie_tag) + uint64_t(b->n_items) >= 0xffffffffull) {
-        CU(cudaMemsetAsync(S.ie_rec.p, 0, S.ie_rec.bytes, s));
-        S.ie_tag = 1;
-    }
+    insp::StepCounters *sc = S.step.as<insp::StepCounters>();
+    insp::launch_step_begin(sc, b->n_items, s);
     insp::DevBatch B = b->dev();
     int32_t *ctr = b->counters.as<int32_t>();
     {
         TimedLaunch tl(b, TK_IA, s);
         insp::launch_ia(B, b->order.as<int32_t>(), ctr + 0, S.ia_bits.as<uint32_t>(), b->ia_slot_words,
-                        S.ia_done.as<int32_t>(), S.ia_epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
+                        S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
     }
     {
         TimedLaunch tl(b, TK_IE, s);
@@ -641,9 +634,8 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
                                  d_ie, b->grid_ie_pull, s);
         else
             insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
-                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, S.ie_tag, d_ie, b->grid_ie, s);
+                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, s);
     }
-    if (!pull) S.ie_tag += uint32_t(b->n_items);
     CU(cudaGetLastError());
     if (st_ia || st_ie) {
         if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
@@ -813,6 +805,55 @@ INSP_API int insp_batch_status(insp_batch *b, int32_t *status) {
     int rc = first_status(b, st);
     if (status) std::copy(st.begin(), st.end(), status);
     return rc;
+}
+
+INSP_API int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t *worker, int64_t *start,
+                               int64_t *end, int64_t *makespan, void *stream) {
+    if (!b || !stream) return fail(INSP_EINVAL, "batch and a non-default stream are required");
+    const void *ptrs[] = {ia, ie, worker, start, end, makespan};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    if (b->mach.pol.policy == INSP_POLICY_LEARNED && !(b->owner && b->owner->has_scorer))
+        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
+    // scratch the step may need is allocated before recording
+    if (b->grid_ie_pull == 0 && !b->ie_global_ready) {
+        int rc = alloc_ie_global(b);
+        if (rc) return rc;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const bool timing = b->timing;
+    b->timing = false;
+    CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    int rc = insp_attributes_batch(b, nullptr, ia, ie, stream);
+    if (rc == INSP_OK) rc = insp_simulate_batch(b, ia, ie, worker, start, end, makespan, stream);
+    const std::string err = g_err;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    b->timing = timing;
+    if (rc != INSP_OK) {
+        if (g) cudaGraphDestroy(g);
+        return fail(rc, "recording failed: " + err);
+    }
+    if (e != cudaSuccess) return fail(INSP_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    e = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->graph = nullptr;
+        return fail(INSP_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    return INSP_OK;
+}
+
+INSP_API int insp_batch_replay(insp_batch *b, void *stream) {
+    if (!b || !b->graph) return fail(INSP_EINVAL, "nothing recorded on this batch (insp_batch_record)");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    CU(cudaGraphLaunch(b->graph, s));
+    return INSP_OK;
 }
 
 INSP_API int insp_batch_set_timing(insp_batch *b, int32_t enable) {

@@ -24,7 +24,8 @@ constexpr int IA_WARPS = 8;
 
 __global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t *counter,
                                                       uint32_t *bits, int64_t slot_words, int32_t *done,
-                                                      int32_t epoch, int32_t *ia_out, int32_t *status) {
+                                                      const int32_t *epoch_ptr, int32_t *ia_out, int32_t *status) {
+    const int32_t epoch = *epoch_ptr;  // this step's value of the done flags
     __shared__ int32_t s_dag;
     __shared__ int32_t s_next;
     __shared__ int32_t s_abort;  // a wait gave up: later waits of this DAG return at once
@@ -112,12 +113,14 @@ __global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t 
 }
 
 // ------------------------------------------------------ inspiring efficiency
-// Per-task record of the sweep: {tag, reach mask, over mask, unused}.  A record
-// whose tag differs from the current work item's is empty (no reset needed).
+// Per-task record of the sweep: {tag low, reach mask, over mask, tag high}.  A
+// record whose 64-bit tag differs from the current work item's is empty (no
+// reset needed; tags grow by the number of work items every step).
 template <typename V>
 __global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                                             const int64_t *unit_time, uint4 *rec, int64_t rec_stride, V *acc,
-                                            int32_t W, uint32_t tag_base, int32_t *ie_out) {
+                                            int32_t W, const uint64_t *tag_base_ptr, int32_t *ie_out) {
+    const uint64_t tag_base = *tag_base_ptr;
     const int lane = threadIdx.x & 31;
     const int64_t warp_id = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     uint4 *my_rec = rec + warp_id * rec_stride;
@@ -136,13 +139,15 @@ __global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base
         const int32_t *rp = B.row_ptr + tb + d;
         const int32_t *col = B.col_idx + eb;
         const int64_t T = unit_time[d];
-        const uint32_t tag = tag_base + uint32_t(item);
+        const uint64_t tag64 = tag_base + uint64_t(item);
+        const uint32_t tag = uint32_t(tag64), tag_hi = uint32_t(tag64 >> 32);
         int32_t cnt = 0;
         int32_t hi = v0 + n_src - 1;
         for (int32_t x = v0; x <= hi; ++x) {
             const uint4 r = my_rec[x];
-            const uint32_t reach = (r.x == tag) ? r.y : 0u;
-            const uint32_t over = (r.x == tag) ? r.z : 0u;
+            const bool mine = r.x == tag && r.w == tag_hi;
+            const uint32_t reach = mine ? r.y : 0u;
+            const uint32_t over = mine ? r.z : 0u;
             const uint32_t src = (x - v0 < n_src) ? (1u << (x - v0)) : 0u;
             const uint32_t pmask = reach | src;
             if (pmask == 0) continue;
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base
                 if (i < ehi) {
                     s = col[i];
                     uint4 q = my_rec[s];
-                    if (q.x != tag) q = make_uint4(tag, 0u, 0u, 0u);
+                    if (q.x != tag || q.w != tag_hi) q = make_uint4(tag, 0u, 0u, tag_hi);
                     old_reach = q.y;
                     old_over = q.z;
                     q.y |= pmask;
@@ -199,14 +204,23 @@ __global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base
     }
 }
 
+// Start of an attributes step: the done-flag epoch and the record tags advance
+// (device-side, so a recorded CUDA graph replays correctly).
+__global__ void k_step_begin(StepCounters *c, int64_t n_items) {
+    c->epoch += 1;
+    c->tag_base += uint64_t(n_items);
+}
+
+void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s) { k_step_begin<<<1, 1, 0, s>>>(c, n_items); }
+
 void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
-               int32_t *done, int32_t epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s) {
+               int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s) {
     k_ia<<<grid, IA_WARPS * 32, 0, s>>>(B, order, counter, bits, slot_words, done, epoch, ia, status);
 }
 
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
-               uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s) {
+               const uint64_t *tag_base, int32_t *ie, int grid, cudaStream_t s) {
     if (wide)
         k_ie<int64_t><<<grid, 256, 0, s>>>(B, item_base, n_items, counter, unit_time, rec, rec_stride,
                                            (int64_t *)acc, W, tag_base, ie);

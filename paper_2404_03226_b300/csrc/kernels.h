@@ -43,11 +43,19 @@ struct SimArgs {
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
                      int grid, cudaStream_t s);
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s);
+// Device-side step counters of the attribute kernels: the done-flag epoch of
+// the ability sweep and the 64-bit record tag base of the efficiency sweep.
+struct StepCounters {
+    int32_t epoch;
+    int32_t pad;
+    uint64_t tag_base;
+};
+void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s);
 void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
-               int32_t *done, int32_t epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s);
+               int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s);
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
-               uint32_t tag_base, int32_t *ie, int grid, cudaStream_t s);
+               const uint64_t *tag_base, int32_t *ie, int grid, cudaStream_t s);
 // inspiring efficiency, pull form (k_ie_pull.cu)
 constexpr int32_t IE_PULL_MAX_W = 512;
 int ie_pull_warps();

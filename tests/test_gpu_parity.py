@@ -173,3 +173,40 @@ def test_single_dag_entry_points():
     np.testing.assert_array_equal(ia, r["ia"]); np.testing.assert_array_equal(ie, r["ie"])
     np.testing.assert_array_equal(w, r["worker"]); np.testing.assert_array_equal(s, r["start"])
     assert int(mk[0]) == r["makespan"]
+
+
+def test_recorded_graph_replays_match_direct_calls():
+    """A recorded evaluation step replayed several times (and interleaved with
+    direct calls) reproduces the direct results: the step counters live on the
+    device, so replays never reuse a stale done-flag epoch or record tag."""
+    import torch
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    b = inputs.layered(64, cfg=98, n_max=1500)
+    m = inputs.MACHINE_LAYERED
+    ref = gpu_run(b, m)
+    M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
+    B = P.DagBatch(M, b)
+    n, nd = b.n_total, b.ndag
+    dev = torch.device("cuda")
+    bufs = dict(ia=torch.empty(n, dtype=torch.int32, device=dev), ie=torch.empty(n, dtype=torch.int32, device=dev),
+                worker=torch.empty(n, dtype=torch.int32, device=dev), start=torch.empty(n, dtype=torch.int64, device=dev),
+                end=torch.empty(n, dtype=torch.int64, device=dev), makespan=torch.empty(nd, dtype=torch.int64, device=dev))
+    s = torch.cuda.Stream()
+    _lib.insp_batch_record(B.handle, bufs["ia"], bufs["ie"], bufs["worker"], bufs["start"], bufs["end"],
+                           bufs["makespan"], s)
+    for rep in range(3):
+        for v in bufs.values():
+            v.fill_(-1)
+        torch.cuda.synchronize()
+        _lib.insp_batch_replay(B.handle, s)
+        s.synchronize()
+        assert _lib.insp_batch_status(B.handle) == 0
+        for k, v in bufs.items():
+            np.testing.assert_array_equal(v.cpu().numpy(), ref[k], err_msg=f"{k}, replay {rep}")
+        if rep == 1:  # a direct step between replays advances the device counters too
+            _lib.insp_attributes_batch(B.handle, None, bufs["ia"], bufs["ie"], s)
+            s.synchronize()
+    with pytest.raises(_lib.InspError):
+        _lib.insp_batch_record(B.handle, bufs["ia"], bufs["ie"], bufs["worker"], bufs["start"], bufs["end"],
+                               bufs["makespan"], None)
