@@ -122,6 +122,24 @@ def traffic_from_profile(kernel: str):
     return rec["bytes_per_launch_full"]
 
 
+# ------------------------------------------------------------ multi-rank
+def rank_first_dag(rank: int, per_rank: int = 4096) -> int:
+    """Weak scaling: rank r evaluates its own window of the DAG stream."""
+    return rank * per_rank
+
+
+def combine_ranks(tasks: float, elapsed_s: float, dist, device) -> tuple[float, float]:
+    """Whole-job tasks (sum over ranks) and the slowest rank's time (max)."""
+    if dist is None:
+        return tasks, elapsed_s
+    import torch
+    t = torch.tensor([tasks, elapsed_s], dtype=torch.float64, device=device)
+    s_ = t.clone()
+    dist.all_reduce(s_, op=dist.ReduceOp.SUM)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(s_[0]), float(t[1])
+
+
 # --------------------------------------------------------------------- arms
 def cpu_baseline(batch, machine, budget_tasks=300000):
     """The oracle, as it stands, on the first DAGs of the workload (one core)."""
@@ -199,7 +217,7 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
 
     # weak scaling: each rank its own 4096 DAGs (--ndag: the first K of them, for profiling captures)
-    batch = inputs.layered4096(ndag=args.ndag, first=rank * 4096)
+    batch = inputs.layered4096(ndag=args.ndag, first=rank_first_dag(rank))
     mach = inputs.MACHINE_LAYERED
     machine = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns)
     b = P.DagBatch(machine, batch)
@@ -244,13 +262,7 @@ def run_ours(args, rank, world, local_rank):
     if _lib.insp_batch_status(b.handle) != 0:
         raise RuntimeError("device-side status not OK: " + _lib.last_error())
 
-    tasks_all, t_max = float(n) * args.steps, elapsed
-    if dist is not None:
-        t = torch.tensor([tasks_all, elapsed], dtype=torch.float64, device=dev)
-        s_ = t.clone()
-        dist.all_reduce(s_, op=dist.ReduceOp.SUM)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tasks_all, t_max = float(s_[0]), float(t[1])
+    tasks_all, t_max = combine_ranks(float(n) * args.steps, elapsed, dist, dev)
     value = tasks_all / t_max
 
     # ---- the same step recorded once as a CUDA graph and replayed
