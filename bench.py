@@ -34,6 +34,23 @@ WORKLOAD = ("4096 random layered DAGs (n~U[50,2000], width U[4,64], p U[0.1,0.5]
             "log-normal costs) on 8 CPU + 2 GPU workers, 20 us transfer, INSPIRIT policy")
 
 
+def make_workload(args, rank):
+    """(batch, machine, description) of the selected workload."""
+    import inputs
+    if args.workload == "layered":
+        # weak scaling: each rank its own 4096 DAGs (--ndag: the first K of them, for profiling captures)
+        b = inputs.layered4096(ndag=args.ndag, first=rank_first_dag(rank))
+        desc = WORKLOAD if args.ndag == 4096 else f"first {args.ndag} of: " + WORKLOAD
+        return b, inputs.MACHINE_LAYERED, desc, "8 CPU + 2 GPU workers, xfer 20000 ns"
+    if args.workload == "tiled":
+        Ns = tuple(int(x) for x in args.tiles.split(","))
+        b = inputs.tiled_workload(Ns=Ns, instances=args.instances)
+        desc = (f"tiled Cholesky / LU / QR DAGs at {args.tiles} tiles x {args.instances} instances each, "
+                f"per-task costs perturbed +-20 % from seed, 16 CPU + 4 GPU workers, 20 us transfer, INSPIRIT policy")
+        return b, inputs.MACHINE_TILED, desc, "16 CPU + 4 GPU workers, xfer 20000 ns"
+    raise ValueError(args.workload)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -96,13 +113,17 @@ class ClockSampler:
 # ---------------------------------------------------------------- roofline
 def algorithmic_bytes(batch):
     """Minimal HBM bytes per launch of each kernel: inputs read once, outputs
-    written once (scratch excluded)."""
+    written once (scratch excluded).  Costs: 1 byte of type per task with
+    per-type tables, or 8 (GPU cost) / 16 (both costs) bytes with per-task costs."""
     n, m, nd = batch.n_total, batch.m_total, batch.ndag
     csr = 4 * (n + nd) + 4 * m  # row_ptr + col_idx
+    per_task = batch.task_cost is not None
+    c_ie = 8 * n if per_task else n
+    c_sim = 16 * n if per_task else n
     return {
-        "k_ia": csr + 4 * n,                          # ia written
-        "k_ie": csr + n + 4 * n,                      # type read, ie written
-        "k_sim": csr + n + 4 * n + 8 * n + 20 * n + 8 * nd,  # type, in-degree, ia+ie read; worker/start/end + makespan
+        "k_ia": csr + 4 * n,                                   # ia written
+        "k_ie": csr + c_ie + 4 * n,                            # GPU cost read, ie written
+        "k_sim": csr + c_sim + 4 * n + 8 * n + 20 * n + 8 * nd,  # costs, in-degree, ia+ie read; schedule written
     }
 
 
@@ -216,9 +237,7 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    # weak scaling: each rank its own 4096 DAGs (--ndag: the first K of them, for profiling captures)
-    batch = inputs.layered4096(ndag=args.ndag, first=rank_first_dag(rank))
-    mach = inputs.MACHINE_LAYERED
+    batch, mach, wdesc, mdesc = make_workload(args, rank)
     machine = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns)
     b = P.DagBatch(machine, batch)
     n, ndag = b.n_tasks, b.ndag
@@ -347,16 +366,18 @@ def run_ours(args, rank, world, local_rank):
         h_tb, h_eb = pinned(batch.task_base), pinned(batch.edge_base)
         h_rp, h_ci, h_ty = pinned(batch.row_ptr), pinned(batch.col_idx), pinned(batch.type)
         h_tc = pinned(batch.type_cost)
+        h_kc = pinned(batch.task_cost) if batch.task_cost is not None else None
         o_w = torch.empty(n, dtype=torch.int32).pin_memory()
         o_s = torch.empty(n, dtype=torch.int64).pin_memory()
         o_e = torch.empty(n, dtype=torch.int64).pin_memory()
         o_m = torch.empty(ndag, dtype=torch.int64).pin_memory()
-        h2d = sum(int(t.numel() * t.element_size()) for t in (h_tb, h_eb, h_rp, h_ci, h_ty, h_tc))
+        h2d = sum(int(t.numel() * t.element_size()) for t in (h_tb, h_eb, h_rp, h_ci, h_ty, h_tc)
+                  + ((h_kc,) if h_kc is not None else ()))
         d2h = sum(int(t.numel() * t.element_size()) for t in (o_w, o_s, o_e, o_m))
 
         def e2e_step():
             h = _lib.insp_batch_load_csr(machine.handle, ndag, h_tb, h_eb, h_rp, h_ci, h_ty, batch.n_types, h_tc,
-                                         None)
+                                         h_kc)
             try:
                 _lib.insp_attributes_batch(h, None, ia, ie, stream)
                 _lib.insp_simulate_batch(h, ia, ie, o_w, o_s, o_e, o_m, stream)  # host outputs: D2H + sync
@@ -382,8 +403,8 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if ndag == 4096 else f"first {ndag} of: " + WORKLOAD, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
-                       "machine": "8 CPU + 2 GPU workers, xfer 20000 ns", "policy": "INSPIRIT (defaults)",
+            "config": {"workload": wdesc, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
+                       "machine": mdesc, "policy": "INSPIRIT (defaults)",
                        "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
                              f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
             "per_dag_form": per_dag,
@@ -408,6 +429,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ndag", type=int, default=4096, help="first K DAGs of the workload (profiling captures)")
+    ap.add_argument("--workload", choices=["layered", "tiled"], default="layered",
+                    help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches")
+    ap.add_argument("--tiles", default="16,32,64", help="tile counts of the tiled workload")
+    ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
     args = ap.parse_args()
