@@ -253,6 +253,12 @@ def run_ours(args, rank, world, local_rank):
         _lib.insp_attributes_batch(b.handle, None, ia, ie, stream)
         _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
 
+    # launch shapes picked on this batch before the timed region (setup, like the load)
+    tuning = _lib.insp_batch_autotune(b.handle, stream).as_dict() if args.autotune else \
+        _lib.insp_batch_get_tuning(b.handle).as_dict()
+    sizes = batch.sizes()
+    ia_bins = 1 if tuning["ia_bin_tasks"] <= 0 else \
+        int((sizes >= tuning["ia_bin_tasks"]).any()) + int((sizes < tuning["ia_bin_tasks"]).any())
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -405,6 +411,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": wdesc, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
                        "machine": mdesc, "policy": "INSPIRIT (defaults)",
+                       "tuning": dict(tuning, autotuned=bool(args.autotune)),
                        "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
                              f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
             "per_dag_form": per_dag,
@@ -414,8 +421,9 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cb,
             "clocks": clk,
             # our kernels in the timed region: ability, efficiency, simulation, plus one
-            # step-counter kernel per attributes call
-            "gpu_launches": int(klaunch[:3].sum() + klaunch[0]),
+            # step-counter kernel per attributes call; the ability sweep is one launch per
+            # non-empty size bin
+            "gpu_launches": int(klaunch[:3].sum() + klaunch[0] * (ia_bins - 1) + klaunch[0]),
         }
         print(json.dumps(res), flush=True)
     if dist is not None:
@@ -433,6 +441,8 @@ def main():
                     help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches")
     ap.add_argument("--tiles", default="16,32,64", help="tile counts of the tiled workload")
     ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the library's default launch shapes instead of autotuning them on the batch")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
     args = ap.parse_args()

@@ -221,6 +221,30 @@ int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t *worker, 
                       int64_t *makespan, void *stream);
 int insp_batch_replay(insp_batch *b, void *stream);
 
+/* ------------------------------------------------------------- tuning
+ * Launch shapes of the batched kernels, picked per batch by the library's own
+ * autotuner (no counterpart in the paper).  The inspiring-ability sweep splits
+ * the DAGs into two size bins at ia_bin_tasks (0: one bin) that run
+ * concurrently, each with its own warps per CTA. */
+typedef struct {
+    int32_t ia_bin_tasks;    /* DAGs with at least this many tasks form the large bin (0: all in one bin) */
+    int32_t ia_warps_small;  /* warps per CTA of the ability sweep, small bin (1..16) */
+    int32_t ia_warps_large;  /* warps per CTA of the ability sweep, large bin (1..16) */
+    int32_t ie_warps;        /* warps per CTA of the efficiency sweep (1..8) */
+    int32_t ie_ring_mb;      /* L2 budget of the efficiency sweep's window rings, MB (>= 1) */
+    int32_t sim_warps;       /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
+    int32_t sim_queue;       /* ready-pool entries per warp kept in shared memory: 32, 64 or 128 */
+} insp_tuning;
+
+/* Time a fixed candidate set of launch shapes on this batch (one step each
+ * after a warm-up, CUDA events on `stream`; device pointers are not needed),
+ * keep the fastest per kernel and return it in *chosen (may be NULL).  The
+ * results of later calls do not depend on the tuning.  Synchronous. */
+int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chosen);
+/* Set or read the tuning explicitly (set: INSP_EINVAL on out-of-range fields). */
+int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t);
+int insp_batch_get_tuning(const insp_batch *b, insp_tuning *t);
+
 /* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
  * call on the batch records CUDA events on its stream around each kernel.
  * insp_batch_timing waits for them and returns the summed milliseconds and

@@ -15,10 +15,10 @@ import numpy as np
 
 from . import _lib
 from ._lib import (INSP_POLICY_FIFO, INSP_POLICY_INSPIRIT, INSP_POLICY_LEARNED, InspError,  # noqa: F401
-                   insp_policy)
+                   insp_policy, insp_tuning)
 
-__all__ = ["Machine", "DagBatch", "InspError", "insp_policy", "INSP_POLICY_INSPIRIT", "INSP_POLICY_FIFO",
-           "INSP_POLICY_LEARNED"]
+__all__ = ["Machine", "DagBatch", "InspError", "insp_policy", "insp_tuning", "INSP_POLICY_INSPIRIT",
+           "INSP_POLICY_FIFO", "INSP_POLICY_LEARNED"]
 
 
 def _np(a, dtype):
@@ -90,6 +90,20 @@ class DagBatch:
         f = _lib.insp_simulate_per_dag if per_dag else _lib.insp_simulate_batch
         f(self.handle, ia, ie, sch.worker, sch.start, sch.end, sch.makespan, stream or torch.cuda.current_stream())
         return sch
+
+    def autotune(self, stream=None) -> dict:
+        """Time the library's candidate launch shapes on this batch and keep the
+        fastest per kernel; returns the chosen tuning as a dict."""
+        import torch
+        return _lib.insp_batch_autotune(self.handle, stream or torch.cuda.current_stream()).as_dict()
+
+    @property
+    def tuning(self) -> dict:
+        return _lib.insp_batch_get_tuning(self.handle).as_dict()
+
+    @tuning.setter
+    def tuning(self, t: dict) -> None:
+        _lib.insp_batch_set_tuning(self.handle, insp_tuning(**t))
 
     def status(self) -> np.ndarray:
         st = np.zeros(max(self.ndag, 1), np.int32)

@@ -23,6 +23,14 @@ class insp_policy(ctypes.Structure):
                 ("c", _i32), ("k_inc_tasks", _i64), ("k_inc_ns", _i64)]
 
 
+class insp_tuning(ctypes.Structure):
+    _fields_ = [("ia_bin_tasks", _i32), ("ia_warps_small", _i32), ("ia_warps_large", _i32), ("ie_warps", _i32),
+                ("ie_ring_mb", _i32), ("sim_warps", _i32), ("sim_queue", _i32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class InspError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERROR_NAMES.get(code, code)}: {msg}")
@@ -59,6 +67,9 @@ _PROTOS = {
     "insp_scorer_quantize": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
     "insp_batch_record": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_replay": (ctypes.c_int, [_vp, _vp]),
+    "insp_batch_autotune": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(insp_tuning)]),
+    "insp_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(insp_tuning)]),
+    "insp_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(insp_tuning)]),
     "insp_simulate_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _i32, _i64,
                                              ctypes.POINTER(insp_policy), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
@@ -249,3 +260,19 @@ def insp_batch_record(b, ia, ie, worker, start, end, makespan, stream) -> None:
 
 def insp_batch_replay(b, stream) -> None:
     check(lib().insp_batch_replay(b, stream_ptr(stream)))
+
+
+def insp_batch_autotune(b, stream=None) -> insp_tuning:
+    t = insp_tuning()
+    check(lib().insp_batch_autotune(b, stream_ptr(stream), ctypes.byref(t)))
+    return t
+
+
+def insp_batch_set_tuning(b, t: insp_tuning) -> None:
+    check(lib().insp_batch_set_tuning(b, ctypes.byref(t)))
+
+
+def insp_batch_get_tuning(b) -> insp_tuning:
+    t = insp_tuning()
+    check(lib().insp_batch_get_tuning(b, ctypes.byref(t)))
+    return t

@@ -70,18 +70,24 @@ bool is_device_ptr(const void *p) {
 
 struct DeviceInfo {
     int sms = 0;
-    int occ_sim = 0, occ_ia = 0, occ_ie = 0;
+    int occ_ie = 0;  // the global-memory efficiency sweep
 };
 
 int device_info(DeviceInfo &di) {
     int dev = 0;
     CU(cudaGetDevice(&dev));
     CU(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
-    di.occ_sim = insp::sim_occupancy();
-    di.occ_ia = insp::ia_occupancy();
     di.occ_ie = insp::ie_occupancy();
-    if (di.occ_sim < 1 || di.occ_ia < 1 || di.occ_ie < 1) return fail(INSP_ECUDA, "occupancy query failed");
+    if (di.occ_ie < 1) return fail(INSP_ECUDA, "occupancy query failed");
     return INSP_OK;
+}
+
+const insp_tuning kDefaultTuning = {0, 8, 8, 4, 64, 8, 64};
+
+bool tuning_ok(const insp_tuning &t) {
+    return t.ia_bin_tasks >= 0 && t.ia_warps_small >= 1 && t.ia_warps_small <= 16 && t.ia_warps_large >= 1 &&
+           t.ia_warps_large <= 16 && t.ie_warps >= 1 && t.ie_warps <= 8 && t.ie_ring_mb >= 1 && t.sim_warps >= 1 &&
+           t.sim_warps <= 8 && (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128);
 }
 
 }  // namespace
@@ -115,6 +121,7 @@ struct insp_batch {
     int32_t ndag = 0, n_types = 1;
     int64_t n_total = 0, m_total = 0;
     std::vector<int64_t> h_task_base, h_edge_base;
+    std::vector<int32_t> h_order;  // DAGs by descending size
     DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
     DBuf pr_ptr, pcol;      // predecessor lists (pull form of the efficiency sweep)
@@ -125,9 +132,16 @@ struct insp_batch {
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;
     std::unique_ptr<Scratch> sc;
-    int64_t ia_slot_words = 0, ie_rec_stride = 0;
+    int64_t ie_rec_stride = 0;
+    // tuning and the launch shapes derived from it
+    insp_tuning tun = kDefaultTuning;
+    int32_t ia_split = 0;                    // DAGs order[0, ia_split) form the large bin
+    int64_t ia_slot_large = 1, ia_slot_small = 1;  // bitset words per CTA slot
+    int grid_ia_large = 0, grid_ia_small = 0;
+    cudaStream_t side = nullptr;             // second stream of the concurrent bins
+    cudaEvent_t fork = nullptr, join = nullptr;
     bool ie_global_ready = false;
-    int grid_sim = 1, grid_ia = 1, grid_ie = 1;
+    int grid_ie = 1;
     cudaStream_t last_stream = nullptr;
     // kernel timing (tracing aid)
     bool timing = false;
@@ -139,6 +153,9 @@ struct insp_batch {
 
     ~insp_batch() {
         if (graph) cudaGraphExecDestroy(graph);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        if (side) cudaStreamDestroy(side);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
     }
@@ -169,6 +186,65 @@ int copy_in(DBuf &dst, const void *src, size_t bytes) {
 
 int alloc_ie_global(insp_batch *b);
 
+// Inspiring-ability scratch for the current tuning: one bitset slot per CTA,
+// sized by the largest DAG of its bin (rows of n tasks x ceil(n/32) words).
+int alloc_ia(insp_batch *b) {
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    Scratch &S = *b->sc;
+    auto size_of = [&](int k) { return b->h_task_base[b->h_order[k] + 1] - b->h_task_base[b->h_order[k]]; };
+    int32_t split = 0;  // h_order is by descending size
+    if (b->tun.ia_bin_tasks <= 0) split = b->ndag;
+    else
+        while (split < b->ndag && size_of(split) >= b->tun.ia_bin_tasks) ++split;
+    b->ia_split = split;
+    const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
+    auto slot_words = [&](int k) {
+        const int64_t n = k < b->ndag ? size_of(k) : 0;
+        return std::max<int64_t>(n * ((n + 31) / 32), 1);
+    };
+    b->ia_slot_large = slot_words(0);
+    b->ia_slot_small = slot_words(split);
+    const int occ_l = std::max(1, insp::ia_occupancy(b->tun.ia_warps_large));
+    const int occ_s = std::max(1, insp::ia_occupancy(b->tun.ia_warps_small));
+    const int64_t n_large = split, n_small = b->ndag - split;
+    int64_t gl = std::min<int64_t>(int64_t(di.sms) * occ_l, n_large);
+    int64_t gs = std::min<int64_t>(int64_t(di.sms) * occ_s, n_small);
+    const int64_t need_l = gl * b->ia_slot_large * 4, need_s = gs * b->ia_slot_small * 4;
+    if (need_l + need_s > budget) {  // shrink both bins' grids in proportion
+        const double f = double(budget) / double(need_l + need_s);
+        gl = n_large ? std::max<int64_t>(1, int64_t(gl * f)) : 0;
+        gs = n_small ? std::max<int64_t>(1, int64_t(gs * f)) : 0;
+    }
+    b->grid_ia_large = int(gl);
+    b->grid_ia_small = int(gs);
+    if (gl > 0 && gs > 0 && !b->side) {  // the side stream of the concurrent bins
+        CU(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+    }
+    return S.ia_bits.alloc(size_t(gl * b->ia_slot_large + gs * b->ia_slot_small) * 4 + 16);
+}
+
+// Window rings of the pull efficiency sweep for the current tuning (L2 budget).
+int alloc_pull_ring(insp_batch *b) {
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    const int wpc = b->tun.ie_warps;
+    const int occ = insp::ie_pull_occupancy(wpc);
+    if (occ < 1) return fail(INSP_ECUDA, "occupancy query failed");
+    const int64_t ring = insp::ie_pull_ring_bytes(b->W);
+    const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(b->tun.ie_ring_mb) << 20) / (ring * wpc));
+    b->grid_ie_pull = int(std::max<int64_t>(1, std::min({int64_t(di.sms) * occ, (b->n_items + wpc - 1) / wpc, l2_ctas})));
+    if ((rc = b->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring))) return rc;
+    // row W of every ring is the all -1 row predecessors older than the sources read
+    std::vector<int32_t> h(b->ie_ring.bytes / 4, -1);
+    CU(cudaMemcpy(b->ie_ring.p, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
+    return INSP_OK;
+}
+
 int alloc_scratch(insp_batch *b) {
     DeviceInfo di;
     int rc = device_info(di);
@@ -190,27 +266,15 @@ int alloc_scratch(insp_batch *b) {
         (rc = S.p_ie.alloc(N * 4)) || (rc = S.p_dr.alloc(N * 8)) || (rc = S.p_cost.alloc(N * 8)) ||
         (rc = S.nl.alloc(N * 4)))
         return rc;
-    b->grid_sim = std::max(1, std::min(di.sms * di.occ_sim, (b->ndag + insp::sim_warps() - 1) / insp::sim_warps()));
-    // inspiring ability: one bitset slot per CTA (rows of max_n tasks x ceil(max_n/32) words)
-    int64_t slot = 0;
-    for (int d = 0; d < b->ndag; ++d) {
-        int64_t n = b->h_task_base[d + 1] - b->h_task_base[d];
-        slot = std::max(slot, n * ((n + 31) / 32));
-    }
-    b->ia_slot_words = std::max<int64_t>(slot, 1);
-    const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
-    int64_t gia = std::min<int64_t>(int64_t(di.sms) * di.occ_ia, std::max(b->ndag, 1));
-    gia = std::max<int64_t>(1, std::min<int64_t>(gia, budget / (b->ia_slot_words * 4)));
-    b->grid_ia = int(gia);
     bool fresh = false;
-    if ((rc = S.ia_bits.alloc(size_t(gia) * b->ia_slot_words * 4)) || (rc = S.ia_done.alloc(N * 4, &fresh)))
-        return rc;
+    if ((rc = S.ia_done.alloc(N * 4, &fresh))) return rc;
     if (fresh) CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
     if ((rc = S.step.alloc(sizeof(insp::StepCounters), &fresh))) return rc;
     if (fresh) {
         const insp::StepCounters c0{0, 0, 1};  // epoch 0 is never published; tag 0 marks empty records
         CU(cudaMemcpy(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice));
     }
+    if ((rc = alloc_ia(b))) return rc;
     // inspiring efficiency: global-memory sweep scratch unless the pull form applies
     // (allocated later if a call needs the global form)
     b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
@@ -500,6 +564,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         return (b->h_task_base[a + 1] - b->h_task_base[a]) > (b->h_task_base[c + 1] - b->h_task_base[c]);
     });
+    b->h_order = order;
     std::vector<int64_t> items(ndag + 1, 0);
     for (int d = 0; d < ndag; ++d) items[d + 1] = items[d] + (b->h_task_base[d + 1] - b->h_task_base[d] + 31) / 32;
     b->n_items = items[ndag];
@@ -510,30 +575,17 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
         (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)) ||
         (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)))
         return bail(rc);
-    // pull form of the efficiency sweep when its window ring fits shared memory
+    // pull form of the efficiency sweep when its window is at most IE_PULL_MAX_W
     if (b->W <= insp::IE_PULL_MAX_W && ndag > 0) {
-        const int occ = insp::ie_pull_occupancy();
-        if (occ > 0) {
-            DBuf cursor;
-            if ((rc = b->pr_ptr.alloc((b->n_total + ndag) * 4)) || (rc = b->pcol.alloc(std::max<int64_t>(b->m_total, 1) * 4)) ||
-                (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
-                return bail(rc);
-            insp::launch_reverse_csr(B, b->indeg0.as<int32_t>(), b->pr_ptr.as<int32_t>(), cursor.as<int32_t>(),
-                                     b->pcol.as<int32_t>(), grid, 0);
-            if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
-                return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
-            // rings of all warps stay L2-resident: ~64 MB of rings at most
-            const int wpc = insp::ie_pull_warps();
-            const int64_t ring = insp::ie_pull_ring_bytes(b->W);
-            const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(64) << 20) / (ring * wpc));
-            b->grid_ie_pull = int(std::max<int64_t>(
-                1, std::min({int64_t(di.sms) * occ, (b->n_items + wpc - 1) / wpc, l2_ctas})));
-            if ((rc = b->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring))) return bail(rc);
-            // row W of every ring is the all -1 row predecessors older than the sources read
-            std::vector<int32_t> h(size_t(b->grid_ie_pull) * wpc * (ring / 4), -1);
-            if (cudaMemcpy(b->ie_ring.p, h.data(), h.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-                return bail(fail(INSP_ECUDA, "initialising window rings"));
-        }
+        DBuf cursor;
+        if ((rc = b->pr_ptr.alloc((b->n_total + ndag) * 4)) || (rc = b->pcol.alloc(std::max<int64_t>(b->m_total, 1) * 4)) ||
+            (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
+            return bail(rc);
+        insp::launch_reverse_csr(B, b->indeg0.as<int32_t>(), b->pr_ptr.as<int32_t>(), cursor.as<int32_t>(),
+                                 b->pcol.as<int32_t>(), grid, 0);
+        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
+            return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
+        if ((rc = alloc_pull_ring(b))) return bail(rc);
     }
     if ((rc = alloc_scratch(b))) return bail(rc);
     *out = b;
@@ -622,16 +674,34 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     insp::DevBatch B = b->dev();
     int32_t *ctr = b->counters.as<int32_t>();
     {
+        // the two size bins of the ability sweep run concurrently (large bin on s, small on a side stream)
         TimedLaunch tl(b, TK_IA, s);
-        insp::launch_ia(B, b->order.as<int32_t>(), ctr + 0, S.ia_bits.as<uint32_t>(), b->ia_slot_words,
-                        S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(), b->grid_ia, s);
+        const int32_t *ord = b->order.as<int32_t>();
+        uint32_t *bits = S.ia_bits.as<uint32_t>();
+        uint32_t *bits_small = bits + int64_t(b->grid_ia_large) * b->ia_slot_large;
+        const bool two = b->grid_ia_large > 0 && b->grid_ia_small > 0;
+        if (two) {
+            CU(cudaEventRecord(b->fork, s));
+            CU(cudaStreamWaitEvent(b->side, b->fork, 0));
+        }
+        if (b->grid_ia_large > 0)
+            insp::launch_ia(B, ord, b->ia_split, ctr + 0, bits, b->ia_slot_large, S.ia_done.as<int32_t>(), &sc->epoch,
+                            d_ia, b->status.as<int32_t>(), b->grid_ia_large, b->tun.ia_warps_large, s);
+        if (b->grid_ia_small > 0)
+            insp::launch_ia(B, ord + b->ia_split, b->ndag - b->ia_split, ctr + 2, bits_small, b->ia_slot_small,
+                            S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(), b->grid_ia_small,
+                            b->tun.ia_warps_small, two ? b->side : s);
+        if (two) {
+            CU(cudaEventRecord(b->join, b->side));
+            CU(cudaStreamWaitEvent(s, b->join, 0));
+        }
     }
     {
         TimedLaunch tl(b, TK_IE, s);
         if (pull)
             insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
                                  b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, b->ie_ring.as<int32_t>(),
-                                 d_ie, b->grid_ie_pull, s);
+                                 d_ie, b->grid_ie_pull, b->tun.ie_warps, s);
         else
             insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
                             b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, s);
@@ -734,14 +804,12 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         } else {
             A.single_dag = -1;
             TimedLaunch tl(b, TK_SIM, s);
-            int grid = b->grid_sim;
-            if (learned) {
-                DeviceInfo di;
-                if ((rc = device_info(di))) return rc;
-                const int occ = std::max(1, insp::sim_learned_occupancy());
-                grid = std::max(1, std::min(di.sms * occ, (b->ndag + insp::sim_warps() - 1) / insp::sim_warps()));
-            }
-            insp::launch_sim(A, grid, s);
+            DeviceInfo di;
+            if ((rc = device_info(di))) return rc;
+            const int wpc = b->tun.sim_warps;
+            const int occ = std::max(1, insp::sim_occupancy(learned, wpc, b->tun.sim_queue));
+            const int grid = std::max(1, std::min(di.sms * occ, (b->ndag + wpc - 1) / wpc));
+            insp::launch_sim(A, grid, wpc, b->tun.sim_queue, s);
         }
         CU(cudaGetLastError());
     }
@@ -854,6 +922,123 @@ INSP_API int insp_batch_replay(insp_batch *b, void *stream) {
     b->last_stream = s;
     CU(cudaGraphLaunch(b->graph, s));
     return INSP_OK;
+}
+
+INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
+    if (!b || !t) return fail(INSP_EINVAL, "NULL argument");
+    if (!tuning_ok(*t)) return fail(INSP_EINVAL, "tuning field out of range");
+    const insp_tuning old = b->tun;
+    b->tun = *t;
+    int rc = INSP_OK;
+    if (old.ia_bin_tasks != t->ia_bin_tasks || old.ia_warps_small != t->ia_warps_small ||
+        old.ia_warps_large != t->ia_warps_large)
+        rc = alloc_ia(b);
+    if (rc == INSP_OK && b->grid_ie_pull > 0 && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
+        rc = alloc_pull_ring(b);
+    if (rc != INSP_OK) b->tun = old;
+    if (b->graph) {  // a recorded step holds the old launch shapes
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return rc;
+}
+
+INSP_API int insp_batch_get_tuning(const insp_batch *b, insp_tuning *t) {
+    if (!b || !t) return fail(INSP_EINVAL, "NULL argument");
+    *t = b->tun;
+    return INSP_OK;
+}
+
+INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chosen) {
+    if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    if (b->ndag == 0) {
+        if (chosen) *chosen = b->tun;
+        return INSP_OK;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    Scratch &S = *b->sc;
+    const int64_t N = std::max<int64_t>(b->n_total, 1);
+    int rc;
+    int32_t *ia, *ie, *worker;
+    int64_t *start, *end, *mk;
+    if ((rc = S.s_ia.alloc(N * 4)) || (rc = S.s_ie.alloc(N * 4)) || (rc = S.s_worker.alloc(N * 4)) ||
+        (rc = S.s_start.alloc(N * 8)) || (rc = S.s_end.alloc(N * 8)) || (rc = S.s_makespan.alloc(b->ndag * 8)))
+        return rc;
+    ia = S.s_ia.as<int32_t>();
+    ie = S.s_ie.as<int32_t>();
+    worker = S.s_worker.as<int32_t>();
+    start = S.s_start.as<int64_t>();
+    end = S.s_end.as<int64_t>();
+    mk = S.s_makespan.as<int64_t>();
+    const bool timing = b->timing;
+    b->timing = false;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    // time one call after a warm-up call; which: 0 attributes, 1 simulation
+    auto time_call = [&](int which, float &ms) -> int {
+        for (int rep = 0; rep < 2; ++rep) {
+            CU(cudaEventRecord(e0, s));
+            const int r = which == 0 ? insp_attributes_batch(b, nullptr, ia, ie, stream)
+                                     : insp_simulate_batch(b, ia, ie, worker, start, end, mk, stream);
+            if (r) return r;
+            CU(cudaEventRecord(e1, s));
+            CU(cudaEventSynchronize(e1));
+        }
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        return INSP_OK;
+    };
+    insp_tuning best = b->tun;
+    auto search = [&](const std::vector<insp_tuning> &cands, int which) -> int {
+        float best_ms = 1e30f;
+        for (const insp_tuning &c : cands) {
+            int r = insp_batch_set_tuning(b, &c);
+            if (r) return r;
+            float ms = 0;
+            if ((r = time_call(which, ms))) return r;
+            if (ms < best_ms) { best_ms = ms; best = c; }
+        }
+        return insp_batch_set_tuning(b, &best);
+    };
+    // 1. ability sweep: size bins and CTA sizes (efficiency sweep at its current shape)
+    std::vector<insp_tuning> c_ia;
+    const int ia_choice[][3] = {{0, 8, 8}, {0, 16, 16}, {0, 4, 4}, {1024, 4, 16}, {1024, 8, 16}, {512, 4, 8}};
+    for (auto &x : ia_choice) {
+        insp_tuning t = best;
+        t.ia_bin_tasks = x[0]; t.ia_warps_small = x[1]; t.ia_warps_large = x[2];
+        c_ia.push_back(t);
+    }
+    rc = search(c_ia, 0);
+    // 2. efficiency sweep: CTA size and ring budget (only the pull form has them)
+    if (rc == INSP_OK && b->grid_ie_pull > 0) {
+        std::vector<insp_tuning> c_ie;
+        for (int w : {2, 4, 8})
+            for (int mb : {32, 64, 128}) {
+                insp_tuning t = best;
+                t.ie_warps = w; t.ie_ring_mb = mb;
+                c_ie.push_back(t);
+            }
+        rc = search(c_ie, 0);
+    }
+    // 3. simulation: DAGs per CTA and queue capacity
+    if (rc == INSP_OK) {
+        CU(cudaStreamSynchronize(s));
+        std::vector<insp_tuning> c_sim;
+        for (int w : {4, 8})
+            for (int q : {32, 64, 128}) {
+                insp_tuning t = best;
+                t.sim_warps = w; t.sim_queue = q;
+                c_sim.push_back(t);
+            }
+        rc = search(c_sim, 1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->timing = timing;
+    if (rc) return rc;
+    if (chosen) *chosen = b->tun;
+    std::vector<int32_t> st;
+    return first_status(b, st);
 }
 
 INSP_API int insp_batch_set_timing(insp_batch *b, int32_t enable) {

@@ -20,9 +20,10 @@
 namespace insp {
 
 // --------------------------------------------------------- inspiring ability
-constexpr int IA_WARPS = 8;
+constexpr int IA_MAX_WARPS = 16;  // warps per CTA: blockDim / 32, up to 16 (per size bin, autotuned)
 
-__global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t *counter,
+__global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t n_order,
+                                                          int32_t *counter,
                                                       uint32_t *bits, int64_t slot_words, int32_t *done,
                                                       const int32_t *epoch_ptr, int32_t *ia_out, int32_t *status) {
     const int32_t epoch = *epoch_ptr;  // this step's value of the done flags
@@ -35,7 +36,7 @@ __global__ void __launch_bounds__(IA_WARPS * 32) k_ia(DevBatch B, const int32_t 
         __syncthreads();
         if (threadIdx.x == 0) {
             int k = atomicAdd(counter, 1);
-            int d = k < B.ndag ? order[k] : -1;
+            int d = k < n_order ? order[k] : -1;
             s_dag = d;
             s_next = d >= 0 ? int32_t(B.task_base[d + 1] - B.task_base[d]) - 1 : -1;
             s_abort = 0;
@@ -213,9 +214,10 @@ __global__ void k_step_begin(StepCounters *c, int64_t n_items) {
 
 void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s) { k_step_begin<<<1, 1, 0, s>>>(c, n_items); }
 
-void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
-               int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s) {
-    k_ia<<<grid, IA_WARPS * 32, 0, s>>>(B, order, counter, bits, slot_words, done, epoch, ia, status);
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint32_t *bits,
+               int64_t slot_words, int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid,
+               int warps, cudaStream_t s) {
+    k_ia<<<grid, 32 * warps, 0, s>>>(B, order, n_order, counter, bits, slot_words, done, epoch, ia, status);
 }
 
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
@@ -229,11 +231,11 @@ void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int
                                            (int32_t *)acc, W, tag_base, ie);
 }
 
-int ia_threads() { return IA_WARPS * 32; }
+int ia_max_warps() { return IA_MAX_WARPS; }
 int ie_threads() { return 256; }
-int ia_occupancy() {
+int ia_occupancy(int warps) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ia, IA_WARPS * 32, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ia, 32 * warps, 0) != cudaSuccess) return 0;
     return nb;
 }
 int ie_occupancy() {

@@ -25,7 +25,7 @@
 
 namespace insp {
 
-constexpr int PULL_WARPS = 4;
+constexpr int PULL_MAX_WARPS = 8;  // warps per CTA: blockDim / 32 (autotuned)
 constexpr int PCH = 32;      // tasks per staged chunk
 constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
@@ -36,7 +36,7 @@ __host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) / 16 * 16;
 
-__global__ void __launch_bounds__(PULL_WARPS * 32)
+__global__ void __launch_bounds__(PULL_MAX_WARPS * 32)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
               int32_t *gring, int32_t *ie_out) {
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(PULL_WARPS * 32)
     const int wib = threadIdx.x >> 5;
     const int32_t wmask = W - 1;
     unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
-    int32_t *__restrict__ val = gring + (int64_t(blockIdx.x) * PULL_WARPS + wib) * (ie_ring_bytes(W) / 4);
+    int32_t *__restrict__ val = gring + (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / 4);
     int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
     int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
     int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
@@ -191,13 +191,13 @@ __global__ void __launch_bounds__(256) k_reverse_csr(DevBatch B, const int32_t *
     }
 }
 
-int ie_pull_warps() { return PULL_WARPS; }
+int ie_pull_max_warps() { return PULL_MAX_WARPS; }
 int64_t ie_pull_ring_bytes(int32_t W) { return ie_ring_bytes(W); }
 
-int ie_pull_occupancy() {
-    const int64_t bytes = IE_PULL_STAGE_BYTES * PULL_WARPS;
+int ie_pull_occupancy(int warps) {
+    const int64_t bytes = IE_PULL_STAGE_BYTES * warps;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, PULL_WARPS * 32, size_t(bytes)) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, warps * 32, size_t(bytes)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -206,9 +206,9 @@ int ie_pull_occupancy() {
 
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
-                    int32_t *gring, int32_t *ie, int grid, cudaStream_t s) {
-    k_ie_pull<<<grid, PULL_WARPS * 32, size_t(IE_PULL_STAGE_BYTES * PULL_WARPS), s>>>(
-        B, pr_ptr, pcol, item_base, item_dag, n_items, counter, unit_time, W, gring, ie);
+                    int32_t *gring, int32_t *ie, int grid, int warps, cudaStream_t s) {
+    k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
+                                                                           n_items, counter, unit_time, W, gring, ie);
 }
 
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,

@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_mlp_samples(int32_t in, int32_t h1, int
             }
         }
         __syncwarp();
-        float z2v[2] = {0, 0}, a2v[2] = {0, 0}, part = 0.f;
+        float z2v[2] = {0, 0}, part = 0.f;
         for (int r = 0; r < 2; ++r) {
             const int j = lane + 32 * r;
             if (j < h2) {
@@ -114,7 +114,6 @@ __global__ void __launch_bounds__(256) k_mlp_samples(int32_t in, int32_t h1, int
                 float a = fmaxf(z, 0.f);
                 if (mode) a = floorf(a);
                 a = fminf(a, 255.f);
-                a2v[r] = a;
                 ws[2 * h1 + j] = a;
                 part += W3[j] * a;
             }

@@ -20,16 +20,20 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace insp {
 
-constexpr int SIM_WARPS = 8;
-constexpr int POOL_C = 64;   // pool entries per warp in shared memory
-constexpr int NL_C = 128;    // released-task buffer per warp in shared memory
+constexpr int SIM_WARPS = 8;  // most warps per CTA (the autotuner may launch fewer)
+constexpr int NL_C = 128;     // released-task buffer per warp in shared memory
 constexpr int NODE_NONE = 0xff;
 
 enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4 };
 enum { ST_INC = 0, ST_DEC = 1 };
 
+// POOL_C: ready-pool entries per warp kept in shared memory (the queue
+// capacity the autotuner picks; entries beyond it spill to global memory).
+template <int POOL_C>
 struct WarpSmem {
     int32_t idw[POOL_C];  // task id | worker << 24
     int32_t seq[POOL_C];
@@ -42,8 +46,9 @@ struct WarpSmem {
     int64_t tcost[MAX_TYPES_SMEM * 2];
 };
 
+template <int POOL_C>
 struct Pool {
-    WarpSmem *sm;
+    WarpSmem<POOL_C> *sm;
     int32_t *g_idw, *g_seq, *g_ia, *g_ie;
     int64_t *g_dr, *g_cost;
     __device__ __forceinline__ int32_t idw(int i) const { return i < POOL_C ? sm->idw[i] : g_idw[i - POOL_C]; }
@@ -153,13 +158,13 @@ struct LearnSmem {
     int32_t cidx[32];
 };
 
-template <bool LEARNED>
+template <bool LEARNED, int POOL_C>
 __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
-    __shared__ WarpSmem smem_all[SIM_WARPS];
+    __shared__ WarpSmem<POOL_C> smem_all[SIM_WARPS];
     extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WarpSmem *sm = &smem_all[wib];
+    WarpSmem<POOL_C> *sm = &smem_all[wib];
     ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn);
     LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn + sizeof(ScorerPacked)) + wib;
     if (LEARNED) {
@@ -191,7 +196,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         int2 *st_a = A.st_a + tb;
         longlong2 *st_b = A.st_b + tb;
         const int32_t *g_ia = A.ia + tb, *g_ie = A.ie + tb;
-        Pool pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
+        Pool<POOL_C> pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
         int32_t *nl_g = A.nl + tb;
 
         // resolved policy parameters (zero = default for P workers and the DAG's default T)
@@ -514,36 +519,49 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
 
 constexpr size_t LEARN_SMEM = sizeof(ScorerPacked) + SIM_WARPS * sizeof(LearnSmem);
 
-void launch_sim(const SimArgs &A, int grid, cudaStream_t s) {
-    if (A.policy == INSP_POLICY_LEARNED) {
-        cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-        k_sim<true><<<grid, SIM_WARPS * 32, LEARN_SMEM, s>>>(A);
+template <bool L, int Q>
+static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
+    if (L) {
+        cudaFuncSetAttribute(k_sim<L, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+        k_sim<L, Q><<<grid, threads, LEARN_SMEM, s>>>(A);
     } else {
-        k_sim<false><<<grid, SIM_WARPS * 32, 0, s>>>(A);
+        k_sim<L, Q><<<grid, threads, 0, s>>>(A);
     }
+}
+
+template <bool L>
+static void launch_l(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
+    if (queue <= 32) launch_q<L, 32>(A, grid, threads, s);
+    else if (queue <= 64) launch_q<L, 64>(A, grid, threads, s);
+    else launch_q<L, 128>(A, grid, threads, s);
+}
+
+void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s) {
+    const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));
+    if (A.policy == INSP_POLICY_LEARNED) launch_l<true>(A, grid, threads, queue, s);
+    else launch_l<false>(A, grid, threads, queue, s);
 }
 // The unbatched form: one launch, one warp, one DAG.
 void launch_sim_single(const SimArgs &A, cudaStream_t s) {
-    if (A.policy == INSP_POLICY_LEARNED) {
-        cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-        k_sim<true><<<1, 32, LEARN_SMEM, s>>>(A);
-    } else {
-        k_sim<false><<<1, 32, 0, s>>>(A);
-    }
+    if (A.policy == INSP_POLICY_LEARNED) launch_l<true>(A, 1, 32, 64, s);
+    else launch_l<false>(A, 1, 32, 64, s);
 }
-int sim_threads() { return SIM_WARPS * 32; }
-int sim_warps() { return SIM_WARPS; }
-int sim_occupancy() {
+int sim_max_warps() { return SIM_WARPS; }
+
+template <bool L, int Q>
+static int occ_q(int threads) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<false>, SIM_WARPS * 32, 0) != cudaSuccess) return 0;
-    return nb;
-}
-int sim_learned_occupancy() {
-    int nb = 0;
-    cudaFuncSetAttribute(k_sim<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<true>, SIM_WARPS * 32, LEARN_SMEM) != cudaSuccess)
+    if (L) cudaFuncSetAttribute(k_sim<L, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q>, threads, L ? LEARN_SMEM : 0) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     return nb;
+}
+int sim_occupancy(bool learned, int warps, int queue) {
+    const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));
+    if (learned) return queue <= 32 ? occ_q<true, 32>(threads) : queue <= 64 ? occ_q<true, 64>(threads) : occ_q<true, 128>(threads);
+    return queue <= 32 ? occ_q<false, 32>(threads) : queue <= 64 ? occ_q<false, 64>(threads) : occ_q<false, 128>(threads);
 }
 
 }  // namespace insp

@@ -51,20 +51,21 @@ struct StepCounters {
     uint64_t tag_base;
 };
 void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s);
-void launch_ia(const DevBatch &B, const int32_t *order, int32_t *counter, uint32_t *bits, int64_t slot_words,
-               int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid, cudaStream_t s);
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint32_t *bits,
+               int64_t slot_words, int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid,
+               int warps, cudaStream_t s);
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
                const uint64_t *tag_base, int32_t *ie, int grid, cudaStream_t s);
 // inspiring efficiency, pull form (k_ie_pull.cu)
 constexpr int32_t IE_PULL_MAX_W = 512;
-int ie_pull_warps();
+int ie_pull_max_warps();
 int64_t ie_pull_ring_bytes(int32_t W);
-int ie_pull_occupancy();
+int ie_pull_occupancy(int warps);
 // gring: per-warp rings of ie_pull_ring_bytes(W) in global memory (row W all -1)
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
-                    int32_t *gring, int32_t *ie, int grid, cudaStream_t s);
+                    int32_t *gring, int32_t *ie, int grid, int warps, cudaStream_t s);
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
                         int grid, cudaStream_t s);
 // learned scorer (k_mlp.cu)
@@ -75,15 +76,13 @@ void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, i
 void launch_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t t, float lr, float b1, float b2,
                   float eps, float wd, cudaStream_t s);
 void launch_quantize(int64_t nw, const float *w, uint16_t *out, cudaStream_t s);
-void launch_sim(const SimArgs &A, int grid, cudaStream_t s);
-int sim_learned_occupancy();
+void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s);
+int sim_occupancy(bool learned, int warps, int queue);
+int sim_max_warps();
 void launch_sim_single(const SimArgs &A, cudaStream_t s);
-int ia_threads();
+int ia_max_warps();
+int ia_occupancy(int warps);
 int ie_threads();
-int sim_threads();
-int sim_warps();
-int sim_occupancy();
-int ia_occupancy();
 int ie_occupancy();
 
 }  // namespace insp
