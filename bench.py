@@ -254,8 +254,9 @@ def run_ours(args, rank, world, local_rank):
         _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
 
     # launch shapes picked on this batch before the timed region (setup, like the load)
-    tuning = _lib.insp_batch_autotune(b.handle, stream).as_dict() if args.autotune else \
-        _lib.insp_batch_get_tuning(b.handle).as_dict()
+    t_struct = _lib.insp_batch_autotune(b.handle, stream) if args.autotune else _lib.insp_batch_get_tuning(b.handle)
+    _lib.insp_machine_set_tuning(machine.handle, t_struct)  # batches loaded later (the e2e leg) start with it
+    tuning = t_struct.as_dict()
     sizes = batch.sizes()
     ia_bins = 1 if tuning["ia_bin_tasks"] <= 0 else \
         int((sizes >= tuning["ia_bin_tasks"]).any()) + int((sizes < tuning["ia_bin_tasks"]).any())

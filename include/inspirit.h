@@ -228,10 +228,11 @@ int insp_batch_replay(insp_batch *b, void *stream);
  * concurrently, each with its own warps per CTA. */
 typedef struct {
     int32_t ia_bin_tasks;    /* DAGs with at least this many tasks form the large bin (0: all in one bin) */
-    int32_t ia_warps_small;  /* warps per CTA of the ability sweep, small bin (1..16) */
-    int32_t ia_warps_large;  /* warps per CTA of the ability sweep, large bin (1..16) */
-    int32_t ie_warps;        /* warps per CTA of the efficiency sweep (1..8) */
-    int32_t ie_ring_mb;      /* L2 budget of the efficiency sweep's window rings, MB (>= 1) */
+    int32_t ia_warps_small;  /* warps per CTA of the ability sweep, small bin (1..32) */
+    int32_t ia_warps_large;  /* warps per CTA of the ability sweep, large bin (1..32) */
+    int32_t ie_warps;        /* warps per CTA of the efficiency sweep (1..16) */
+    int32_t ie_ring_mb;      /* device memory for the efficiency sweep's window rings, MB (1..65536); it
+                                bounds the warps in flight, and rings beyond L2 spill to HBM */
     int32_t sim_warps;       /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
     int32_t sim_queue;       /* ready-pool entries per warp kept in shared memory: 32, 64 or 128 */
 } insp_tuning;
@@ -241,9 +242,14 @@ typedef struct {
  * keep the fastest per kernel and return it in *chosen (may be NULL).  The
  * results of later calls do not depend on the tuning.  Synchronous. */
 int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chosen);
-/* Set or read the tuning explicitly (set: INSP_EINVAL on out-of-range fields). */
+/* Set or read the tuning explicitly (set: INSP_EINVAL on out-of-range fields;
+ * may allocate, INSP_ENOMEM).  insp_machine_set_tuning sets the tuning that
+ * batches loaded later on the machine start with (the default is the library's
+ * fixed choice), e.g. one found by insp_batch_autotune on a batch of the same
+ * shape. */
 int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t);
 int insp_batch_get_tuning(const insp_batch *b, insp_tuning *t);
+int insp_machine_set_tuning(insp_machine *m, const insp_tuning *t);
 
 /* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
  * call on the batch records CUDA events on its stream around each kernel.

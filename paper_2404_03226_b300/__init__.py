@@ -33,6 +33,10 @@ class Machine:
         self.n_cpu, self.n_gpu, self.xfer_ns = n_cpu, n_gpu, xfer_ns
         self.handle = _lib.insp_machine_create(n_cpu, n_gpu, xfer_ns, policy)
 
+    def set_tuning(self, t: dict) -> None:
+        """Launch shapes that batches loaded later on this machine start with."""
+        _lib.insp_machine_set_tuning(self.handle, insp_tuning(**t))
+
     def __del__(self):
         h = getattr(self, "handle", None)
         if h:

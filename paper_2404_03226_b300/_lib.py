@@ -70,6 +70,7 @@ _PROTOS = {
     "insp_batch_autotune": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(insp_tuning)]),
     "insp_batch_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(insp_tuning)]),
     "insp_batch_get_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(insp_tuning)]),
+    "insp_machine_set_tuning": (ctypes.c_int, [_vp, ctypes.POINTER(insp_tuning)]),
     "insp_simulate_noalloc": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _i32, _i32, _i64,
                                              ctypes.POINTER(insp_policy), _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
 }
@@ -276,3 +277,7 @@ def insp_batch_get_tuning(b) -> insp_tuning:
     t = insp_tuning()
     check(lib().insp_batch_get_tuning(b, ctypes.byref(t)))
     return t
+
+
+def insp_machine_set_tuning(m, t: insp_tuning) -> None:
+    check(lib().insp_machine_set_tuning(m, ctypes.byref(t)))

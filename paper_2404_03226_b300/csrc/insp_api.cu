@@ -85,8 +85,9 @@ int device_info(DeviceInfo &di) {
 const insp_tuning kDefaultTuning = {0, 8, 8, 4, 64, 8, 64};
 
 bool tuning_ok(const insp_tuning &t) {
-    return t.ia_bin_tasks >= 0 && t.ia_warps_small >= 1 && t.ia_warps_small <= 16 && t.ia_warps_large >= 1 &&
-           t.ia_warps_large <= 16 && t.ie_warps >= 1 && t.ie_warps <= 8 && t.ie_ring_mb >= 1 && t.sim_warps >= 1 &&
+    return t.ia_bin_tasks >= 0 && t.ia_warps_small >= 1 && t.ia_warps_small <= 32 && t.ia_warps_large >= 1 &&
+           t.ia_warps_large <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
+           t.ie_ring_mb <= 65536 && t.sim_warps >= 1 &&
            t.sim_warps <= 8 && (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128);
 }
 
@@ -100,6 +101,7 @@ struct Scratch {
     DBuf ia_bits, ia_done;                                         // inspiring ability
     DBuf ie_rec, ie_acc;                                           // inspiring efficiency
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
+    DBuf ie_ring;  // per-warp window rings of the pull efficiency sweep (global, meant to stay in L2)
     DBuf step;              // insp::StepCounters (device-side epoch and record tags)
 };
 
@@ -110,6 +112,7 @@ struct insp_machine {
     bool has_scorer = false;
     DBuf scorer;  // insp::ScorerPacked in device memory
     std::vector<std::unique_ptr<Scratch>> spare;
+    insp_tuning tun = kDefaultTuning;  // the tuning batches loaded on this machine start with
 };
 
 enum { TK_IA = 0, TK_IE = 1, TK_SIM = 2, TK_SIM_SINGLE = 3, TK_N = 4 };
@@ -125,8 +128,8 @@ struct insp_batch {
     DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
     DBuf pr_ptr, pcol;      // predecessor lists (pull form of the efficiency sweep)
-    int grid_ie_pull = 0;   // > 0: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
-    DBuf ie_ring;           // per-warp rings of the pull sweep (global, L2-resident)
+    bool pull = false;      // predecessor lists built: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
+    int grid_ie_pull = 0;   // its grid for the current tuning
     DBuf item_dag;          // DAG of every 32-source work item
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
@@ -238,11 +241,8 @@ int alloc_pull_ring(insp_batch *b) {
     const int64_t ring = insp::ie_pull_ring_bytes(b->W);
     const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(b->tun.ie_ring_mb) << 20) / (ring * wpc));
     b->grid_ie_pull = int(std::max<int64_t>(1, std::min({int64_t(di.sms) * occ, (b->n_items + wpc - 1) / wpc, l2_ctas})));
-    if ((rc = b->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring))) return rc;
-    // row W of every ring is the all -1 row predecessors older than the sources read
-    std::vector<int32_t> h(b->ie_ring.bytes / 4, -1);
-    CU(cudaMemcpy(b->ie_ring.p, h.data(), h.size() * 4, cudaMemcpyHostToDevice));
-    return INSP_OK;
+    // (the kernel writes every ring row before reading it, row W included)
+    return b->sc->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring);
 }
 
 int alloc_scratch(insp_batch *b) {
@@ -278,7 +278,7 @@ int alloc_scratch(insp_batch *b) {
     // inspiring efficiency: global-memory sweep scratch unless the pull form applies
     // (allocated later if a call needs the global form)
     b->ie_rec_stride = std::max<int32_t>(b->max_n, 1);
-    return b->grid_ie_pull > 0 ? INSP_OK : alloc_ie_global(b);
+    return b->pull ? alloc_pull_ring(b) : alloc_ie_global(b);
 }
 
 // Scratch of the global-memory inspiring-efficiency sweep: per warp one record
@@ -483,6 +483,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
     b->owner = m;
+    b->tun = m->tun;
     b->mach_params.n_cpu = m->n_cpu;
     b->mach_params.n_gpu = m->n_gpu;
     b->mach_params.xfer = m->xfer;
@@ -585,7 +586,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
                                  b->pcol.as<int32_t>(), grid, 0);
         if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
             return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
-        if ((rc = alloc_pull_ring(b))) return bail(rc);
+        b->pull = true;
     }
     if ((rc = alloc_scratch(b))) return bail(rc);
     *out = b;
@@ -667,7 +668,7 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     if (b->ndag == 0) return INSP_OK;
     CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
     CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
-    const bool pull = !wide && b->grid_ie_pull > 0;
+    const bool pull = !wide && b->pull;
     if (!pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
     insp::StepCounters *sc = S.step.as<insp::StepCounters>();
     insp::launch_step_begin(sc, b->n_items, s);
@@ -700,7 +701,7 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
         TimedLaunch tl(b, TK_IE, s);
         if (pull)
             insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
-                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, b->ie_ring.as<int32_t>(),
+                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, S.ie_ring.as<int32_t>(),
                                  d_ie, b->grid_ie_pull, b->tun.ie_warps, s);
         else
             insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
@@ -884,7 +885,7 @@ INSP_API int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t 
     if (b->mach.pol.policy == INSP_POLICY_LEARNED && !(b->owner && b->owner->has_scorer))
         return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
     // scratch the step may need is allocated before recording
-    if (b->grid_ie_pull == 0 && !b->ie_global_ready) {
+    if (!b->pull && !b->ie_global_ready) {
         int rc = alloc_ie_global(b);
         if (rc) return rc;
     }
@@ -933,7 +934,7 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
     if (old.ia_bin_tasks != t->ia_bin_tasks || old.ia_warps_small != t->ia_warps_small ||
         old.ia_warps_large != t->ia_warps_large)
         rc = alloc_ia(b);
-    if (rc == INSP_OK && b->grid_ie_pull > 0 && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
+    if (rc == INSP_OK && b->pull && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
         rc = alloc_pull_ring(b);
     if (rc != INSP_OK) b->tun = old;
     if (b->graph) {  // a recorded step holds the old launch shapes
@@ -941,6 +942,13 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
         b->graph = nullptr;
     }
     return rc;
+}
+
+INSP_API int insp_machine_set_tuning(insp_machine *m, const insp_tuning *t) {
+    if (!m || !t) return fail(INSP_EINVAL, "NULL argument");
+    if (!tuning_ok(*t)) return fail(INSP_EINVAL, "tuning field out of range");
+    m->tun = *t;
+    return INSP_OK;
 }
 
 INSP_API int insp_batch_get_tuning(const insp_batch *b, insp_tuning *t) {
@@ -1002,7 +1010,8 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     };
     // 1. ability sweep: size bins and CTA sizes (efficiency sweep at its current shape)
     std::vector<insp_tuning> c_ia;
-    const int ia_choice[][3] = {{0, 8, 8}, {0, 16, 16}, {0, 4, 4}, {1024, 4, 16}, {1024, 8, 16}, {512, 4, 8}};
+    const int ia_choice[][3] = {{0, 8, 8},     {0, 16, 16},    {0, 32, 32},
+                                {1024, 8, 32}, {1024, 16, 32}, {512, 8, 16}};
     for (auto &x : ia_choice) {
         insp_tuning t = best;
         t.ia_bin_tasks = x[0]; t.ia_warps_small = x[1]; t.ia_warps_large = x[2];
@@ -1010,10 +1019,10 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     }
     rc = search(c_ia, 0);
     // 2. efficiency sweep: CTA size and ring budget (only the pull form has them)
-    if (rc == INSP_OK && b->grid_ie_pull > 0) {
+    if (rc == INSP_OK && b->pull) {
         std::vector<insp_tuning> c_ie;
-        for (int w : {2, 4, 8})
-            for (int mb : {32, 64, 128}) {
+        for (int w : {4, 8, 16})
+            for (int mb : {64, 128, 256, 512, 1024}) {
                 insp_tuning t = best;
                 t.ie_warps = w; t.ie_ring_mb = mb;
                 c_ie.push_back(t);
@@ -1024,7 +1033,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     if (rc == INSP_OK) {
         CU(cudaStreamSynchronize(s));
         std::vector<insp_tuning> c_sim;
-        for (int w : {4, 8})
+        for (int w : {2, 4, 8})
             for (int q : {32, 64, 128}) {
                 insp_tuning t = best;
                 t.sim_warps = w; t.sim_queue = q;

@@ -25,7 +25,7 @@
 
 namespace insp {
 
-constexpr int PULL_MAX_WARPS = 8;  // warps per CTA: blockDim / 32 (autotuned)
+constexpr int PULL_MAX_WARPS = 16;  // warps per CTA: blockDim / 32 (autotuned)
 constexpr int PCH = 32;      // tasks per staged chunk
 constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
@@ -197,6 +197,7 @@ int64_t ie_pull_ring_bytes(int32_t W) { return ie_ring_bytes(W); }
 int ie_pull_occupancy(int warps) {
     const int64_t bytes = IE_PULL_STAGE_BYTES * warps;
     int nb = 0;
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, warps * 32, size_t(bytes)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -207,6 +208,7 @@ int ie_pull_occupancy(int warps) {
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
                     int32_t *gring, int32_t *ie, int grid, int warps, cudaStream_t s) {
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
     k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
                                                                            n_items, counter, unit_time, W, gring, ie);
 }
