@@ -141,8 +141,10 @@ struct insp_batch {
     int32_t ia_split = 0;                    // DAGs order[0, ia_split) form the large bin
     int64_t ia_slot_large = 1, ia_slot_small = 1;  // bitset words per CTA slot
     int grid_ia_large = 0, grid_ia_small = 0;
-    cudaStream_t side = nullptr;             // second stream of the concurrent bins
-    cudaEvent_t fork = nullptr, join = nullptr;
+    // side streams: the ability sweep's small bin and the efficiency sweep run
+    // concurrently with the ability sweep's large bin (the three are independent)
+    cudaStream_t side = nullptr, side_ie = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr, join_ie = nullptr;
     bool ie_global_ready = false;
     int grid_ie = 1;
     cudaStream_t last_stream = nullptr;
@@ -158,7 +160,9 @@ struct insp_batch {
         if (graph) cudaGraphExecDestroy(graph);
         if (fork) cudaEventDestroy(fork);
         if (join) cudaEventDestroy(join);
+        if (join_ie) cudaEventDestroy(join_ie);
         if (side) cudaStreamDestroy(side);
+        if (side_ie) cudaStreamDestroy(side_ie);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
     }
@@ -222,10 +226,12 @@ int alloc_ia(insp_batch *b) {
     }
     b->grid_ia_large = int(gl);
     b->grid_ia_small = int(gs);
-    if (gl > 0 && gs > 0 && !b->side) {  // the side stream of the concurrent bins
+    if (!b->side) {
         CU(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        CU(cudaStreamCreateWithFlags(&b->side_ie, cudaStreamNonBlocking));
         CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&b->join_ie, cudaEventDisableTiming));
     }
     return S.ia_bits.alloc(size_t(gl * b->ia_slot_large + gs * b->ia_slot_small) * 4 + 16);
 }
@@ -674,17 +680,27 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     insp::launch_step_begin(sc, b->n_items, s);
     insp::DevBatch B = b->dev();
     int32_t *ctr = b->counters.as<int32_t>();
+    // the ability sweep's two size bins and the efficiency sweep are independent:
+    // large bin on s, small bin on side, efficiency on side_ie, joined back into s
+    const bool two = b->grid_ia_large > 0 && b->grid_ia_small > 0;
+    CU(cudaEventRecord(b->fork, s));
+    CU(cudaStreamWaitEvent(b->side_ie, b->fork, 0));
+    if (two) CU(cudaStreamWaitEvent(b->side, b->fork, 0));
     {
-        // the two size bins of the ability sweep run concurrently (large bin on s, small on a side stream)
+        TimedLaunch tl(b, TK_IE, b->side_ie);
+        if (pull)
+            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
+                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, S.ie_ring.as<int32_t>(),
+                                 d_ie, b->grid_ie_pull, b->tun.ie_warps, b->side_ie);
+        else
+            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
+                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, b->side_ie);
+    }
+    {
         TimedLaunch tl(b, TK_IA, s);
         const int32_t *ord = b->order.as<int32_t>();
         uint32_t *bits = S.ia_bits.as<uint32_t>();
         uint32_t *bits_small = bits + int64_t(b->grid_ia_large) * b->ia_slot_large;
-        const bool two = b->grid_ia_large > 0 && b->grid_ia_small > 0;
-        if (two) {
-            CU(cudaEventRecord(b->fork, s));
-            CU(cudaStreamWaitEvent(b->side, b->fork, 0));
-        }
         if (b->grid_ia_large > 0)
             insp::launch_ia(B, ord, b->ia_split, ctr + 0, bits, b->ia_slot_large, S.ia_done.as<int32_t>(), &sc->epoch,
                             d_ia, b->status.as<int32_t>(), b->grid_ia_large, b->tun.ia_warps_large, s);
@@ -697,16 +713,8 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
             CU(cudaStreamWaitEvent(s, b->join, 0));
         }
     }
-    {
-        TimedLaunch tl(b, TK_IE, s);
-        if (pull)
-            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
-                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, S.ie_ring.as<int32_t>(),
-                                 d_ie, b->grid_ie_pull, b->tun.ie_warps, s);
-        else
-            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
-                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, s);
-    }
+    CU(cudaEventRecord(b->join_ie, b->side_ie));
+    CU(cudaStreamWaitEvent(s, b->join_ie, 0));
     CU(cudaGetLastError());
     if (st_ia || st_ie) {
         if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
