@@ -112,7 +112,7 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- roofline
 def algorithmic_bytes(batch):
-    """Minimal HBM bytes per launch of each kernel: inputs read once, outputs
+    """Minimal HBM bytes per step of each kernel (all its launches): inputs read once, outputs
     written once (scratch excluded).  Costs: 1 byte of type per task with
     per-type tables, or 8 (GPU cost) / 16 (both costs) bytes with per-task costs."""
     n, m, nd = batch.n_total, batch.m_total, batch.ndag
@@ -249,17 +249,13 @@ def run_ours(args, rank, world, local_rank):
     end = torch.empty(n, dtype=torch.int64, device=dev)
     mk = torch.empty(ndag, dtype=torch.int64, device=dev)
 
-    def step():
-        _lib.insp_attributes_batch(b.handle, None, ia, ie, stream)
-        _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
+    def step():  # attributes + schedule of every DAG, pipelined by size groups
+        _lib.insp_evaluate_batch(b.handle, None, ia, ie, worker, start, end, mk, stream)
 
     # launch shapes picked on this batch before the timed region (setup, like the load)
     t_struct = _lib.insp_batch_autotune(b.handle, stream) if args.autotune else _lib.insp_batch_get_tuning(b.handle)
     _lib.insp_machine_set_tuning(machine.handle, t_struct)  # batches loaded later (the e2e leg) start with it
     tuning = t_struct.as_dict()
-    sizes = batch.sizes()
-    ia_bins = 1 if tuning["ia_bin_tasks"] <= 0 else \
-        int((sizes >= tuning["ia_bin_tasks"]).any()) + int((sizes < tuning["ia_bin_tasks"]).any())
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -319,7 +315,9 @@ def run_ours(args, rank, world, local_rank):
     share = {names[k]: kms[k] / max(kms[:3].sum(), 1e-9) for k in range(3)}
     dom = max(names, key=lambda k: share[k])
     peak, peak_kind = load_peaks()
-    achieved = alg[dom] / (per_launch_ms[dom] / 1e3) / 1e9
+    # algorithmic bytes of all the kernel's launches in the timed region over their summed
+    # durations (= bytes per launch / mean launch time; one launch per size group and step)
+    achieved = alg[dom] * args.steps / (kms[names.index(dom)] / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_from_profile(dom), "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
                 "kernel_ms": {k: round(v, 4) for k, v in per_launch_ms.items()},
@@ -386,8 +384,8 @@ def run_ours(args, rank, world, local_rank):
             h = _lib.insp_batch_load_csr(machine.handle, ndag, h_tb, h_eb, h_rp, h_ci, h_ty, batch.n_types, h_tc,
                                          h_kc)
             try:
-                _lib.insp_attributes_batch(h, None, ia, ie, stream)
-                _lib.insp_simulate_batch(h, ia, ie, o_w, o_s, o_e, o_m, stream)  # host outputs: D2H + sync
+                # schedule to pinned host arrays (D2H + sync inside); ia / ie stay on the device
+                _lib.insp_evaluate_batch(h, None, ia, ie, o_w, o_s, o_e, o_m, stream)
             finally:
                 _lib.insp_batch_destroy(h)
 
@@ -422,9 +420,9 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cb,
             "clocks": clk,
             # our kernels in the timed region: ability, efficiency, simulation, plus one
-            # step-counter kernel per attributes call; the ability sweep is one launch per
-            # non-empty size bin
-            "gpu_launches": int(klaunch[:3].sum() + klaunch[0] * (ia_bins - 1) + klaunch[0]),
+            # step-counter kernel per step; ability, efficiency and simulation kernels once
+            # per size group
+            "gpu_launches": int(klaunch[:3].sum() + args.steps),
         }
         print(json.dumps(res), flush=True)
     if dist is not None:

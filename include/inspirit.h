@@ -149,6 +149,18 @@ int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *wo
 int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
                         int64_t *end, int64_t *makespan, void *stream);
 
+/* The whole evaluation step: insp_attributes_batch, then insp_simulate_batch
+ * with its results, in one call with the same outputs.  With device arrays the
+ * step is pipelined (the batch's tuning, field groups): the DAGs are cut into
+ * size groups along descending size, and the simulation of a group starts on
+ * its own stream once the group's attributes are done, concurrently with the
+ * attribute sweeps of the later groups.  Outputs may be device or host arrays
+ * (host arrays are staged through library-owned device memory; the call then
+ * synchronises `stream` and returns the first per-DAG status).  Stream-ordered
+ * on `stream`.  Errors: as the two calls. */
+int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
+                        int64_t *start, int64_t *end, int64_t *makespan, void *stream);
+
 /* The same simulation launched once per DAG (one warp on the GPU per launch,
  * serial on `stream`): the unbatched form used as the throughput baseline. */
 int insp_simulate_per_dag(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
@@ -222,25 +234,25 @@ int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t *worker, 
 int insp_batch_replay(insp_batch *b, void *stream);
 
 /* ------------------------------------------------------------- tuning
- * Launch shapes of the batched kernels, picked per batch by the library's own
- * autotuner (no counterpart in the paper).  The inspiring-ability sweep splits
- * the DAGs into two size bins at ia_bin_tasks (0: one bin) that run
- * concurrently, each with its own warps per CTA. */
+ * Launch shapes of the batched kernels and the pipelining of the evaluation
+ * step, picked per batch by the library's own autotuner (no counterpart in the
+ * paper).  None of them changes a result. */
 typedef struct {
-    int32_t ia_bin_tasks;    /* DAGs with at least this many tasks form the large bin (0: all in one bin) */
-    int32_t ia_warps_small;  /* warps per CTA of the ability sweep, small bin (1..32) */
-    int32_t ia_warps_large;  /* warps per CTA of the ability sweep, large bin (1..32) */
-    int32_t ie_warps;        /* warps per CTA of the efficiency sweep (1..16) */
-    int32_t ie_ring_mb;      /* device memory for the efficiency sweep's window rings, MB (1..65536); it
-                                bounds the warps in flight, and rings beyond L2 spill to HBM */
-    int32_t sim_warps;       /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
-    int32_t sim_queue;       /* ready-pool entries per warp kept in shared memory: 32, 64 or 128 */
+    int32_t groups;        /* size groups of insp_evaluate_batch (1..16; 1: all attributes, then the simulation) */
+    int32_t attr_overlap;  /* 1: ability and efficiency sweeps on two streams, concurrently; 0: one after the other */
+    int32_t ia_warps;      /* warps per CTA of the ability sweep (1..32) */
+    int32_t ie_warps;      /* warps per CTA of the efficiency sweep (1..16) */
+    int32_t ie_ring_mb;    /* device memory for the efficiency sweep's window rings, MB (1..65536); it
+                              bounds the warps in flight, and rings beyond L2 spill to HBM */
+    int32_t sim_warps;     /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
+    int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64 or 128 */
 } insp_tuning;
 
-/* Time a fixed candidate set of launch shapes on this batch (one step each
- * after a warm-up, CUDA events on `stream`; device pointers are not needed),
- * keep the fastest per kernel and return it in *chosen (may be NULL).  The
- * results of later calls do not depend on the tuning.  Synchronous. */
+/* Time a fixed candidate set of tunings on this batch (one insp_evaluate_batch
+ * step each after a warm-up step, CUDA events on `stream`; the library's own
+ * scratch holds the outputs), in a coordinate search over the fields, keep the
+ * fastest and return it in *chosen (may be NULL).  The results of later calls
+ * do not depend on the tuning.  Synchronous. */
 int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chosen);
 /* Set or read the tuning explicitly (set: INSP_EINVAL on out-of-range fields;
  * may allocate, INSP_ENOMEM).  insp_machine_set_tuning sets the tuning that

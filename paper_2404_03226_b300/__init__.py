@@ -95,6 +95,18 @@ class DagBatch:
         f(self.handle, ia, ie, sch.worker, sch.start, sch.end, sch.makespan, stream or torch.cuda.current_stream())
         return sch
 
+    def evaluate(self, unit_time_ns=None, stream=None):
+        """Attributes and schedule in one pipelined call: (ia, ie, Schedule)."""
+        import torch
+        ia = self._out(self.n_tasks, torch.int32)
+        ie = self._out(self.n_tasks, torch.int32)
+        sch = Schedule(self._out(self.n_tasks, torch.int32), self._out(self.n_tasks, torch.int64),
+                       self._out(self.n_tasks, torch.int64), self._out(self.ndag, torch.int64))
+        ut = None if unit_time_ns is None else _np(unit_time_ns, np.int64)
+        _lib.insp_evaluate_batch(self.handle, ut, ia, ie, sch.worker, sch.start, sch.end, sch.makespan,
+                                 stream or torch.cuda.current_stream())
+        return ia, ie, sch
+
     def autotune(self, stream=None) -> dict:
         """Time the library's candidate launch shapes on this batch and keep the
         fastest per kernel; returns the chosen tuning as a dict."""

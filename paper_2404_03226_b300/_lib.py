@@ -24,7 +24,7 @@ class insp_policy(ctypes.Structure):
 
 
 class insp_tuning(ctypes.Structure):
-    _fields_ = [("ia_bin_tasks", _i32), ("ia_warps_small", _i32), ("ia_warps_large", _i32), ("ie_warps", _i32),
+    _fields_ = [("groups", _i32), ("attr_overlap", _i32), ("ia_warps", _i32), ("ie_warps", _i32),
                 ("ie_ring_mb", _i32), ("sim_warps", _i32), ("sim_queue", _i32)]
 
     def as_dict(self):
@@ -53,6 +53,7 @@ _PROTOS = {
     "insp_attributes_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "insp_simulate": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_evaluate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -186,6 +187,11 @@ def insp_simulate(d, ia, ie, worker, start, end, makespan, stream=None) -> None:
 def insp_simulate_batch(b, ia, ie, worker, start, end, makespan, stream=None) -> None:
     check(lib().insp_simulate_batch(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
                                     stream_ptr(stream)))
+
+
+def insp_evaluate_batch(b, unit_time_ns, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    check(lib().insp_evaluate_batch(b, ptr(unit_time_ns), ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end),
+                                    ptr(makespan), stream_ptr(stream)))
 
 
 def insp_simulate_per_dag(b, ia, ie, worker, start, end, makespan, stream=None) -> None:

@@ -82,13 +82,14 @@ int device_info(DeviceInfo &di) {
     return INSP_OK;
 }
 
-const insp_tuning kDefaultTuning = {0, 8, 8, 4, 64, 8, 64};
+constexpr int MAX_GROUPS = 16;
+const insp_tuning kDefaultTuning = {4, 0, 32, 16, 512, 4, 64};
 
 bool tuning_ok(const insp_tuning &t) {
-    return t.ia_bin_tasks >= 0 && t.ia_warps_small >= 1 && t.ia_warps_small <= 32 && t.ia_warps_large >= 1 &&
-           t.ia_warps_large <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
-           t.ie_ring_mb <= 65536 && t.sim_warps >= 1 &&
-           t.sim_warps <= 8 && (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128);
+    return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
+           t.ia_warps >= 1 && t.ia_warps <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
+           t.ie_ring_mb <= 65536 && t.sim_warps >= 1 && t.sim_warps <= 8 &&
+           (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128);
 }
 
 }  // namespace
@@ -103,6 +104,33 @@ struct Scratch {
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
     DBuf ie_ring;  // per-warp window rings of the pull efficiency sweep (global, meant to stay in L2)
     DBuf step;              // insp::StepCounters (device-side epoch and record tags)
+    // streams and events of the pipelined step: q[0] runs the efficiency sweep
+    // when it overlaps the ability sweep, q[1 + g] the simulation of size group g
+    cudaStream_t q[1 + MAX_GROUPS] = {};
+    cudaEvent_t ev_ia[MAX_GROUPS] = {}, ev_ie[MAX_GROUPS] = {}, ev_sim[MAX_GROUPS] = {}, ev_fork = nullptr;
+    bool streams_ready = false;
+    int make_streams() {
+        if (streams_ready) return INSP_OK;
+        for (auto &x : q) CU(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        for (int g = 0; g < MAX_GROUPS; ++g) {
+            CU(cudaEventCreateWithFlags(&ev_ia[g], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&ev_ie[g], cudaEventDisableTiming));
+            CU(cudaEventCreateWithFlags(&ev_sim[g], cudaEventDisableTiming));
+        }
+        CU(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+        streams_ready = true;
+        return INSP_OK;
+    }
+    ~Scratch() {
+        for (auto x : q)
+            if (x) cudaStreamDestroy(x);
+        for (int g = 0; g < MAX_GROUPS; ++g) {
+            if (ev_ia[g]) cudaEventDestroy(ev_ia[g]);
+            if (ev_ie[g]) cudaEventDestroy(ev_ie[g]);
+            if (ev_sim[g]) cudaEventDestroy(ev_sim[g]);
+        }
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
 };
 
 struct insp_machine {
@@ -130,7 +158,9 @@ struct insp_batch {
     DBuf pr_ptr, pcol;      // predecessor lists (pull form of the efficiency sweep)
     bool pull = false;      // predecessor lists built: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
     int grid_ie_pull = 0;   // its grid for the current tuning
-    DBuf item_dag;          // DAG of every 32-source work item
+    DBuf item_dag;          // DAG of every 32-source work item (items numbered by DAG id)
+    DBuf item_dag_lpt, item_base_lpt;  // the same items numbered along the size order (pull sweep)
+    std::vector<int64_t> h_rank_item;  // first item (size-order numbering) of the DAG at each rank
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;
@@ -138,13 +168,8 @@ struct insp_batch {
     int64_t ie_rec_stride = 0;
     // tuning and the launch shapes derived from it
     insp_tuning tun = kDefaultTuning;
-    int32_t ia_split = 0;                    // DAGs order[0, ia_split) form the large bin
-    int64_t ia_slot_large = 1, ia_slot_small = 1;  // bitset words per CTA slot
-    int grid_ia_large = 0, grid_ia_small = 0;
-    // side streams: the ability sweep's small bin and the efficiency sweep run
-    // concurrently with the ability sweep's large bin (the three are independent)
-    cudaStream_t side = nullptr, side_ie = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr, join_ie = nullptr;
+    int64_t ia_slot = 1;  // bitset words per CTA slot of the ability sweep
+    int grid_ia = 0;
     bool ie_global_ready = false;
     int grid_ie = 1;
     cudaStream_t last_stream = nullptr;
@@ -158,11 +183,6 @@ struct insp_batch {
 
     ~insp_batch() {
         if (graph) cudaGraphExecDestroy(graph);
-        if (fork) cudaEventDestroy(fork);
-        if (join) cudaEventDestroy(join);
-        if (join_ie) cudaEventDestroy(join_ie);
-        if (side) cudaStreamDestroy(side);
-        if (side_ie) cudaStreamDestroy(side_ie);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
     }
@@ -194,46 +214,19 @@ int copy_in(DBuf &dst, const void *src, size_t bytes) {
 int alloc_ie_global(insp_batch *b);
 
 // Inspiring-ability scratch for the current tuning: one bitset slot per CTA,
-// sized by the largest DAG of its bin (rows of n tasks x ceil(n/32) words).
+// sized by the largest DAG (rows of n tasks x ceil(n/32) words).
 int alloc_ia(insp_batch *b) {
     DeviceInfo di;
     int rc = device_info(di);
     if (rc) return rc;
-    Scratch &S = *b->sc;
-    auto size_of = [&](int k) { return b->h_task_base[b->h_order[k] + 1] - b->h_task_base[b->h_order[k]]; };
-    int32_t split = 0;  // h_order is by descending size
-    if (b->tun.ia_bin_tasks <= 0) split = b->ndag;
-    else
-        while (split < b->ndag && size_of(split) >= b->tun.ia_bin_tasks) ++split;
-    b->ia_split = split;
+    const int64_t n = b->max_n;
+    b->ia_slot = std::max<int64_t>(n * ((n + 31) / 32), 1);
+    const int occ = std::max(1, insp::ia_occupancy(b->tun.ia_warps));
     const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
-    auto slot_words = [&](int k) {
-        const int64_t n = k < b->ndag ? size_of(k) : 0;
-        return std::max<int64_t>(n * ((n + 31) / 32), 1);
-    };
-    b->ia_slot_large = slot_words(0);
-    b->ia_slot_small = slot_words(split);
-    const int occ_l = std::max(1, insp::ia_occupancy(b->tun.ia_warps_large));
-    const int occ_s = std::max(1, insp::ia_occupancy(b->tun.ia_warps_small));
-    const int64_t n_large = split, n_small = b->ndag - split;
-    int64_t gl = std::min<int64_t>(int64_t(di.sms) * occ_l, n_large);
-    int64_t gs = std::min<int64_t>(int64_t(di.sms) * occ_s, n_small);
-    const int64_t need_l = gl * b->ia_slot_large * 4, need_s = gs * b->ia_slot_small * 4;
-    if (need_l + need_s > budget) {  // shrink both bins' grids in proportion
-        const double f = double(budget) / double(need_l + need_s);
-        gl = n_large ? std::max<int64_t>(1, int64_t(gl * f)) : 0;
-        gs = n_small ? std::max<int64_t>(1, int64_t(gs * f)) : 0;
-    }
-    b->grid_ia_large = int(gl);
-    b->grid_ia_small = int(gs);
-    if (!b->side) {
-        CU(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
-        CU(cudaStreamCreateWithFlags(&b->side_ie, cudaStreamNonBlocking));
-        CU(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
-        CU(cudaEventCreateWithFlags(&b->join_ie, cudaEventDisableTiming));
-    }
-    return S.ia_bits.alloc(size_t(gl * b->ia_slot_large + gs * b->ia_slot_small) * 4 + 16);
+    int64_t g = std::min<int64_t>(int64_t(di.sms) * occ, b->ndag);
+    g = std::max<int64_t>(1, std::min(g, budget / (b->ia_slot * 4)));
+    b->grid_ia = int(g);
+    return b->sc->ia_bits.alloc(size_t(g * b->ia_slot) * 4 + 16);
 }
 
 // Window rings of the pull efficiency sweep for the current tuning (L2 budget).
@@ -280,6 +273,7 @@ int alloc_scratch(insp_batch *b) {
         const insp::StepCounters c0{0, 0, 1};  // epoch 0 is never published; tag 0 marks empty records
         CU(cudaMemcpy(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice));
     }
+    if ((rc = S.make_streams())) return rc;
     if ((rc = alloc_ia(b))) return rc;
     // inspiring efficiency: global-memory sweep scratch unless the pull form applies
     // (allocated later if a call needs the global form)
@@ -535,7 +529,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     }
     if ((rc = b->indeg0.alloc(std::max<int64_t>(b->n_total, 1) * 4)) ||
         (rc = b->unit_time_def.alloc(std::max(ndag, 1) * 8)) || (rc = b->unit_time_user.alloc(std::max(ndag, 1) * 8)) ||
-        (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(64)))
+        (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(512)))
         return bail(rc);
     if (cudaMemset(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4) != cudaSuccess ||
         cudaMemset(b->max_span.p, 0, 4) != cudaSuccess)
@@ -578,9 +572,21 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     std::vector<int32_t> idag(std::max<int64_t>(b->n_items, 1));
     for (int d = 0; d < ndag; ++d)
         for (int64_t k = items[d]; k < items[d + 1]; ++k) idag[k] = d;
+    // the same items numbered along the size order: a size group's items are a contiguous range
+    b->h_rank_item.assign(ndag + 1, 0);
+    std::vector<int64_t> base_lpt(std::max(ndag, 1), 0);
+    std::vector<int32_t> idag_lpt(std::max<int64_t>(b->n_items, 1));
+    for (int r = 0; r < ndag; ++r) {
+        const int d = order[r];
+        base_lpt[d] = b->h_rank_item[r];
+        b->h_rank_item[r + 1] = b->h_rank_item[r] + (items[d + 1] - items[d]);
+        for (int64_t k = b->h_rank_item[r]; k < b->h_rank_item[r + 1]; ++k) idag_lpt[k] = d;
+    }
     if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4)) ||
         (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)) ||
-        (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)))
+        (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)) ||
+        (rc = copy_in(b->item_base_lpt, base_lpt.data(), base_lpt.size() * 8)) ||
+        (rc = copy_in(b->item_dag_lpt, idag_lpt.data(), idag_lpt.size() * 4)))
         return bail(rc);
     // pull form of the efficiency sweep when its window is at most IE_PULL_MAX_W
     if (b->W <= insp::IE_PULL_MAX_W && ndag > 0) {
@@ -635,6 +641,77 @@ INSP_API int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_task
     return INSP_OK;
 }
 
+namespace {
+
+// The per-DAG unit time T of the efficiency sweep: the defaults, or the
+// caller's array (entries <= 0 take the default).  *wide: some T >= 2^31.
+int prep_unit_time(insp_batch *b, const int64_t *unit_time_ns, cudaStream_t s, const int64_t *&ut, bool &wide) {
+    ut = b->unit_time_def.as<int64_t>();
+    wide = b->max_unit_def >= 0x7fffffffLL;
+    if (!unit_time_ns) return INSP_OK;
+    if (is_device_ptr(unit_time_ns)) {
+        CU(cudaMemcpyAsync(b->unit_time_user.p, unit_time_ns, size_t(b->ndag) * 8, cudaMemcpyDeviceToDevice, s));
+        wide = true;
+    } else {
+        std::vector<int64_t> h(unit_time_ns, unit_time_ns + b->ndag);
+        std::vector<int64_t> def(std::max(b->ndag, 1));
+        bool need_def = false;
+        for (auto v : h) need_def |= v <= 0;
+        if (need_def && b->ndag)
+            CU(cudaMemcpy(def.data(), b->unit_time_def.p, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost));
+        int64_t mx = 1;
+        for (int d = 0; d < b->ndag; ++d) {
+            if (h[d] <= 0) h[d] = def[d];
+            mx = std::max(mx, h[d]);
+        }
+        wide = mx >= 0x7fffffffLL;
+        if (b->ndag)
+            CU(cudaMemcpyAsync(b->unit_time_user.p, h.data(), size_t(b->ndag) * 8, cudaMemcpyHostToDevice, s));
+        if (b->ndag) CU(cudaStreamSynchronize(s));  // h is a local vector
+    }
+    ut = b->unit_time_user.as<int64_t>();
+    return INSP_OK;
+}
+
+// The attribute sweeps of the DAGs at ranks [r0, r1) of the size order: the
+// ability sweep on s_ia, the efficiency sweep on s_ie (the two are
+// independent).  ctr: this launch pair's two work counters (zeroed).  The
+// global-memory efficiency sweep (wide unit times or long edges) only runs over
+// the whole batch.
+int launch_attr(insp_batch *b, int r0, int r1, int32_t *ctr, const int64_t *ut, bool pull, bool wide, int32_t *d_ia,
+                int32_t *d_ie, cudaStream_t s_ia, cudaStream_t s_ie) {
+    Scratch &S = *b->sc;
+    insp::StepCounters *sc = S.step.as<insp::StepCounters>();
+    const insp::DevBatch B = b->dev();
+    const int nd = r1 - r0;
+    if (nd <= 0) return INSP_OK;
+    {
+        TimedLaunch tl(b, TK_IA, s_ia);
+        insp::launch_ia(B, b->order.as<int32_t>() + r0, nd, ctr + 0, S.ia_bits.as<uint32_t>(), b->ia_slot,
+                        S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(),
+                        std::min(b->grid_ia, nd), b->tun.ia_warps, s_ia);
+    }
+    {
+        TimedLaunch tl(b, TK_IE, s_ie);
+        if (pull) {
+            const int64_t i0 = b->h_rank_item[r0], i1 = b->h_rank_item[r1];
+            const int wpc = b->tun.ie_warps;
+            const int grid = int(std::max<int64_t>(1, std::min<int64_t>(b->grid_ie_pull, (i1 - i0 + wpc - 1) / wpc)));
+            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base_lpt.as<int64_t>(),
+                                 b->item_dag_lpt.as<int32_t>(), i0, i1, ctr + 1, ut, b->W, S.ie_ring.as<int32_t>(),
+                                 d_ie, grid, wpc, s_ie);
+        } else {
+            if (r0 != 0 || r1 != b->ndag) return fail(INSP_EINVAL, "internal: global efficiency sweep over a part");
+            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 1, ut, S.ie_rec.as<uint4>(),
+                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, s_ie);
+        }
+    }
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
+}  // namespace
+
 INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
                                    void *stream) {
     if (!b || !ia || !ie) return fail(INSP_EINVAL, "NULL argument");
@@ -646,75 +723,27 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     bool st_ia, st_ie;
     Scratch &S = *b->sc;
     if ((rc = stage_out(S.s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(S.s_ie, ie, N, d_ie, st_ie))) return rc;
-    const int64_t *ut = b->unit_time_def.as<int64_t>();
-    bool wide = b->max_unit_def >= 0x7fffffffLL;
-    if (unit_time_ns) {
-        if (is_device_ptr(unit_time_ns)) {
-            CU(cudaMemcpyAsync(b->unit_time_user.p, unit_time_ns, size_t(b->ndag) * 8, cudaMemcpyDeviceToDevice, s));
-            wide = true;
-        } else {
-            std::vector<int64_t> h(unit_time_ns, unit_time_ns + b->ndag);
-            std::vector<int64_t> def(std::max(b->ndag, 1));
-            bool need_def = false;
-            for (auto v : h) need_def |= v <= 0;
-            if (need_def && b->ndag)
-                CU(cudaMemcpy(def.data(), b->unit_time_def.p, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost));
-            int64_t mx = 1;
-            for (int d = 0; d < b->ndag; ++d) {
-                if (h[d] <= 0) h[d] = def[d];
-                mx = std::max(mx, h[d]);
-            }
-            wide = mx >= 0x7fffffffLL;
-            if (b->ndag)
-                CU(cudaMemcpyAsync(b->unit_time_user.p, h.data(), size_t(b->ndag) * 8, cudaMemcpyHostToDevice, s));
-            if (b->ndag) CU(cudaStreamSynchronize(s));  // h is a local vector
-        }
-        ut = b->unit_time_user.as<int64_t>();
-    }
+    const int64_t *ut;
+    bool wide;
+    if ((rc = prep_unit_time(b, unit_time_ns, s, ut, wide))) return rc;
     if (b->ndag == 0) return INSP_OK;
-    CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
+    CU(cudaMemsetAsync(b->counters.p, 0, b->counters.bytes, s));
     CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
     const bool pull = !wide && b->pull;
     if (!pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
-    insp::StepCounters *sc = S.step.as<insp::StepCounters>();
-    insp::launch_step_begin(sc, b->n_items, s);
-    insp::DevBatch B = b->dev();
-    int32_t *ctr = b->counters.as<int32_t>();
-    // the ability sweep's two size bins and the efficiency sweep are independent:
-    // large bin on s, small bin on side, efficiency on side_ie, joined back into s
-    const bool two = b->grid_ia_large > 0 && b->grid_ia_small > 0;
-    CU(cudaEventRecord(b->fork, s));
-    CU(cudaStreamWaitEvent(b->side_ie, b->fork, 0));
-    if (two) CU(cudaStreamWaitEvent(b->side, b->fork, 0));
-    {
-        TimedLaunch tl(b, TK_IE, b->side_ie);
-        if (pull)
-            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base.as<int64_t>(),
-                                 b->item_dag.as<int32_t>(), b->n_items, ctr + 4, ut, b->W, S.ie_ring.as<int32_t>(),
-                                 d_ie, b->grid_ie_pull, b->tun.ie_warps, b->side_ie);
-        else
-            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ctr + 4, ut, S.ie_rec.as<uint4>(),
-                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, d_ie, b->grid_ie, b->side_ie);
+    insp::launch_step_begin(S.step.as<insp::StepCounters>(), b->n_items, s);
+    const bool ov = b->tun.attr_overlap != 0;
+    if (ov) {
+        CU(cudaEventRecord(S.ev_fork, s));
+        CU(cudaStreamWaitEvent(S.q[0], S.ev_fork, 0));
     }
-    {
-        TimedLaunch tl(b, TK_IA, s);
-        const int32_t *ord = b->order.as<int32_t>();
-        uint32_t *bits = S.ia_bits.as<uint32_t>();
-        uint32_t *bits_small = bits + int64_t(b->grid_ia_large) * b->ia_slot_large;
-        if (b->grid_ia_large > 0)
-            insp::launch_ia(B, ord, b->ia_split, ctr + 0, bits, b->ia_slot_large, S.ia_done.as<int32_t>(), &sc->epoch,
-                            d_ia, b->status.as<int32_t>(), b->grid_ia_large, b->tun.ia_warps_large, s);
-        if (b->grid_ia_small > 0)
-            insp::launch_ia(B, ord + b->ia_split, b->ndag - b->ia_split, ctr + 2, bits_small, b->ia_slot_small,
-                            S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(), b->grid_ia_small,
-                            b->tun.ia_warps_small, two ? b->side : s);
-        if (two) {
-            CU(cudaEventRecord(b->join, b->side));
-            CU(cudaStreamWaitEvent(s, b->join, 0));
-        }
+    if ((rc = launch_attr(b, 0, b->ndag, b->counters.as<int32_t>() + 16, ut, pull, wide, d_ia, d_ie, s,
+                          ov ? S.q[0] : s)))
+        return rc;
+    if (ov) {
+        CU(cudaEventRecord(S.ev_ie[0], S.q[0]));
+        CU(cudaStreamWaitEvent(s, S.ev_ie[0], 0));
     }
-    CU(cudaEventRecord(b->join_ie, b->side_ie));
-    CU(cudaStreamWaitEvent(s, b->join_ie, 0));
     CU(cudaGetLastError());
     if (st_ia || st_ie) {
         if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
@@ -741,6 +770,71 @@ struct Rollout {
     int32_t *feat_task = nullptr, *feat = nullptr, *feat_n = nullptr;
 };
 
+// Arguments of the simulation kernel over the whole batch (size order, counter 8).
+void fill_sim_args(insp_batch *b, insp::SimArgs &A, const int32_t *d_ia, const int32_t *d_ie, int32_t *d_worker,
+                   int64_t *d_start, int64_t *d_end, int64_t *d_mk, const Rollout &ro) {
+    const bool learned = b->mach.pol.policy == INSP_POLICY_LEARNED;
+    Scratch &S = *b->sc;
+    A.B = b->dev();
+    A.n_cpu = b->mach.n_cpu;
+    A.n_gpu = b->mach.n_gpu;
+    A.xfer = b->mach.xfer;
+    A.policy = b->mach.pol.policy;
+    A.task_window = b->mach.pol.task_window;
+    A.s_inc = b->mach.pol.s_inc;
+    A.s_dec = b->mach.pol.s_dec;
+    A.dec_step = b->mach.pol.dec_step;
+    A.c = b->mach.pol.c;
+    A.k_inc_tasks = b->mach.pol.k_inc_tasks;
+    A.k_inc_ns = b->mach.pol.k_inc_ns;
+    A.unit_time_def = b->unit_time_def.as<int64_t>();
+    A.indeg0 = b->indeg0.as<int32_t>();
+    A.ia = d_ia;
+    A.ie = d_ie;
+    A.worker = d_worker;
+    A.start = d_start;
+    A.end = d_end;
+    A.makespan = d_mk;
+    A.status = b->status.as<int32_t>();
+    A.st_a = S.st_a.as<int2>();
+    A.st_b = S.st_b.as<longlong2>();
+    A.p_idw = S.p_idw.as<int32_t>();
+    A.p_seq = S.p_seq.as<int32_t>();
+    A.p_ia = S.p_ia.as<int32_t>();
+    A.p_ie = S.p_ie.as<int32_t>();
+    A.p_dr = S.p_dr.as<int64_t>();
+    A.p_cost = S.p_cost.as<int64_t>();
+    A.nl = S.nl.as<int32_t>();
+    A.order = b->order.as<int32_t>();
+    A.counter = b->counters.as<int32_t>() + 8;
+    A.scorer = learned ? b->owner->scorer.as<insp::ScorerPacked>() : nullptr;
+    A.force_pop = ro.force_pop;
+    A.force_task = ro.force_task;
+    A.feat_pop = ro.feat_pop;
+    A.feat_cap = ro.feat_cap;
+    A.feat_task = ro.feat_task;
+    A.feat = ro.feat;
+    A.feat_n = ro.feat_n;
+    A.n_order = b->ndag;
+    A.single_dag = -1;
+}
+
+// The batched simulation of the DAGs A.order[0, A.n_order) on stream s.
+int launch_sim_part(insp_batch *b, const insp::SimArgs &A, cudaStream_t s) {
+    if (A.n_order <= 0) return INSP_OK;
+    TimedLaunch tl(b, TK_SIM, s);
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    const bool learned = A.policy == INSP_POLICY_LEARNED;
+    const int wpc = b->tun.sim_warps;
+    const int occ = std::max(1, insp::sim_occupancy(learned, wpc, b->tun.sim_queue));
+    const int grid = std::max(1, std::min(di.sms * occ, (A.n_order + wpc - 1) / wpc));
+    insp::launch_sim(A, grid, wpc, b->tun.sim_queue, s);
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
 int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
                   int64_t *end, int64_t *makespan, void *stream, bool per_dag, const Rollout &ro = Rollout()) {
     if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
@@ -764,61 +858,15 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
         CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
         insp::SimArgs A{};
-        A.B = b->dev();
-        A.n_cpu = b->mach.n_cpu;
-        A.n_gpu = b->mach.n_gpu;
-        A.xfer = b->mach.xfer;
-        A.policy = b->mach.pol.policy;
-        A.task_window = b->mach.pol.task_window;
-        A.s_inc = b->mach.pol.s_inc;
-        A.s_dec = b->mach.pol.s_dec;
-        A.dec_step = b->mach.pol.dec_step;
-        A.c = b->mach.pol.c;
-        A.k_inc_tasks = b->mach.pol.k_inc_tasks;
-        A.k_inc_ns = b->mach.pol.k_inc_ns;
-        A.unit_time_def = b->unit_time_def.as<int64_t>();
-        A.indeg0 = b->indeg0.as<int32_t>();
-        A.ia = d_ia;
-        A.ie = d_ie;
-        A.worker = d_worker;
-        A.start = d_start;
-        A.end = d_end;
-        A.makespan = d_mk;
-        A.status = b->status.as<int32_t>();
-        A.st_a = S.st_a.as<int2>();
-        A.st_b = S.st_b.as<longlong2>();
-        A.p_idw = S.p_idw.as<int32_t>();
-        A.p_seq = S.p_seq.as<int32_t>();
-        A.p_ia = S.p_ia.as<int32_t>();
-        A.p_ie = S.p_ie.as<int32_t>();
-        A.p_dr = S.p_dr.as<int64_t>();
-        A.p_cost = S.p_cost.as<int64_t>();
-        A.nl = S.nl.as<int32_t>();
-        A.order = b->order.as<int32_t>();
-        A.counter = b->counters.as<int32_t>() + 8;
-        A.scorer = learned ? b->owner->scorer.as<insp::ScorerPacked>() : nullptr;
-        A.force_pop = ro.force_pop;
-        A.force_task = ro.force_task;
-        A.feat_pop = ro.feat_pop;
-        A.feat_cap = ro.feat_cap;
-        A.feat_task = ro.feat_task;
-        A.feat = ro.feat;
-        A.feat_n = ro.feat_n;
+        fill_sim_args(b, A, d_ia, d_ie, d_worker, d_start, d_end, d_mk, ro);
         if (per_dag) {
             for (int d = 0; d < b->ndag; ++d) {
                 A.single_dag = d;
                 TimedLaunch tl(b, TK_SIM_SINGLE, s);
                 insp::launch_sim_single(A, s);
             }
-        } else {
-            A.single_dag = -1;
-            TimedLaunch tl(b, TK_SIM, s);
-            DeviceInfo di;
-            if ((rc = device_info(di))) return rc;
-            const int wpc = b->tun.sim_warps;
-            const int occ = std::max(1, insp::sim_occupancy(learned, wpc, b->tun.sim_queue));
-            const int grid = std::max(1, std::min(di.sms * occ, (b->ndag + wpc - 1) / wpc));
-            insp::launch_sim(A, grid, wpc, b->tun.sim_queue, s);
+        } else if ((rc = launch_sim_part(b, A, s))) {
+            return rc;
         }
         CU(cudaGetLastError());
     }
@@ -839,6 +887,93 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
 INSP_API int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
                                  int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
     return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
+                                 int32_t *worker, int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
+    if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
+    if (b->mach.pol.policy == INSP_POLICY_LEARNED && !(b->owner && b->owner->has_scorer))
+        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    int rc;
+    Scratch &S = *b->sc;
+    // host arrays are staged through the batch's scratch and copied back at the end
+    const int64_t N = b->n_total;
+    int32_t *d_ia, *d_ie, *d_worker;
+    int64_t *d_start, *d_end, *d_mk;
+    bool h[6];
+    if ((rc = stage_out(S.s_ia, ia, N, d_ia, h[0])) || (rc = stage_out(S.s_ie, ie, N, d_ie, h[1])) ||
+        (rc = stage_out(S.s_worker, worker, N, d_worker, h[2])) || (rc = stage_out(S.s_start, start, N, d_start, h[3])) ||
+        (rc = stage_out(S.s_end, end, N, d_end, h[4])) || (rc = stage_out(S.s_makespan, makespan, b->ndag, d_mk, h[5])))
+        return rc;
+    const int64_t *ut;
+    bool wide;
+    if ((rc = prep_unit_time(b, unit_time_ns, s, ut, wide))) return rc;
+    if (b->ndag == 0) return INSP_OK;
+    const bool pull = !wide && b->pull;
+    if (!pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
+    const int G = pull ? std::min(b->tun.groups, b->ndag) : 1;
+    const bool ov = b->tun.attr_overlap != 0;
+    int32_t *ctr = b->counters.as<int32_t>();
+    CU(cudaMemsetAsync(b->counters.p, 0, b->counters.bytes, s));
+    CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
+    insp::launch_step_begin(S.step.as<insp::StepCounters>(), b->n_items, s);
+    insp::SimArgs A{};
+    fill_sim_args(b, A, d_ia, d_ie, d_worker, d_start, d_end, d_mk, Rollout());
+    cudaStream_t s_ie = ov ? S.q[0] : s;
+    if (ov) {
+        CU(cudaEventRecord(S.ev_fork, s));
+        CU(cudaStreamWaitEvent(S.q[0], S.ev_fork, 0));
+    }
+    // size groups along the size order (largest DAGs first, equal DAG counts): the
+    // simulation of group g starts on its own stream as soon as the attributes of
+    // group g are done, while the attributes of the later groups still run
+    for (int g = 0; g < G; ++g) {
+        const int r0 = int(int64_t(g) * b->ndag / G), r1 = int(int64_t(g + 1) * b->ndag / G);
+        int32_t *cg = ctr + 16 + 4 * g;
+        if ((rc = launch_attr(b, r0, r1, cg, ut, pull, wide, d_ia, d_ie, s, s_ie))) return rc;
+        A.order = b->order.as<int32_t>() + r0;
+        A.n_order = r1 - r0;
+        A.counter = cg + 2;
+        if (G == 1) {
+            if (ov) {
+                CU(cudaEventRecord(S.ev_ie[0], s_ie));
+                CU(cudaStreamWaitEvent(s, S.ev_ie[0], 0));
+            }
+            if ((rc = launch_sim_part(b, A, s))) return rc;
+        } else {
+            cudaStream_t qg = S.q[1 + g];
+            CU(cudaEventRecord(S.ev_ia[g], s));
+            CU(cudaStreamWaitEvent(qg, S.ev_ia[g], 0));
+            if (ov) {
+                CU(cudaEventRecord(S.ev_ie[g], s_ie));
+                CU(cudaStreamWaitEvent(qg, S.ev_ie[g], 0));
+            }
+            if ((rc = launch_sim_part(b, A, qg))) return rc;
+            CU(cudaEventRecord(S.ev_sim[g], qg));
+        }
+    }
+    if (G > 1) {
+        for (int g = 0; g < G; ++g) CU(cudaStreamWaitEvent(s, S.ev_sim[g], 0));
+        if (ov) {
+            CU(cudaEventRecord(S.ev_ie[0], s_ie));
+            CU(cudaStreamWaitEvent(s, S.ev_ie[0], 0));
+        }
+    }
+    CU(cudaGetLastError());
+    if (h[0] || h[1] || h[2] || h[3] || h[4] || h[5]) {
+        if (h[0]) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
+        if (h[1]) CU(cudaMemcpyAsync(ie, d_ie, N * 4, cudaMemcpyDeviceToHost, s));
+        if (h[2]) CU(cudaMemcpyAsync(worker, d_worker, N * 4, cudaMemcpyDeviceToHost, s));
+        if (h[3]) CU(cudaMemcpyAsync(start, d_start, N * 8, cudaMemcpyDeviceToHost, s));
+        if (h[4]) CU(cudaMemcpyAsync(end, d_end, N * 8, cudaMemcpyDeviceToHost, s));
+        if (h[5]) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        std::vector<int32_t> st;
+        return first_status(b, st);
+    }
+    return INSP_OK;
 }
 
 INSP_API int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
@@ -901,8 +1036,7 @@ INSP_API int insp_batch_record(insp_batch *b, int32_t *ia, int32_t *ie, int32_t 
     const bool timing = b->timing;
     b->timing = false;
     CU(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
-    int rc = insp_attributes_batch(b, nullptr, ia, ie, stream);
-    if (rc == INSP_OK) rc = insp_simulate_batch(b, ia, ie, worker, start, end, makespan, stream);
+    int rc = insp_evaluate_batch(b, nullptr, ia, ie, worker, start, end, makespan, stream);
     const std::string err = g_err;
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -939,9 +1073,7 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
     const insp_tuning old = b->tun;
     b->tun = *t;
     int rc = INSP_OK;
-    if (old.ia_bin_tasks != t->ia_bin_tasks || old.ia_warps_small != t->ia_warps_small ||
-        old.ia_warps_large != t->ia_warps_large)
-        rc = alloc_ia(b);
+    if (old.ia_warps != t->ia_warps) rc = alloc_ia(b);
     if (rc == INSP_OK && b->pull && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
         rc = alloc_pull_ring(b);
     if (rc != INSP_OK) b->tun = old;
@@ -991,12 +1123,11 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    // time one call after a warm-up call; which: 0 attributes, 1 simulation
-    auto time_call = [&](int which, float &ms) -> int {
+    // one evaluation step, timed after a warm-up step
+    auto time_step = [&](float &ms) -> int {
         for (int rep = 0; rep < 2; ++rep) {
             CU(cudaEventRecord(e0, s));
-            const int r = which == 0 ? insp_attributes_batch(b, nullptr, ia, ie, stream)
-                                     : insp_simulate_batch(b, ia, ie, worker, start, end, mk, stream);
+            const int r = insp_evaluate_batch(b, nullptr, ia, ie, worker, start, end, mk, stream);
             if (r) return r;
             CU(cudaEventRecord(e1, s));
             CU(cudaEventSynchronize(e1));
@@ -1005,49 +1136,58 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
         return INSP_OK;
     };
     insp_tuning best = b->tun;
-    auto search = [&](const std::vector<insp_tuning> &cands, int which) -> int {
+    // coordinate search: each stage varies some fields of the best tuning so far
+    auto search = [&](const std::vector<insp_tuning> &cands) -> int {
         float best_ms = 1e30f;
         for (const insp_tuning &c : cands) {
             int r = insp_batch_set_tuning(b, &c);
             if (r) return r;
             float ms = 0;
-            if ((r = time_call(which, ms))) return r;
+            if ((r = time_step(ms))) return r;
             if (ms < best_ms) { best_ms = ms; best = c; }
         }
         return insp_batch_set_tuning(b, &best);
     };
-    // 1. ability sweep: size bins and CTA sizes (efficiency sweep at its current shape)
-    std::vector<insp_tuning> c_ia;
-    const int ia_choice[][3] = {{0, 8, 8},     {0, 16, 16},    {0, 32, 32},
-                                {1024, 8, 32}, {1024, 16, 32}, {512, 8, 16}};
-    for (auto &x : ia_choice) {
-        insp_tuning t = best;
-        t.ia_bin_tasks = x[0]; t.ia_warps_small = x[1]; t.ia_warps_large = x[2];
-        c_ia.push_back(t);
-    }
-    rc = search(c_ia, 0);
+    std::vector<insp_tuning> c;
+    // 1. simulation: DAGs per CTA and queue capacity
+    for (int w : {2, 4, 8})
+        for (int q : {32, 64, 128}) {
+            insp_tuning t = best;
+            t.sim_warps = w; t.sim_queue = q;
+            c.push_back(t);
+        }
+    rc = search(c);
     // 2. efficiency sweep: CTA size and ring budget (only the pull form has them)
     if (rc == INSP_OK && b->pull) {
-        std::vector<insp_tuning> c_ie;
+        c.clear();
         for (int w : {4, 8, 16})
-            for (int mb : {64, 128, 256, 512, 1024}) {
+            for (int mb : {128, 256, 512, 1024}) {
                 insp_tuning t = best;
                 t.ie_warps = w; t.ie_ring_mb = mb;
-                c_ie.push_back(t);
+                c.push_back(t);
             }
-        rc = search(c_ie, 0);
+        rc = search(c);
     }
-    // 3. simulation: DAGs per CTA and queue capacity
+    // 3. ability sweep: CTA size
     if (rc == INSP_OK) {
-        CU(cudaStreamSynchronize(s));
-        std::vector<insp_tuning> c_sim;
-        for (int w : {2, 4, 8})
-            for (int q : {32, 64, 128}) {
+        c.clear();
+        for (int w : {8, 16, 32}) {
+            insp_tuning t = best;
+            t.ia_warps = w;
+            c.push_back(t);
+        }
+        rc = search(c);
+    }
+    // 4. pipelining: size groups and concurrent attribute sweeps
+    if (rc == INSP_OK) {
+        c.clear();
+        for (int g : {1, 2, 4, 8, 16})
+            for (int ov : {0, 1}) {
                 insp_tuning t = best;
-                t.sim_warps = w; t.sim_queue = q;
-                c_sim.push_back(t);
+                t.groups = g; t.attr_overlap = ov;
+                c.push_back(t);
             }
-        rc = search(c_sim, 1);
+        rc = search(c);
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -38,8 +38,8 @@ constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) 
 
 __global__ void __launch_bounds__(PULL_MAX_WARPS * 32)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
-              const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
-              int32_t *gring, int32_t *ie_out) {
+              const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
+              const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32)
 
     for (;;) {
         int64_t item = 0;
-        if (lane == 0) item = atomicAdd(counter, 1);
+        if (lane == 0) item = item_lo + atomicAdd(counter, 1);
         item = __shfl_sync(FULL, item, 0);
-        if (item >= n_items) return;
+        if (item >= item_hi) return;
         const int d = item_dag[item];
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];
         const int32_t n = int32_t(B.task_base[d + 1] - tb);
@@ -206,11 +206,13 @@ int ie_pull_occupancy(int warps) {
 }
 
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
-                    const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
-                    int32_t *gring, int32_t *ie, int grid, int warps, cudaStream_t s) {
+                    const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
+                    const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie, int grid, int warps,
+                    cudaStream_t s) {
     cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
     k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
-                                                                           n_items, counter, unit_time, W, gring, ie);
+                                                                           item_lo, item_hi, counter, unit_time, W,
+                                                                           gring, ie);
 }
 
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,

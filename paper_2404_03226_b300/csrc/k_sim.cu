@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             int k = 0;
             if (lane == 0) k = atomicAdd(A.counter, 1);
             k = __shfl_sync(FULL, k, 0);
-            if (k >= B.ndag) return;
+            if (k >= A.n_order) return;
             d = A.order[k];
         }
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];

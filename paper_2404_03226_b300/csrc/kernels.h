@@ -27,7 +27,8 @@ struct SimArgs {
     int64_t *p_dr, *p_cost;
     int32_t *nl;        // released-task spill
     // work distribution
-    const int32_t *order;  // DAGs by descending size
+    const int32_t *order;  // DAGs by descending size (or a contiguous part of that order)
+    int32_t n_order;       // DAGs in order[]
     int32_t *counter;
     int32_t single_dag;    // >= 0: only that DAG, one warp
     // learned scorer (policy INSP_POLICY_LEARNED)
@@ -64,8 +65,9 @@ int64_t ie_pull_ring_bytes(int32_t W);
 int ie_pull_occupancy(int warps);
 // gring: per-warp rings of ie_pull_ring_bytes(W) in global memory (row W all -1)
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
-                    const int32_t *item_dag, int64_t n_items, int32_t *counter, const int64_t *unit_time, int32_t W,
-                    int32_t *gring, int32_t *ie, int grid, int warps, cudaStream_t s);
+                    const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
+                    const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie, int grid, int warps,
+                    cudaStream_t s);
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
                         int grid, cudaStream_t s);
 // learned scorer (k_mlp.cu)

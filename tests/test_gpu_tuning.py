@@ -1,7 +1,7 @@
-"""Launch shapes of the batched kernels (the library's autotuner, no
-counterpart in the paper): every tuning gives the oracle's results bit for
-bit, the autotuner returns a valid tuning, and out-of-range fields are
-rejected."""
+"""Launch shapes and pipelining of the batched kernels (the library's
+autotuner, no counterpart in the paper): under every tuning both the two-call
+step and the pipelined evaluation step give the oracle's results bit for bit,
+the autotuner returns a valid tuning, and out-of-range fields are rejected."""
 import numpy as np
 import pytest
 
@@ -11,13 +11,11 @@ from helpers import compare_dag, edge_case_dags
 pytestmark = pytest.mark.gpu
 
 TUNINGS = [
-    dict(ia_bin_tasks=0, ia_warps_small=8, ia_warps_large=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64),
-    dict(ia_bin_tasks=300, ia_warps_small=2, ia_warps_large=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32),
-    dict(ia_bin_tasks=0, ia_warps_small=32, ia_warps_large=32, ie_warps=16, ie_ring_mb=2048, sim_warps=8,
-         sim_queue=128),
-    dict(ia_bin_tasks=100000, ia_warps_small=5, ia_warps_large=3, ie_warps=8, ie_ring_mb=256, sim_warps=3,
-         sim_queue=128),
-    dict(ia_bin_tasks=1, ia_warps_small=1, ia_warps_large=7, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32),
+    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64),
+    dict(groups=3, attr_overlap=1, ia_warps=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32),
+    dict(groups=16, attr_overlap=0, ia_warps=32, ie_warps=16, ie_ring_mb=2048, sim_warps=8, sim_queue=128),
+    dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128),
+    dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32),
 ]
 
 
@@ -25,10 +23,13 @@ def _batch():
     return inputs.concat([inputs.layered(40, cfg=41, n_min=1, n_max=900), inputs.concat_dags(edge_case_dags())])
 
 
-def _run(B):
+def _run(B, fused=False, unit_time=None):
     import torch
-    ia, ie = B.attributes()
-    s = B.simulate(ia, ie)
+    if fused:
+        ia, ie, s = B.evaluate(unit_time)
+    else:
+        ia, ie = B.attributes(unit_time)
+        s = B.simulate(ia, ie)
     torch.cuda.synchronize()
     assert (B.status() == 0).all()
     return dict(ia=ia.cpu().numpy(), ie=ie.cpu().numpy(), worker=s.worker.cpu().numpy(), start=s.start.cpu().numpy(),
@@ -36,14 +37,46 @@ def _run(B):
 
 
 @pytest.mark.parametrize("k", range(len(TUNINGS)))
-def test_every_tuning_matches_oracle(k):
+@pytest.mark.parametrize("fused", [False, True])
+def test_every_tuning_matches_oracle(k, fused):
     import paper_2404_03226_b300 as P
     b, m = _batch(), inputs.MACHINE_LAYERED
     M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
     B = P.DagBatch(M, b)
     B.tuning = TUNINGS[k]
     assert B.tuning == TUNINGS[k]
-    out = _run(B)
+    out = _run(B, fused)
+    for d in range(b.ndag):
+        compare_dag(b, d, out, m)
+
+
+@pytest.mark.parametrize("wide", [False, True])
+def test_pipelined_step_with_unit_times(wide):
+    """Caller unit times: narrow ones keep the pipelined pull sweep, wide ones
+    (>= 2^31 ns) take the global sweep in one group."""
+    import paper_2404_03226_b300 as P
+    b, m = _batch(), inputs.MACHINE_LAYERED
+    rng = np.random.default_rng(8)
+    ut = rng.integers(1, 3_000_000, b.ndag).astype(np.int64)
+    ut[::7] = 0  # defaults
+    if wide:
+        ut[1] = (1 << 31) + 5
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = TUNINGS[3]
+    out = _run(B, True, ut)
+    ref = _run(B, False, ut)
+    for f in out:
+        np.testing.assert_array_equal(out[f], ref[f], err_msg=f)
+    for d in range(0, b.ndag, 3):
+        compare_dag(b, d, out, m, unit_time=int(ut[d]) if ut[d] > 0 else None)
+
+
+def test_pipelined_step_more_groups_than_dags():
+    import paper_2404_03226_b300 as P
+    b, m = inputs.concat_dags(edge_case_dags()[:3]), inputs.MACHINE_LAYERED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = TUNINGS[2]
+    out = _run(B, True)
     for d in range(b.ndag):
         compare_dag(b, d, out, m)
 
@@ -67,8 +100,8 @@ def test_tuning_rejects_out_of_range():
     b, m = _batch(), inputs.MACHINE_LAYERED
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
     good = B.tuning
-    for field, bad in (("ia_warps_small", 0), ("ia_warps_large", 33), ("ie_warps", 17), ("ie_ring_mb", 0),
-                       ("sim_warps", 0), ("sim_queue", 48), ("ia_bin_tasks", -1)):
+    for field, bad in (("groups", 0), ("groups", 17), ("attr_overlap", 2), ("ia_warps", 0), ("ia_warps", 33),
+                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48)):
         t = dict(good, **{field: bad})
         with pytest.raises(P.InspError):
             B.tuning = t
