@@ -253,7 +253,13 @@ def run_ours(args, rank, world, local_rank):
         _lib.insp_evaluate_batch(b.handle, None, ia, ie, worker, start, end, mk, stream)
 
     # launch shapes picked on this batch before the timed region (setup, like the load)
-    t_struct = _lib.insp_batch_autotune(b.handle, stream) if args.autotune else _lib.insp_batch_get_tuning(b.handle)
+    if args.tuning:  # explicit launch shapes (profiling captures)
+        _lib.insp_batch_set_tuning(b.handle, _lib.insp_tuning(**json.loads(args.tuning)))
+        t_struct = _lib.insp_batch_get_tuning(b.handle)
+    elif args.autotune:
+        t_struct = _lib.insp_batch_autotune(b.handle, stream)
+    else:
+        t_struct = _lib.insp_batch_get_tuning(b.handle)
     _lib.insp_machine_set_tuning(machine.handle, t_struct)  # batches loaded later (the e2e leg) start with it
     tuning = t_struct.as_dict()
     for _ in range(args.warmup):
@@ -410,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": wdesc, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
                        "machine": mdesc, "policy": "INSPIRIT (defaults)",
-                       "tuning": dict(tuning, autotuned=bool(args.autotune)),
+                       "tuning": dict(tuning, autotuned=bool(args.autotune and not args.tuning)),
                        "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
                              f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
             "per_dag_form": per_dag,
@@ -442,6 +448,9 @@ def main():
     ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shapes instead of autotuning them on the batch")
+    ap.add_argument("--tuning", default=None,
+                    help='explicit tuning as JSON, e.g. \'{"groups": 1, "attr_overlap": 0, "ia_warps": 32, '
+                         '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64}\'')
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
     args = ap.parse_args()
