@@ -122,14 +122,14 @@ def algorithmic_bytes(batch):
     c_sim = 16 * n if per_task else n
     return {
         "k_ia": csr + 4 * n,                                   # ia written
-        "k_ie": csr + c_ie + 4 * n,                            # GPU cost read, ie written
+        "k_ie_pull": csr + c_ie + 4 * n,                            # GPU cost read, ie written
         "k_sim": csr + c_sim + 4 * n + 8 * n + 20 * n + 8 * nd,  # costs, in-degree, ia+ie read; schedule written
     }
 
 
-def traffic_from_profile(kernel: str):
-    """dram bytes per launch recorded by an ncu capture in profiles/, if the
-    kernel source has not changed since."""
+def traffic_from_profile(kernel: str, launches_per_step: float):
+    """dram bytes per launch from the per-step figure an ncu capture recorded in
+    profiles/, if the kernel source has not changed since."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
@@ -140,7 +140,7 @@ def traffic_from_profile(kernel: str):
     src = os.path.join(ROOT, "paper_2404_03226_b300", "csrc", rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
         return None
-    return rec["bytes_per_launch_full"]
+    return rec["bytes_per_step_full"] / max(launches_per_step, 1.0)
 
 
 # ------------------------------------------------------------ multi-rank
@@ -315,7 +315,7 @@ def run_ours(args, rank, world, local_rank):
              "launches_per_step": 1}
 
     # ---- roofline of the dominant kernel
-    names = ["k_ia", "k_ie", "k_sim"]
+    names = ["k_ia", "k_ie_pull", "k_sim"]  # the layered and tiled workloads take the pull efficiency sweep
     alg = algorithmic_bytes(batch)
     per_launch_ms = {names[k]: kms[k] / max(klaunch[k], 1) for k in range(3)}
     share = {names[k]: kms[k] / max(kms[:3].sum(), 1e-9) for k in range(3)}
@@ -325,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     # durations (= bytes per launch / mean launch time; one launch per size group and step)
     achieved = alg[dom] * args.steps / (kms[names.index(dom)] / 1e3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(dom), "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
+                "traffic": traffic_from_profile(dom, klaunch[names.index(dom)] / args.steps), "kernel": dom, "peak_source": f"{peak_kind} hbm_gbs",
                 "kernel_ms": {k: round(v, 4) for k, v in per_launch_ms.items()},
                 "kernel_share": {k: round(v, 4) for k, v in share.items()},
                 "step_bytes": int(sum(alg.values())),
