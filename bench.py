@@ -42,6 +42,11 @@ def make_workload(args, rank):
         b = inputs.layered4096(ndag=args.ndag, first=rank_first_dag(rank))
         desc = WORKLOAD if args.ndag == 4096 else f"first {args.ndag} of: " + WORKLOAD
         return b, inputs.MACHINE_LAYERED, desc, "8 CPU + 2 GPU workers, xfer 20000 ns"
+    if args.workload == "layered_degree":
+        b = inputs.layered4096_degree(ndag=args.ndag, first=rank_first_dag(rank))
+        desc = ("the same 4096 layered DAG shapes with 16 task types by in/out degree bucket (per-type log-normal "
+                "costs), 8 CPU + 2 GPU workers, 20 us transfer, INSPIRIT policy")
+        return b, inputs.MACHINE_LAYERED, desc, "8 CPU + 2 GPU workers, xfer 20000 ns"
     if args.workload == "tiled":
         Ns = tuple(int(x) for x in args.tiles.split(","))
         b = inputs.tiled_workload(Ns=Ns, instances=args.instances)
@@ -442,7 +447,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ndag", type=int, default=4096, help="first K DAGs of the workload (profiling captures)")
-    ap.add_argument("--workload", choices=["layered", "tiled"], default="layered",
+    ap.add_argument("--workload", choices=["layered", "layered_degree", "tiled"], default="layered",
                     help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches")
     ap.add_argument("--tiles", default="16,32,64", help="tile counts of the tiled workload")
     ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")

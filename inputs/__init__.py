@@ -54,7 +54,7 @@ class _LayeredParams(ctypes.Structure):
         ("d_min", ctypes.c_int32), ("d_max", ctypes.c_int32),
         ("n_types", ctypes.c_int32),
         ("cost_median_ns", ctypes.c_double), ("cost_sigma", ctypes.c_double),
-        ("speed_min", ctypes.c_double), ("speed_max", ctypes.c_double),
+        ("speed_min", ctypes.c_double), ("speed_max", ctypes.c_double), ("typing", ctypes.c_int32),
     ]
 
 
@@ -199,10 +199,14 @@ def _from_c(ptr) -> Batch:
 
 def layered(ndag: int, cfg: int = 2, first: int = 0, *, n_min=50, n_max=2000, w_min=4, w_max=64,
             p_min=0.1, p_max=0.5, d_min=1, d_max=3, n_types=8, cost_median_ns=100 * US,
-            cost_sigma=1.0, speed_min=0.5, speed_max=20.0, base_seed=BASE_SEED) -> Batch:
-    """Random layered DAGs (defaults: the 4096-DAG layered workload's shape)."""
+            cost_sigma=1.0, speed_min=0.5, speed_max=20.0, typing: str = "random", base_seed=BASE_SEED) -> Batch:
+    """Random layered DAGs (defaults: the 4096-DAG layered workload's shape).
+    typing "degree": 16 task types by in/out degree bucket instead of random types."""
+    ty = {"random": 0, "degree": 1}[typing]
+    if ty == 1:
+        n_types = 16
     p = _LayeredParams(n_min, n_max, w_min, w_max, p_min, p_max, d_min, d_max, n_types,
-                       float(cost_median_ns), float(cost_sigma), float(speed_min), float(speed_max))
+                       float(cost_median_ns), float(cost_sigma), float(speed_min), float(speed_max), ty)
     return _from_c(_load().insg_layered(base_seed, cfg, first, ndag, ctypes.byref(p)))
 
 
@@ -273,6 +277,11 @@ def cholesky8() -> Batch:
 def layered4096(ndag: int = 4096, first: int = 0) -> Batch:
     """The 4096 random layered DAGs (or a prefix / window of them)."""
     return layered(ndag, cfg=2, first=first)
+
+
+def layered4096_degree(ndag: int = 4096, first: int = 0) -> Batch:
+    """The same 4096 layered DAG shapes with task types by in/out degree."""
+    return layered(ndag, cfg=2, first=first, typing="degree")
 
 
 def tiled_workload(Ns=(16, 32, 64), instances: int = 256, kinds=(KIND_CHOLESKY, KIND_LU, KIND_QR)) -> Batch:

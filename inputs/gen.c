@@ -7,7 +7,8 @@
  * Workloads (stand-ins for the evaluation section of the paper):
  *   - random layered DAGs, the "logically layered" auto-generated graphs the
  *     authors fed to their Taskbench extension (Sec. 4.4 "Implementation
- *     details", Sec. 5.2);
+ *     details", Sec. 5.2), with random task types or, as the authors did,
+ *     types by in/out degree;
  *   - tiled Cholesky / LU / QR DAGs (Sec. 5.3: Cholesky with 960x960 tiles,
  *     LU with 160x160 tiles; QR is added as a third dense factorisation),
  *     whose edges are inferred from tile reads and writes the way a
@@ -129,12 +130,25 @@ typedef struct {
     double cost_median_ns;    /* CPU cost per type: round(exp(ln median + sigma N(0,1))) */
     double cost_sigma;
     double speed_min, speed_max; /* GPU cost = max(1, round(cpu / U[speed_min, speed_max))) */
+    int32_t typing;           /* 0: type ~ U{0..n_types-1}; 1: by in/out degree (n_types must be 16) */
 } insg_layered_params;
+
+/* Degree-based codelet of a task (the authors gave their generated tasks
+ * codelets by inbound and outbound degree, Sec. 4.4 "Implementation details"):
+ * 4 x bucket(in-degree) + bucket(out-degree), bucket(k) = min(3, bit length of k),
+ * i.e. buckets {0}, {1}, {2, 3}, {4, ...}: 16 types. */
+static uint8_t degree_type(int32_t indeg, int32_t outdeg) {
+    int32_t bi = 0, bo = 0;
+    while (bi < 3 && (indeg >> bi) != 0) ++bi;
+    while (bo < 3 && (outdeg >> bo) != 0) ++bo;
+    return (uint8_t)(4 * bi + bo);
+}
 
 /* Draw order per DAG (fixed): n, p, d, layer widths, edge coin flips in
  * (u ascending, layer ascending, v ascending) order, the fix-up parent of
- * every parentless non-first-layer node in id order, task types in id order,
- * then per type: normal deviate for CPU cost, then GPU speed-up. */
+ * every parentless non-first-layer node in id order, task types in id order
+ * (random typing only; degree typing draws none), then per type: normal
+ * deviate for CPU cost, then GPU speed-up. */
 static int gen_layered_one(uint64_t seed, const insg_layered_params *P, one_dag *d) {
     uint64_t s = seed;
     int32_t n = (int32_t)urange(&s, P->n_min, P->n_max);
@@ -182,7 +196,15 @@ static int gen_layered_one(uint64_t seed, const insg_layered_params *P, one_dag 
     edges_free(&E);
     d->type = (uint8_t *)malloc((size_t)n + 1);
     if (!d->type) return -1;
-    for (int32_t i = 0; i < n; ++i) d->type[i] = (uint8_t)urange(&s, 0, P->n_types - 1);
+    if (P->typing == 1) {
+        int32_t *indeg = (int32_t *)calloc((size_t)n + 1, sizeof(int32_t));
+        if (!indeg) return -1;
+        for (int32_t e = 0; e < d->m; ++e) indeg[d->col_idx[e]]++;
+        for (int32_t i = 0; i < n; ++i) d->type[i] = degree_type(indeg[i], d->row_ptr[i + 1] - d->row_ptr[i]);
+        free(indeg);
+    } else {
+        for (int32_t i = 0; i < n; ++i) d->type[i] = (uint8_t)urange(&s, 0, P->n_types - 1);
+    }
     for (int32_t k = 0; k < P->n_types; ++k) {
         double z = std_normal(&s);
         double cpu = exp(log(P->cost_median_ns) + P->cost_sigma * z);
@@ -390,7 +412,8 @@ EXPORT void insg_free(insg_batch *B) {
 EXPORT insg_batch *insg_layered(uint64_t base, uint32_t cfg, uint64_t first, int32_t ndag,
                                 const insg_layered_params *P) {
     if (ndag < 0 || P->n_types < 1 || P->n_types > 16 || P->n_min < 0 || P->n_max < P->n_min ||
-        P->w_min < 1 || P->w_max < P->w_min || P->d_min < 1 || P->d_max < P->d_min)
+        P->w_min < 1 || P->w_max < P->w_min || P->d_min < 1 || P->d_max < P->d_min ||
+        (P->typing != 0 && P->typing != 1) || (P->typing == 1 && P->n_types != 16))
         return NULL;
     one_dag *D = (one_dag *)calloc((size_t)ndag + 1, sizeof(one_dag));
     if (!D) return NULL;

@@ -30,6 +30,16 @@ def test_layered_small_sizes(policy):
         compare_dag(b, d, g, m, policy)
 
 
+def test_layered_degree_typed():
+    """The layered shapes with 16 task types by in/out degree."""
+    b = inputs.layered(40, cfg=2, first=100, n_max=900, typing="degree")
+    m = inputs.MACHINE_LAYERED
+    g = gpu_run(b, m)
+    assert (g["status"] == 0).all()
+    for d in range(b.ndag):
+        compare_dag(b, d, g, m)
+
+
 @pytest.mark.parametrize("machine", [inputs.Machine(1, 0, 0), inputs.Machine(0, 1, 5), inputs.Machine(3, 2, 7),
                                      inputs.Machine(32, 8, 20000), inputs.Machine(60, 4, 1000)])
 def test_edge_case_dags(machine):

@@ -56,3 +56,24 @@ def test_layered_costs():
     assert 60_000 < np.median(cpu) < 160_000  # log-normal around 100 us
     r = cpu / gpu
     assert r.min() > 0.45 and r.max() < 21
+
+
+def test_layered_degree_typing():
+    """Degree typing keeps the random layered shapes and gives every task the
+    type 4 * bucket(in-degree) + bucket(out-degree), buckets {0}, {1}, {2,3}, {4..}."""
+    r = inputs.layered(12, cfg=2)
+    g = inputs.layered(12, cfg=2, typing="degree")
+    assert g.n_types == 16
+    assert np.array_equal(r.row_ptr, g.row_ptr) and np.array_equal(r.col_idx, g.col_idx)
+    _check_csr(g)
+
+    def bucket(k):
+        return np.select([k == 0, k == 1, k <= 3], [0, 1, 2], 3)
+
+    for d in range(g.ndag):
+        x = g.dag(d)
+        indeg = np.bincount(x.col_idx, minlength=x.n)
+        outdeg = np.diff(x.row_ptr)
+        np.testing.assert_array_equal(x.type, 4 * bucket(indeg) + bucket(outdeg))
+    assert (g.type_cost[:, :, 0] >= 1).all() and (g.type_cost[:, :, 1] >= 1).all()
+    assert len(np.unique(g.type)) > 6
