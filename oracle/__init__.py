@@ -31,8 +31,8 @@ _lock = threading.Lock()
 _lib = None
 
 OK, EINVAL, ENOTTOPO, ENOMEM, EOVERFLOW = 0, 1, 2, 3, 6
-POLICY_INSPIRIT, POLICY_FIFO, POLICY_LEARNED = 0, 1, 2
-MODE_FIFO, MODE_ABILITY, MODE_EFI, MODE_EFI_LOC, MODE_LEARNED = 0, 1, 2, 3, 4
+POLICY_INSPIRIT, POLICY_FIFO, POLICY_LEARNED, POLICY_DMDAP_IA, POLICY_DMDAP_BL = 0, 1, 2, 3, 4
+MODE_FIFO, MODE_ABILITY, MODE_EFI, MODE_EFI_LOC, MODE_LEARNED, MODE_PRIO = 0, 1, 2, 3, 4, 5
 STATE_INC, STATE_DEC = 0, 1
 MLP_IN, MLP_H = 16, 64
 
@@ -58,7 +58,9 @@ class Ctrl(ctypes.Structure):
 class _Trace(ctypes.Structure):
     _fields_ = [("t", _i64p), ("nready", _i32p), ("mode", _i32p), ("task", _i32p), ("worker", _i32p),
                 ("npop", ctypes.c_int32), ("feat_pop", ctypes.c_int32), ("feat_cap", ctypes.c_int32),
-                ("n_feat", ctypes.c_int32), ("feat_task", _i32p), ("feat", _i32p)]
+                ("n_feat", ctypes.c_int32), ("feat_task", _i32p), ("feat", _i32p),
+                ("push_t", _i64p), ("push_task", _i32p), ("push_worker", _i32p), ("push_nready", _i32p),
+                ("npush", ctypes.c_int32)]
 
 
 class _Force(ctypes.Structure):
@@ -96,6 +98,8 @@ def _L():
         lib.orc_validate.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int64, _i32p, _i64p, _i64p, ctypes.c_int64, _i32p]
         _dp = ctypes.POINTER(ctypes.c_double)
+        lib.orc_bottom_level.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
+                                         ctypes.c_int64, _i64p]
         lib.orc_mlp_loss_grad.restype = ctypes.c_double
         lib.orc_mlp_loss_grad.argtypes = [ctypes.c_int32] * 3 + [_dp, ctypes.c_int32, ctypes.c_int32, _dp, _dp, _dp]
         lib.orc_adamw.argtypes = [ctypes.c_int32, _dp, _dp, _dp, _dp, ctypes.c_int32] + [ctypes.c_double] * 5
@@ -201,10 +205,14 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
         cap = max(n, 1)
         bufs = dict(t=np.zeros(cap, np.int64), nready=np.zeros(cap, np.int32), mode=np.zeros(cap, np.int32),
                     task=np.zeros(cap, np.int32), worker=np.zeros(cap, np.int32),
-                    feat_task=np.zeros(max(feat_cap, 1), np.int32), feat=np.zeros(max(feat_cap, 1) * MLP_IN, np.int32))
+                    feat_task=np.zeros(max(feat_cap, 1), np.int32), feat=np.zeros(max(feat_cap, 1) * MLP_IN, np.int32),
+                    push_t=np.zeros(cap, np.int64), push_task=np.zeros(cap, np.int32),
+                    push_worker=np.zeros(cap, np.int32), push_nready=np.zeros(cap, np.int32))
         tr = _Trace(_p(bufs["t"], _i64p), _p(bufs["nready"], _i32p), _p(bufs["mode"], _i32p),
                     _p(bufs["task"], _i32p), _p(bufs["worker"], _i32p), 0, feat_pop, feat_cap, 0,
-                    _p(bufs["feat_task"], _i32p), _p(bufs["feat"], _i32p))
+                    _p(bufs["feat_task"], _i32p), _p(bufs["feat"], _i32p),
+                    _p(bufs["push_t"], _i64p) if trace else None, _p(bufs["push_task"], _i32p),
+                    _p(bufs["push_worker"], _i32p), _p(bufs["push_nready"], _i32p), 0)
     # k_inc's default is P tasks per the DAG's *default* unit time, whatever T the
     # attributes used (0 lets orc_simulate take the default).
     rc = _L().orc_simulate(n, _p(rp, _i32p), _p(ci, _i32p), _p(cc, _i64p), _p(cg, _i64p), machine.n_cpu,
@@ -217,10 +225,22 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
     if tr is not None:
         k = tr.npop
         out["trace"] = {key: bufs[key][:k] for key in ("t", "nready", "mode", "task", "worker")}
+        out["trace"].update({key: bufs[key][:tr.npush] for key in ("push_t", "push_task", "push_worker",
+                                                                     "push_nready")})
         nf = tr.n_feat if feat_pop >= 0 else 0
         out["feat_task"] = bufs["feat_task"][:nf]
         out["feat"] = bufs["feat"][:nf * MLP_IN].reshape(nf, MLP_IN)
     return out
+
+
+def bottom_level(dag, machine) -> np.ndarray:
+    """Static priority of the DMDAP baseline: HEFT upward rank over mean costs (int64 per task)."""
+    bl = np.zeros(max(dag.n, 1), np.int64)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    rc = _L().orc_bottom_level(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_cpu), _i64p),
+                               _p(_i64(dag.c_gpu), _i64p), machine.n_cpu, machine.n_gpu, machine.xfer_ns, _p(bl, _i64p))
+    assert rc == OK
+    return bl[:dag.n]
 
 
 def validate(dag, machine, worker, start, end, makespan) -> tuple[int, int]:

@@ -6,6 +6,8 @@ Pure Python, deliberately different algorithms from ``oracle.c``:
     reached task, the heaviest path weight (GPU times, both ends included)
     from the start of the source (Sec. 4.3 with the cone / longest-path
     reading);
+  - the bottom level of the DMDAP baseline by enumerating every path to a
+    sink, with the worker and pair means taken by listing workers and pairs;
 Exponential in the worst case: only for DAGs of a few dozen tasks.
 """
 from __future__ import annotations
@@ -50,4 +52,30 @@ def ie(dag, T):
             u = p[-1]
             heaviest[u] = max(heaviest.get(u, w), w)
         res.append(sum(1 for u, w in heaviest.items() if w <= T))
+    return res
+
+
+def bottom_level(dag, machine):
+    """HEFT upward rank by path enumeration: for each task, the heaviest path to
+    a sink, weighing every task by its mean cost over the workers and every
+    edge by the mean transfer cost over ordered worker pairs (both floored),
+    the means taken by listing the workers and the pairs one by one."""
+    workers = [0] * machine.n_cpu + [1] * machine.n_gpu  # kind of each worker
+    P = len(workers)
+    node = [0 if k == 0 else 1 + i for i, k in enumerate(workers)]  # CPUs share node 0
+    distinct = sum(1 for a in range(P) for b in range(P) if node[a] != node[b])
+    cbar = machine.xfer_ns * distinct // (P * P)
+
+    def wbar(x):
+        return sum(int(dag.c_cpu[x]) if k == 0 else int(dag.c_gpu[x]) for k in workers) // P
+
+    succ = _succ(dag)
+    res = []
+    for v in range(dag.n):
+        best = 0
+        for p in all_paths_from(dag, v):
+            if succ[p[-1]]:
+                continue  # only paths that end at a sink
+            best = max(best, sum(wbar(x) for x in p) + (len(p) - 1) * cbar)
+        res.append(best)
     return res

@@ -16,10 +16,17 @@
  *                (GPU execution times, v's own time included, unlimited
  *                workers, tasks outside v's cone treated as done) finishes
  *                within the unit time T.  Plain longest-path DP over the cone.
+ *  orc_bottom_level  the static priority of the DMDAP baseline (Sec. 2.1,
+ *                Sec. 3 Observation 1): HEFT's upward rank (Topcuoglu et al.,
+ *                2002, cited in Sec. 2) over mean worker costs.
  *  orc_simulate  the list-scheduling run (Sec. 2.1 push/pop, Sec. 4.1 steps
  *                1-3, Sec. 4.4 Nready regulation with the adaptive-priority
  *                pseudocode): in-degree countdown, earliest-finish push with
- *                transfer cost (DMDA, Sec. 2.1), pop by the Nready controller.
+ *                transfer cost (DMDA, Sec. 2.1), pop by the Nready controller;
+ *                or the baselines: DMDA (FIFO pop) and DMDAP with a static
+ *                priority (IA, or the bottom level), optionally with a trace
+ *                of every push and pop (Sec. 4.4 "Implementation details":
+ *                the Nready time piling of push and pop).
  *  orc_validate  an independent check of a schedule's feasibility.
  *  orc_optimum   exhaustive optimum makespan for tiny DAGs.
  *  orc_mlp_*     integer restatement of the learned proposal scorer (fixed
@@ -45,8 +52,8 @@
 #define EXPORT __attribute__((visibility("default")))
 
 enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOTTOPO = 2, ORC_ENOMEM = 3, ORC_EOVERFLOW = 6 };
-enum { POL_INSPIRIT = 0, POL_FIFO = 1, POL_LEARNED = 2 };
-enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4 };
+enum { POL_INSPIRIT = 0, POL_FIFO = 1, POL_LEARNED = 2, POL_DMDAP_IA = 3, POL_DMDAP_BL = 4 };
+enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
 enum { ST_INC = 0, ST_DEC = 1 };
 
 /* ------------------------------------------------------------ DAG checks */
@@ -192,6 +199,32 @@ EXPORT int64_t orc_default_unit_time(int32_t n, const int64_t *c_gpu) {
     free(s);
     int64_t T = 4 * med;
     return T < 1 ? 1 : T;
+}
+
+/* ------------------------------------------------------------ bottom level */
+
+/* HEFT upward rank with integer means, ids being a topological order:
+ *   rank(v) = wbar(v) + max over successors s of (cbar + rank(s))  (no successor: wbar(v)),
+ *   wbar(v) = floor((n_cpu * c_cpu(v) + n_gpu * c_gpu(v)) / P), the mean cost over the P workers,
+ *   cbar    = floor(xfer * D / P^2), the mean transfer cost over ordered worker pairs, D of the
+ *             P^2 pairs being on distinct memory nodes (CPUs share one node, each GPU has its own):
+ *             D = P^2 - n_cpu^2 - n_gpu. */
+EXPORT int orc_bottom_level(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int64_t *c_cpu,
+                            const int64_t *c_gpu, int32_t n_cpu, int32_t n_gpu, int64_t xfer, int64_t *bl) {
+    int32_t P = n_cpu + n_gpu;
+    if (n < 0 || n_cpu < 0 || n_gpu < 0 || P < 1 || xfer < 0) return ORC_EINVAL;
+    __int128 D = (__int128)P * P - (__int128)n_cpu * n_cpu - n_gpu;
+    int64_t cbar = (int64_t)(((__int128)xfer * D) / ((__int128)P * P));
+    for (int32_t v = n - 1; v >= 0; --v) {
+        int64_t wbar = (int64_t)(((__int128)n_cpu * c_cpu[v] + (__int128)n_gpu * c_gpu[v]) / P);
+        int64_t tail = 0;
+        for (int32_t e = row_ptr[v]; e < row_ptr[v + 1]; ++e) {
+            int64_t x = cbar + bl[col_idx[e]];
+            if (x > tail) tail = x;
+        }
+        bl[v] = wbar + tail;
+    }
+    return ORC_OK;
 }
 
 /* ----------------------------------------------------------- the policy */
@@ -373,6 +406,11 @@ typedef struct {
     int32_t feat_pop, feat_cap, n_feat;
     int32_t *feat_task; /* feat_cap */
     int32_t *feat;      /* feat_cap * 16 */
+    /* per push (capacity n; push_t NULL: not recorded): time, task, chosen
+     * worker, Nready after the push */
+    int64_t *push_t;
+    int32_t *push_task, *push_worker, *push_nready;
+    int32_t npush;
 } orc_trace;
 
 typedef struct {
@@ -416,6 +454,7 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
     if (n_cpu < 0 || n_gpu < 0 || P < 1 || P > 64) return ORC_EINVAL;
     int rc = orc_check_dag(n, row_ptr, col_idx, c_cpu, c_gpu, xfer);
     if (rc) return rc;
+    if (pol_in->policy < POL_INSPIRIT || pol_in->policy > POL_DMDAP_BL) return ORC_EINVAL;
     if (pol_in->policy == POL_LEARNED && !mlp_w) return ORC_EINVAL;
     /* unit_time only sets k_inc's default (P tasks per unit_time ns); <= 0
      * selects the DAG's default unit time. */
@@ -423,7 +462,7 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
     orc_policy pol;
     orc_resolve_policy(pol_in, P, unit_time, &pol);
     *makespan = 0;
-    if (trace) trace->npop = 0;
+    if (trace) { trace->npop = 0; trace->npush = 0; }
     if (n == 0) return ORC_OK;
 
     int32_t m = row_ptr[n];
@@ -438,11 +477,13 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
     int64_t *busy_end = (int64_t *)calloc((size_t)P, sizeof(int64_t));
     int64_t *queued_cost = (int64_t *)calloc((size_t)P, sizeof(int64_t));
     int32_t *running = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
+    int64_t *bl = (int64_t *)malloc(sizeof(int64_t) * ((size_t)n + 1));
     if (!pr || !pc || !fill || !indeg || !newly || !completed || !queue || !qlen || !busy_end ||
-        !queued_cost || !running) {
+        !queued_cost || !running || !bl) {
         rc = ORC_ENOMEM;
         goto out;
     }
+    if (pol.policy == POL_DMDAP_BL) orc_bottom_level(n, row_ptr, col_idx, c_cpu, c_gpu, n_cpu, n_gpu, xfer, bl);
     for (int32_t e = 0; e < m; ++e) pr[col_idx[e] + 1]++;
     for (int32_t i = 0; i < n; ++i) pr[i + 1] += pr[i];
     for (int32_t i = 0; i < n; ++i) fill[i] = pr[i];
@@ -478,6 +519,13 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
         qlen[best]++;                                                                    \
         queued_cost[best] += COST(pt_, best);                                              \
         nready++;                                                                        \
+        if (trace && trace->push_t) {                                                    \
+            trace->push_t[trace->npush] = now;                                           \
+            trace->push_task[trace->npush] = pt_;                                          \
+            trace->push_worker[trace->npush] = best;                                     \
+            trace->push_nready[trace->npush] = (int32_t)nready;                          \
+            trace->npush++;                                                              \
+        }                                                                                \
     } while (0)
 
     /* initial pushes: every task without predecessors, ascending id */
@@ -490,7 +538,11 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
             if (running[w] >= 0 || qlen[w] == 0) continue;
             int64_t cur = nready;
             int32_t mode = MODE_FIFO;
-            if (pol.policy != POL_FIFO) {
+            if (pol.policy == POL_DMDAP_IA) {
+                mode = MODE_ABILITY; /* static priority: inspiring ability */
+            } else if (pol.policy == POL_DMDAP_BL) {
+                mode = MODE_PRIO; /* static priority: bottom level */
+            } else if (pol.policy != POL_FIFO) {
                 orc_ctrl_step(&ctl, &pol, cur, now);
                 mode = ctl.mode;
             }
@@ -523,12 +575,12 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
                 pick = forced;
             } else if (pol.policy == POL_LEARNED) {
                 /* pick already chosen by the scorer */
-            } else if (mode == MODE_ABILITY || mode == MODE_EFI || mode == MODE_EFI_LOC) {
+            } else if (mode == MODE_ABILITY || mode == MODE_EFI || mode == MODE_EFI_LOC || mode == MODE_PRIO) {
                 int64_t best_key = 0;
                 int32_t best_loc = 0;
                 for (int32_t i = 0; i < qlen[w]; ++i) {
                     int32_t t = Q[i].task;
-                    int64_t key = (mode == MODE_ABILITY) ? ia[t] : ie[t];
+                    int64_t key = (mode == MODE_ABILITY) ? ia[t] : (mode == MODE_PRIO ? bl[t] : ie[t]);
                     int32_t loc = 0;
                     if (mode == MODE_EFI_LOC)
                         loc = data_ready(t, w, pr, pc, worker, end, n_cpu, xfer) <= now;
@@ -590,7 +642,7 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
 #undef COST
 out:
     free(pr); free(pc); free(fill); free(indeg); free(newly); free(completed); free(queue);
-    free(qlen); free(busy_end); free(queued_cost); free(running);
+    free(qlen); free(busy_end); free(queued_cost); free(running); free(bl);
     return rc;
 }
 

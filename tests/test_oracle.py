@@ -124,7 +124,8 @@ def test_policy_defaults():
 
 # ------------------------------------------------------------- the simulation
 def _policy(name):
-    return oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO}[name])
+    return oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO,
+                          "dmdap_ia": oracle.POLICY_DMDAP_IA, "dmdap_bl": oracle.POLICY_DMDAP_BL}[name])
 
 
 def test_simulation_hand_traced():
@@ -285,3 +286,72 @@ def test_mlp_score_matches_float_network():
         h1 = np.clip(np.floor(np.maximum(f @ W1 + b1, 0)), 0, 255)
         h2 = np.clip(np.floor(np.maximum(h1 @ W2 + b2, 0)), 0, 255)
         assert oracle.mlp_score(k, f) == int(round((h2 @ W3 + b3) * 64))
+
+
+# ---------------------------------------------- DMDAP baselines and the trace
+@pytest.mark.parametrize("seed", range(6))
+def test_bottom_level_matches_path_enumeration(seed):
+    rng = np.random.default_rng(3000 + seed)
+    d = _rand_dag(rng, int(rng.integers(1, 14)), float(rng.uniform(0.1, 0.5)), cmax=1000)
+    for m in (inputs.Machine(1, 0, 0), inputs.Machine(4, 1, 777), inputs.Machine(8, 2, 20000),
+              inputs.Machine(0, 3, 5), inputs.Machine(3, 3, 1)):
+        np.testing.assert_array_equal(oracle.bottom_level(d, m), brute.bottom_level(d, m))
+
+
+def test_bottom_level_closed_forms():
+    """A chain of n equal tasks: rank(i) = (n - i) * wbar + (n - 1 - i) * cbar; with
+    8 CPUs + 2 GPUs, 34 of the 100 ordered worker pairs sit on distinct nodes."""
+    n = 9
+    d = _chain(n, 300, 40)
+    m = inputs.Machine(8, 2, 1000)
+    wbar, cbar = (8 * 300 + 2 * 40) // 10, 1000 * 34 // 100
+    np.testing.assert_array_equal(oracle.bottom_level(d, m), [(n - i) * wbar + (n - 1 - i) * cbar for i in range(n)])
+    # one worker: no transfer between distinct nodes, wbar = the CPU cost
+    np.testing.assert_array_equal(oracle.bottom_level(d, inputs.Machine(1, 0, 5)), [(n - i) * 300 for i in range(n)])
+
+
+@pytest.mark.parametrize("policy", ["dmdap_ia", "dmdap_bl"])
+def test_dmdap_one_worker_sums_and_validity(policy):
+    rng = np.random.default_rng(11)
+    costs = rng.integers(1, 1000, 20)
+    indep = inputs.make_dag(20, [], costs, costs)
+    assert oracle.simulate(indep, inputs.Machine(1, 0, 5), _policy(policy))["makespan"] == int(costs.sum())
+    for seed in range(6):
+        r2 = np.random.default_rng(4000 + seed)
+        d = _rand_dag(r2, int(r2.integers(2, 50)), float(r2.uniform(0.03, 0.3)), cmax=100)
+        m = inputs.Machine(int(r2.integers(1, 4)), int(r2.integers(0, 3)), int(r2.integers(0, 40)))
+        r = oracle.simulate(d, m, _policy(policy), trace=True)
+        assert r["rc"] == 0
+        assert oracle.validate(d, m, r["worker"], r["start"], r["end"], r["makespan"]) == (0, -1)
+        assert r["makespan"] >= _lower_bound(d, m)
+        assert set(r["trace"]["mode"]) == {oracle.MODE_ABILITY if policy == "dmdap_ia" else oracle.MODE_PRIO}
+
+
+@pytest.mark.parametrize("policy", ["inspirit", "fifo", "dmdap_bl"])
+def test_push_pop_trace_consistent(policy):
+    """The push/pop trace (Nready time piling): every task is pushed once and
+    popped once, on the worker it was pushed to; pushes at an event time come
+    before that time's pops, so Nready after the k-th push is k + 1 minus the
+    pops at earlier times, and Nready before a pop is the pushes up to its time
+    minus the earlier pops; times never decrease."""
+    rng = np.random.default_rng(21)
+    for _ in range(5):
+        d = _rand_dag(rng, int(rng.integers(5, 70)), float(rng.uniform(0.03, 0.25)), cmax=60)
+        m = inputs.Machine(int(rng.integers(1, 5)), int(rng.integers(0, 3)), int(rng.integers(0, 30)))
+        r = oracle.simulate(d, m, _policy(policy), trace=True)
+        tr = r["trace"]
+        n = d.n
+        assert len(tr["push_task"]) == n and len(tr["task"]) == n
+        assert sorted(tr["push_task"]) == list(range(n)) and sorted(tr["task"]) == list(range(n))
+        np.testing.assert_array_equal(tr["push_worker"], r["worker"][tr["push_task"]])
+        np.testing.assert_array_equal(tr["worker"], r["worker"][tr["task"]])
+        assert (np.diff(tr["push_t"]) >= 0).all() and (np.diff(tr["t"]) >= 0).all()
+        for k in range(n):
+            pops_before = int((tr["t"] < tr["push_t"][k]).sum())
+            assert tr["push_nready"][k] == k + 1 - pops_before
+        for j in range(n):
+            pushes = int((tr["push_t"] <= tr["t"][j]).sum())
+            assert tr["nready"][j] == pushes - j
+        # a task is popped no earlier than it was pushed
+        pushed_at = dict(zip(tr["push_task"], tr["push_t"]))
+        assert all(t >= pushed_at[x] for x, t in zip(tr["task"], tr["t"]))
