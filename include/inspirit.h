@@ -56,6 +56,12 @@ extern "C" {
 #define INSP_POLICY_FIFO 1     /* DMDA without priorities: pop in push order (Sec. 2.1) */
 #define INSP_POLICY_LEARNED 2  /* controller runs, but the pop takes the learned scorer's best candidate
                                   (highest score, ties to the lowest id); needs insp_set_scorer */
+/* DMDAP baselines (Sec. 2.1: DMDA with task priorities; Sec. 3 Observation 1):
+ * the pop always takes the highest static priority of the worker's queue, ties
+ * to the lowest id, with no Nready controller. */
+#define INSP_POLICY_DMDAP_IA 3 /* priority = inspiring ability (the ia input) */
+#define INSP_POLICY_DMDAP_BL 4 /* priority = bottom level, HEFT's upward rank (insp_bottom_level_batch);
+                                  the library computes it, the ia / ie inputs are not read */
 
 /* Controller parameters of Sec. 4.4 (the paper gives no values).  A zero
  * field takes its default for P = n_cpu + n_gpu workers and the DAG's default
@@ -160,6 +166,35 @@ int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int
  * on `stream`.  Errors: as the two calls. */
 int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
                         int64_t *start, int64_t *end, int64_t *makespan, void *stream);
+
+/* Bottom level of every task, the static priority of INSP_POLICY_DMDAP_BL:
+ * HEFT's upward rank (Topcuoglu et al. 2002, cited in Sec. 2) over the
+ * machine's mean costs, ids being a topological order:
+ *   bl[v] = wbar(v) + max over successors s of (cbar + bl[s])  (no successor: wbar(v)),
+ *   wbar(v) = floor((n_cpu * c_cpu(v) + n_gpu * c_gpu(v)) / P),
+ *   cbar = floor(xfer * D / P^2), D = P^2 - n_cpu^2 - n_gpu the ordered worker
+ *          pairs on distinct memory nodes (CPUs share one node, each GPU has its own).
+ * bl: int64[task_base[ndag]] (device or host). */
+int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream);
+
+/* Push/pop trace of a simulation (the Nready time piling of Sec. 4.4
+ * "Implementation details"), a tracing aid.  Device arrays of
+ * task_base[ndag] entries; the k-th push and the k-th pop of DAG d sit at
+ * task_base[d] + k (each DAG pushes and pops each of its tasks once):
+ *   push_*: time, task (local id), chosen worker, Nready after the push;
+ *   pop_*:  time, task, worker, Nready before the pop, pick mode
+ *           (0 FIFO, 1 ability, 2 efficiency, 3 locality then efficiency,
+ *           4 learned, 5 bottom level).
+ * At one event time the pushes come before the pops. */
+typedef struct {
+    int64_t *push_time;
+    int32_t *push_task, *push_worker, *push_nready;
+    int64_t *pop_time;
+    int32_t *pop_task, *pop_worker, *pop_nready, *pop_mode;
+} insp_trace;
+/* insp_simulate_batch that also writes the trace (device pointers only). */
+int insp_simulate_trace(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
+                        int64_t *end, int64_t *makespan, const insp_trace *trace, void *stream);
 
 /* The same simulation launched once per DAG (one warp on the GPU per launch,
  * serial on `stream`): the unbatched form used as the throughput baseline. */
@@ -292,7 +327,8 @@ int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_
  * type[n], type_cost[n_types][2] or task_cost[n][2], ia[n], ie[n] (from
  * insp_attributes or the caller's own) and the outputs worker[n], start[n],
  * end[n], makespan[1].  n above INSP_NOALLOC_MAX_TASKS gives INSP_EINVAL.
- * policy may be NULL; INSP_POLICY_LEARNED is not accepted.
+ * policy may be NULL; INSP_POLICY_LEARNED and INSP_POLICY_DMDAP_BL are not
+ * accepted.
  *
  * The first call on a device looks up the array's device address on that
  * device; make that first call before any stream capture.  Every call reuses

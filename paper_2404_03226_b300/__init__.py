@@ -14,11 +14,11 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import _lib
-from ._lib import (INSP_POLICY_FIFO, INSP_POLICY_INSPIRIT, INSP_POLICY_LEARNED, InspError,  # noqa: F401
-                   insp_policy, insp_tuning)
+from ._lib import (INSP_POLICY_DMDAP_BL, INSP_POLICY_DMDAP_IA, INSP_POLICY_FIFO,  # noqa: F401
+                   INSP_POLICY_INSPIRIT, INSP_POLICY_LEARNED, InspError, insp_policy, insp_tuning)
 
 __all__ = ["Machine", "DagBatch", "InspError", "insp_policy", "insp_tuning", "INSP_POLICY_INSPIRIT",
-           "INSP_POLICY_FIFO", "INSP_POLICY_LEARNED"]
+           "INSP_POLICY_FIFO", "INSP_POLICY_LEARNED", "INSP_POLICY_DMDAP_IA", "INSP_POLICY_DMDAP_BL"]
 
 
 def _np(a, dtype):
@@ -94,6 +94,25 @@ class DagBatch:
         f = _lib.insp_simulate_per_dag if per_dag else _lib.insp_simulate_batch
         f(self.handle, ia, ie, sch.worker, sch.start, sch.end, sch.makespan, stream or torch.cuda.current_stream())
         return sch
+
+    def simulate_trace(self, ia, ie, stream=None):
+        """Schedule plus the push/pop trace: (Schedule, dict of device tensors, the
+        k-th push / pop of DAG d at task_base[d] + k)."""
+        import torch
+        sch = Schedule(self._out(self.n_tasks, torch.int32), self._out(self.n_tasks, torch.int64),
+                       self._out(self.n_tasks, torch.int64), self._out(self.ndag, torch.int64))
+        tr = {k: self._out(self.n_tasks, torch.int64 if k.endswith("_time") else torch.int32)
+              for k in _lib.TRACE_FIELDS}
+        _lib.insp_simulate_trace(self.handle, ia, ie, sch.worker, sch.start, sch.end, sch.makespan, tr,
+                                 stream or torch.cuda.current_stream())
+        return sch, tr
+
+    def bottom_level(self, stream=None):
+        """int64 CUDA tensor: each task's bottom level (static priority of INSP_POLICY_DMDAP_BL)."""
+        import torch
+        bl = self._out(self.n_tasks, torch.int64)
+        _lib.insp_bottom_level_batch(self.handle, bl, stream or torch.cuda.current_stream())
+        return bl
 
     def evaluate(self, unit_time_ns=None, stream=None):
         """Attributes and schedule in one pipelined call: (ia, ie, Schedule)."""

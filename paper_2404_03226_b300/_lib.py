@@ -10,7 +10,7 @@ import os
 from . import build as _build
 
 INSP_OK, INSP_EINVAL, INSP_ENOTTOPO, INSP_ENOMEM, INSP_ECUDA, INSP_ETIMEOUT, INSP_EOVERFLOW = range(7)
-INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO, INSP_POLICY_LEARNED = 0, 1, 2
+INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO, INSP_POLICY_LEARNED, INSP_POLICY_DMDAP_IA, INSP_POLICY_DMDAP_BL = 0, 1, 2, 3, 4
 ERROR_NAMES = {0: "INSP_OK", 1: "INSP_EINVAL", 2: "INSP_ENOTTOPO", 3: "INSP_ENOMEM", 4: "INSP_ECUDA",
                5: "INSP_ETIMEOUT", 6: "INSP_EOVERFLOW"}
 
@@ -29,6 +29,12 @@ class insp_tuning(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class insp_trace(ctypes.Structure):
+    _fields_ = [("push_time", ctypes.c_void_p), ("push_task", ctypes.c_void_p), ("push_worker", ctypes.c_void_p),
+                ("push_nready", ctypes.c_void_p), ("pop_time", ctypes.c_void_p), ("pop_task", ctypes.c_void_p),
+                ("pop_worker", ctypes.c_void_p), ("pop_nready", ctypes.c_void_p), ("pop_mode", ctypes.c_void_p)]
 
 
 class InspError(RuntimeError):
@@ -54,6 +60,8 @@ _PROTOS = {
     "insp_simulate": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_evaluate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_simulate_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(insp_trace), _vp]),
+    "insp_bottom_level_batch": (ctypes.c_int, [_vp, _vp, _vp]),
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -287,3 +295,18 @@ def insp_batch_get_tuning(b) -> insp_tuning:
 
 def insp_machine_set_tuning(m, t: insp_tuning) -> None:
     check(lib().insp_machine_set_tuning(m, ctypes.byref(t)))
+
+
+TRACE_FIELDS = ("push_time", "push_task", "push_worker", "push_nready", "pop_time", "pop_task", "pop_worker",
+                "pop_nready", "pop_mode")
+
+
+def insp_simulate_trace(b, ia, ie, worker, start, end, makespan, trace: dict, stream=None) -> None:
+    """trace: dict of the TRACE_FIELDS names to device tensors."""
+    t = insp_trace(*[ptr(trace[k]) for k in TRACE_FIELDS])
+    check(lib().insp_simulate_trace(b, ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end), ptr(makespan),
+                                    ctypes.byref(t), stream_ptr(stream)))
+
+
+def insp_bottom_level_batch(b, bl, stream=None) -> None:
+    check(lib().insp_bottom_level_batch(b, ptr(bl), stream_ptr(stream)))

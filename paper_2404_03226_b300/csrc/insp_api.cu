@@ -103,6 +103,7 @@ struct Scratch {
     DBuf ie_rec, ie_acc;                                           // inspiring efficiency
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
     DBuf ie_ring;  // per-warp window rings of the pull efficiency sweep (global, meant to stay in L2)
+    DBuf blevel;   // bottom levels (INSP_POLICY_DMDAP_BL)
     DBuf step;              // insp::StepCounters (device-side epoch and record tags)
     // streams and events of the pipelined step: q[0] runs the efficiency sweep
     // when it overlaps the ability sweep, q[1 + g] the simulation of size group g
@@ -274,6 +275,7 @@ int alloc_scratch(insp_batch *b) {
         CU(cudaMemcpy(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice));
     }
     if ((rc = S.make_streams())) return rc;
+    if (b->mach.pol.policy == INSP_POLICY_DMDAP_BL && (rc = S.blevel.alloc(N * 8))) return rc;
     if ((rc = alloc_ia(b))) return rc;
     // inspiring efficiency: global-memory sweep scratch unless the pull form applies
     // (allocated later if a call needs the global form)
@@ -374,7 +376,7 @@ INSP_API int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, 
     if (xfer_ns < 0 || xfer_ns > insp::TIME_BOUND) return fail(INSP_EINVAL, "xfer_ns out of range");
     insp_policy p{};
     if (policy) p = *policy;
-    if (p.policy < INSP_POLICY_INSPIRIT || p.policy > INSP_POLICY_LEARNED) return fail(INSP_EINVAL, "unknown policy");
+    if (p.policy < INSP_POLICY_INSPIRIT || p.policy > INSP_POLICY_DMDAP_BL) return fail(INSP_EINVAL, "unknown policy");
     if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
         p.k_inc_ns < 0)
         return fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");
@@ -770,6 +772,24 @@ struct Rollout {
     int32_t *feat_task = nullptr, *feat = nullptr, *feat_n = nullptr;
 };
 
+// Bottom levels of every task of the batch into bl (device), counter slot 12.
+int launch_blevel_all(insp_batch *b, int64_t *bl, cudaStream_t s) {
+    if (b->ndag == 0) return INSP_OK;
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    const int32_t nc = b->mach.n_cpu, ng = b->mach.n_gpu;
+    const __int128 P = nc + ng;
+    const __int128 D = P * P - __int128(nc) * nc - ng;  // ordered worker pairs on distinct memory nodes
+    const int64_t cbar = int64_t(__int128(b->mach.xfer) * D / (P * P));
+    int32_t *ctr = b->counters.as<int32_t>() + 12;
+    CU(cudaMemsetAsync(ctr, 0, 4, s));
+    const int grid = std::max(1, std::min(di.sms * 8, (b->ndag + 7) / 8));
+    insp::launch_blevel(b->dev(), nc, ng, cbar, b->order.as<int32_t>(), ctr, bl, grid, s);
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
 // Arguments of the simulation kernel over the whole batch (size order, counter 8).
 void fill_sim_args(insp_batch *b, insp::SimArgs &A, const int32_t *d_ia, const int32_t *d_ie, int32_t *d_worker,
                    int64_t *d_start, int64_t *d_end, int64_t *d_mk, const Rollout &ro) {
@@ -817,6 +837,7 @@ void fill_sim_args(insp_batch *b, insp::SimArgs &A, const int32_t *d_ia, const i
     A.feat_n = ro.feat_n;
     A.n_order = b->ndag;
     A.single_dag = -1;
+    A.blevel = b->mach.pol.policy == INSP_POLICY_DMDAP_BL ? S.blevel.as<int64_t>() : nullptr;
 }
 
 // The batched simulation of the DAGs A.order[0, A.n_order) on stream s.
@@ -836,7 +857,8 @@ int launch_sim_part(insp_batch *b, const insp::SimArgs &A, cudaStream_t s) {
 }
 
 int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
-                  int64_t *end, int64_t *makespan, void *stream, bool per_dag, const Rollout &ro = Rollout()) {
+                  int64_t *end, int64_t *makespan, void *stream, bool per_dag, const Rollout &ro = Rollout(),
+                  const insp_trace *tr = nullptr) {
     if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
     const bool learned = b->mach.pol.policy == INSP_POLICY_LEARNED;
     if (learned && !(b->owner && b->owner->has_scorer))
@@ -859,6 +881,18 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         CU(cudaMemsetAsync(b->status.p, 0, size_t(b->ndag) * 4, s));
         insp::SimArgs A{};
         fill_sim_args(b, A, d_ia, d_ie, d_worker, d_start, d_end, d_mk, ro);
+        if (tr) {
+            A.tr_push_time = tr->push_time;
+            A.tr_push_task = tr->push_task;
+            A.tr_push_worker = tr->push_worker;
+            A.tr_push_nready = tr->push_nready;
+            A.tr_pop_time = tr->pop_time;
+            A.tr_pop_task = tr->pop_task;
+            A.tr_pop_worker = tr->pop_worker;
+            A.tr_pop_nready = tr->pop_nready;
+            A.tr_pop_mode = tr->pop_mode;
+        }
+        if (A.blevel && (rc = launch_blevel_all(b, S.blevel.as<int64_t>(), s))) return rc;
         if (per_dag) {
             for (int d = 0; d < b->ndag; ++d) {
                 A.single_dag = d;
@@ -887,6 +921,35 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
 INSP_API int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
                                  int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
     return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_simulate_trace(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker,
+                                 int64_t *start, int64_t *end, int64_t *makespan, const insp_trace *trace,
+                                 void *stream) {
+    if (!b || !trace) return fail(INSP_EINVAL, "NULL argument");
+    const void *ptrs[] = {ia, ie, worker, start, end, makespan, trace->push_time, trace->push_task,
+                          trace->push_worker, trace->push_nready, trace->pop_time, trace->pop_task,
+                          trace->pop_worker, trace->pop_nready, trace->pop_mode};
+    if (b->ndag > 0 && b->n_total > 0)
+        for (const void *q : ptrs)
+            if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false, Rollout(), trace);
+}
+
+INSP_API int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream) {
+    if (!b || !bl) return fail(INSP_EINVAL, "NULL argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    int64_t *d_bl;
+    bool staged;
+    int rc = stage_out(b->sc->s_start, bl, b->n_total, d_bl, staged);
+    if (rc) return rc;
+    if ((rc = launch_blevel_all(b, d_bl, s))) return rc;
+    if (staged) {
+        if (b->n_total) CU(cudaMemcpyAsync(bl, d_bl, size_t(b->n_total) * 8, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    return INSP_OK;
 }
 
 INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
@@ -921,6 +984,7 @@ INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int
     insp::launch_step_begin(S.step.as<insp::StepCounters>(), b->n_items, s);
     insp::SimArgs A{};
     fill_sim_args(b, A, d_ia, d_ie, d_worker, d_start, d_end, d_mk, Rollout());
+    if (A.blevel && (rc = launch_blevel_all(b, S.blevel.as<int64_t>(), s))) return rc;
     cudaStream_t s_ie = ov ? S.q[0] : s;
     if (ov) {
         CU(cudaEventRecord(S.ev_fork, s));

@@ -115,8 +115,8 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     if (n_types < 1 || n_types > 64) return na_fail(INSP_EINVAL, "n_types must be in 1..64");
     insp_policy p{};
     if (policy) p = *policy;
-    if (p.policy != INSP_POLICY_INSPIRIT && p.policy != INSP_POLICY_FIFO)
-        return na_fail(INSP_EINVAL, "policy must be INSP_POLICY_INSPIRIT or INSP_POLICY_FIFO");
+    if (p.policy != INSP_POLICY_INSPIRIT && p.policy != INSP_POLICY_FIFO && p.policy != INSP_POLICY_DMDAP_IA)
+        return na_fail(INSP_EINVAL, "policy must be INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO or INSP_POLICY_DMDAP_IA");
     if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
         p.k_inc_ns < 0)
         return na_fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");

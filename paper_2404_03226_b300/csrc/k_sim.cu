@@ -28,7 +28,7 @@ constexpr int SIM_WARPS = 8;  // most warps per CTA (the autotuner may launch fe
 constexpr int NL_C = 128;     // released-task buffer per warp in shared memory
 constexpr int NODE_NONE = 0xff;
 
-enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4 };
+enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
 enum { ST_INC = 0, ST_DEC = 1 };
 
 // POOL_C: ready-pool entries per warp kept in shared memory (the queue
@@ -207,7 +207,12 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         const int32_t cslack = A.c > 0 ? A.c : (P / 2 > 1 ? P / 2 : 1);
         const int64_t kt = A.k_inc_tasks > 0 ? A.k_inc_tasks : P;
         const int64_t kns = A.k_inc_ns > 0 ? A.k_inc_ns : A.unit_time_def[d];
-        const bool fifo_policy = (A.policy == INSP_POLICY_FIFO);
+        // static pick modes: DMDA (FIFO) and the DMDAP baselines; -1: the Nready controller decides
+        const int32_t static_mode = A.policy == INSP_POLICY_FIFO       ? MODE_FIFO
+                                    : A.policy == INSP_POLICY_DMDAP_IA ? MODE_ABILITY
+                                    : A.policy == INSP_POLICY_DMDAP_BL ? MODE_PRIO
+                                                                       : -1;
+        const bool by_level = A.policy == INSP_POLICY_DMDAP_BL;
 
         // per-DAG init: cost table, per-task release state
         if (smem_types) {
@@ -236,7 +241,15 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         auto push = [&](int32_t t) {
             const int2 a = st_a[t];
             const longlong2 b = st_b[t];
-            const int32_t tia = g_ia[t], tie = g_ie[t];
+            int32_t tia, tie;
+            if (by_level) {  // the pool's two priority fields carry the bottom level (< 2^54)
+                const int64_t l = A.blevel[tb + t];
+                tia = int32_t(l >> 31);
+                tie = int32_t(l & 0x7fffffff);
+            } else {
+                tia = g_ia[t];
+                tie = g_ie[t];
+            }
             const int64_t cc = cost_of(t, 0), cg = cost_of(t, 1);
             uint64_t k0 = ~0ull, k1 = ~0ull;
             int64_t dr0 = 0, dr1 = 0;
@@ -261,6 +274,13 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 const int64_t c = ws < n_cpu ? cc : cg;
                 if (hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
                 pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
+                if (A.tr_push_time) {
+                    const int64_t r = tb + seq;
+                    A.tr_push_time[r] = now;
+                    A.tr_push_task[r] = t;
+                    A.tr_push_worker[r] = ws;
+                    A.tr_push_nready[r] = nready + 1;
+                }
             }
             seq += 1;
             nready += 1;
@@ -278,8 +298,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         // Returns false (no fault) if w has no entry, which would be a bookkeeping error.
         auto pop = [&](int32_t w) -> bool {
             const int64_t cur = nready;
-            int32_t mode = MODE_FIFO;
-            if (!fifo_policy) {
+            int32_t mode = static_mode;
+            if (static_mode < 0) {
                 ctrl_step(ctl, cur, now, tw, s_inc, s_dec, dec_step, cslack, kt, kns);
                 mode = ctl.mode;
             }
@@ -360,6 +380,21 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                         }
                         __syncwarp();
                     }
+                } else if (mode == MODE_PRIO) {
+                    // highest bottom level (54 bits), then lowest id: the lane's best by both, then
+                    // a warp max of the level and, among the lanes holding it, of the id key
+                    uint32_t lo_best = 0;
+                    for (int32_t i = lane; i < nready; i += 32) {
+                        const int32_t e = pool.idw(i);
+                        if ((e >> 24) != w) continue;
+                        const uint64_t lvl = (1ull << 63) | (uint64_t(uint32_t(pool.ia(i))) << 31) |
+                                             uint64_t(uint32_t(pool.ie(i)));
+                        const uint32_t lo = 0x7fffffffu - uint32_t(e & 0xffffff);
+                        if (lvl > best || (lvl == best && lo > lo_best)) { best = lvl; lo_best = lo; bi = i; }
+                    }
+                    const uint64_t top = warp_max_u64(best);
+                    const uint32_t lo_top = __reduce_max_sync(FULL, best == top ? lo_best : 0u);
+                    if (best != top || lo_best != lo_top) { best = 0; bi = -1; }
                 } else {
                     for (int32_t i = lane; i < nready; i += 32) {
                         const int32_t e = pool.idw(i);
@@ -401,6 +436,14 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 A.worker[tb + t] = w;
                 A.start[tb + t] = s;
                 A.end[tb + t] = e;
+                if (A.tr_pop_time) {
+                    const int64_t r = tb + npop - 1;
+                    A.tr_pop_time[r] = now;
+                    A.tr_pop_task[r] = t;
+                    A.tr_pop_worker[r] = w;
+                    A.tr_pop_nready[r] = int32_t(cur);
+                    A.tr_pop_mode[r] = LEARNED ? MODE_LEARNED : mode;
+                }
             }
             __syncwarp();
             return true;

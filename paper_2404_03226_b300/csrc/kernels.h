@@ -39,6 +39,12 @@ struct SimArgs {
     const int32_t *force_pop, *force_task, *feat_pop;
     int32_t feat_cap;
     int32_t *feat_task, *feat, *feat_n;
+    // static priority of INSP_POLICY_DMDAP_BL (bottom level per task, global index)
+    const int64_t *blevel;
+    // push/pop trace (null: off), indexed by task_base[d] + k for the k-th push / pop of DAG d
+    int64_t *tr_push_time, *tr_pop_time;
+    int32_t *tr_push_task, *tr_push_worker, *tr_push_nready;
+    int32_t *tr_pop_task, *tr_pop_worker, *tr_pop_nready, *tr_pop_mode;
 };
 
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
@@ -79,6 +85,10 @@ void launch_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int3
                   float eps, float wd, cudaStream_t s);
 void launch_quantize(int64_t nw, const float *w, uint16_t *out, cudaStream_t s);
 void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s);
+// Bottom levels (HEFT upward rank over mean costs) of every task; cbar = the mean
+// transfer cost (computed by the host).  One warp per DAG, DAGs in size order.
+void launch_blevel(const DevBatch &B, int32_t n_cpu, int32_t n_gpu, int64_t cbar, const int32_t *order,
+                   int32_t *counter, int64_t *bl, int grid, cudaStream_t s);
 int sim_occupancy(bool learned, int warps, int queue);
 int sim_max_warps();
 void launch_sim_single(const SimArgs &A, cudaStream_t s);

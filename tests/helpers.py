@@ -9,7 +9,7 @@ import oracle
 def machine_policy(policy_name):
     from paper_2404_03226_b300 import insp_policy
     p = insp_policy()
-    p.policy = {"inspirit": 0, "fifo": 1}[policy_name]
+    p.policy = {"inspirit": 0, "fifo": 1, "dmdap_ia": 3, "dmdap_bl": 4}[policy_name]
     return p
 
 
@@ -30,7 +30,8 @@ def gpu_run(batch, machine, policy="inspirit", unit_time=None, per_dag=False):
 
 def oracle_dag(batch, d, machine, policy="inspirit", unit_time=None):
     g = batch.dag(d)
-    pol = oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO}[policy])
+    pol = oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO,
+                         "dmdap_ia": oracle.POLICY_DMDAP_IA, "dmdap_bl": oracle.POLICY_DMDAP_BL}[policy])
     return g, oracle.simulate(g, machine, pol, unit_time=unit_time)
 
 
