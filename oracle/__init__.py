@@ -98,6 +98,8 @@ def _L():
         lib.orc_validate.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
                                      ctypes.c_int64, _i32p, _i64p, _i64p, ctypes.c_int64, _i32p]
         _dp = ctypes.POINTER(ctypes.c_double)
+        lib.orc_unit_time_search.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, ctypes.POINTER(ctypes.c_uint8),
+                                             ctypes.c_int32, _i64p, _i32p]
         lib.orc_bottom_level.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int32, ctypes.c_int32,
                                          ctypes.c_int64, _i64p]
         lib.orc_mlp_loss_grad.restype = ctypes.c_double
@@ -231,6 +233,19 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
         out["feat_task"] = bufs["feat_task"][:nf]
         out["feat"] = bufs["feat"][:nf * MLP_IN].reshape(nf, MLP_IN)
     return out
+
+
+def unit_time_search(dag, k_max: int = 16) -> tuple[int, int]:
+    """(T, k): the searched unit time of a DAG and its exponent (see orc_unit_time_search)."""
+    T = np.zeros(1, np.int64)
+    k = np.zeros(1, np.int32)
+    ty = np.ascontiguousarray(dag.type if dag.n > 0 else np.zeros(1), np.uint8)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
+    rc = _L().orc_unit_time_search(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_gpu) if dag.n else
+                                   np.ones(1, np.int64), _i64p), ty.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                   k_max, _p(T, _i64p), _p(k, _i32p))
+    assert rc == OK
+    return int(T[0]), int(k[0])
 
 
 def bottom_level(dag, machine) -> np.ndarray:

@@ -79,3 +79,19 @@ def bottom_level(dag, machine):
             best = max(best, sum(wbar(x) for x in p) + (len(p) - 1) * cbar)
         res.append(best)
     return res
+
+
+def layers(dag):
+    """Topological layer of every task: the most edges on any path from a
+    source to it, by enumerating all paths from every source."""
+    preds = [0] * dag.n
+    for u in range(dag.n):
+        for s in dag.col_idx[dag.row_ptr[u]:dag.row_ptr[u + 1]]:
+            preds[int(s)] += 1
+    best = [0] * dag.n
+    for v in range(dag.n):
+        if preds[v]:
+            continue
+        for p in all_paths_from(dag, v):
+            best[p[-1]] = max(best[p[-1]], len(p) - 1)
+    return best

@@ -16,6 +16,9 @@
  *                (GPU execution times, v's own time included, unlimited
  *                workers, tasks outside v's cone treated as done) finishes
  *                within the unit time T.  Plain longest-path DP over the cone.
+ *  orc_unit_time_search  automatic choice of the unit time T of Sec. 4.3 (the
+ *                paper tunes it by hand): the smallest T = med * 2^k whose IE
+ *                separates as many tasks as the DAG's structure does.
  *  orc_bottom_level  the static priority of the DMDAP baseline (Sec. 2.1,
  *                Sec. 3 Observation 1): HEFT's upward rank (Topcuoglu et al.,
  *                2002, cited in Sec. 2) over mean worker costs.
@@ -199,6 +202,59 @@ EXPORT int64_t orc_default_unit_time(int32_t n, const int64_t *c_gpu) {
     free(s);
     int64_t T = 4 * med;
     return T < 1 ? 1 : T;
+}
+
+/* ------------------------------------------------------- unit-time search */
+
+static int64_t count_distinct_i64(int64_t *v, int32_t n) {
+    if (n <= 0) return 0;
+    qsort(v, (size_t)n, sizeof(int64_t), cmp_i64);
+    int64_t c = 1;
+    for (int32_t i = 1; i < n; ++i) c += v[i] != v[i - 1];
+    return c;
+}
+
+/* Automatic choice of the unit time T (Sec. 4.3 tunes T by hand, iteratively;
+ * this is the batched search that replaces the hand tuning): candidates
+ * T_k = med * 2^k for k = 0..k_max (med = the lower median GPU cost, so T_2 is
+ * the default unit time; saturating at 2^62), and the chosen T is the smallest
+ * candidate whose IE takes at least
+ *     target = min(#distinct (topological layer, type) pairs, #distinct IA)
+ * distinct values over the DAG's tasks, else T_{k_max}.  The topological layer
+ * of a task is the number of edges on the longest path reaching it from a
+ * source.  An empty DAG gets T = 1.  Outputs T and its k. */
+EXPORT int orc_unit_time_search(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const int64_t *c_gpu,
+                                const uint8_t *type, int32_t k_max, int64_t *T_out, int32_t *k_out) {
+    if (n < 0 || k_max < 0 || k_max > 62) return ORC_EINVAL;
+    *T_out = 1;
+    *k_out = 0;
+    if (n == 0) return ORC_OK;
+    int64_t med = orc_default_unit_time(n, c_gpu) / 4; /* the default is 4 x the lower median */
+    int32_t *ia = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *ie = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *layer = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int64_t *tmp = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!ia || !ie || !layer || !tmp) { free(ia); free(ie); free(layer); free(tmp); return ORC_ENOMEM; }
+    orc_ia(n, row_ptr, col_idx, ia);
+    for (int32_t u = 0; u < n; ++u) /* ids are topological: u's layer is final here */
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (layer[col_idx[e]] < layer[u] + 1) layer[col_idx[e]] = layer[u] + 1;
+    for (int32_t i = 0; i < n; ++i) tmp[i] = ia[i];
+    int64_t d_ia = count_distinct_i64(tmp, n);
+    for (int32_t i = 0; i < n; ++i) tmp[i] = (int64_t)layer[i] * 256 + type[i];
+    int64_t d_pairs = count_distinct_i64(tmp, n);
+    int64_t target = d_ia < d_pairs ? d_ia : d_pairs;
+    const int64_t cap = ((int64_t)1) << 62;
+    for (int32_t k = 0; k <= k_max; ++k) {
+        int64_t T = med > (cap >> k) ? cap : med << k;
+        orc_ie(n, row_ptr, col_idx, c_gpu, T, ie);
+        for (int32_t i = 0; i < n; ++i) tmp[i] = ie[i];
+        *T_out = T;
+        *k_out = k;
+        if (count_distinct_i64(tmp, n) >= target) break;
+    }
+    free(ia); free(ie); free(layer); free(tmp);
+    return ORC_OK;
 }
 
 /* ------------------------------------------------------------ bottom level */

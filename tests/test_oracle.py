@@ -355,3 +355,44 @@ def test_push_pop_trace_consistent(policy):
         # a task is popped no earlier than it was pushed
         pushed_at = dict(zip(tr["push_task"], tr["push_t"]))
         assert all(t >= pushed_at[x] for x, t in zip(tr["task"], tr["t"]))
+
+
+# ------------------------------------------------------- unit-time search
+@pytest.mark.parametrize("n", [1, 2, 5, 8, 9, 33])
+def test_unit_time_search_chain_closed_form(n):
+    """Chain of n tasks of GPU cost c: IA and the layers take n distinct values,
+    and IE at T = c 2^k takes min(n, 2^k) values, so the search stops at the
+    first k with 2^k >= n."""
+    c = 7
+    d = _chain(n, 50, c)
+    k = int(np.ceil(np.log2(n))) if n > 1 else 0
+    assert oracle.unit_time_search(d, 16) == (c << k, k)
+    if k > 1:  # a cap below the answer returns the last candidate
+        assert oracle.unit_time_search(d, k - 1) == (c << (k - 1), k - 1)
+
+
+def test_unit_time_search_special_cases():
+    # independent tasks: IA is all 0 (one value), so the first candidate (the lower median) suffices
+    d = inputs.make_dag(6, [], [9] * 6, [5, 1, 8, 3, 3, 20])
+    assert oracle.unit_time_search(d) == (3, 0)
+    # empty DAG
+    assert oracle.unit_time_search(inputs.make_dag(0, [], [], [])) == (1, 0)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_unit_time_search_matches_brute_force(seed):
+    rng = np.random.default_rng(5000 + seed)
+    n = int(rng.integers(2, 12))
+    d = _rand_dag(rng, n, float(rng.uniform(0.15, 0.5)), cmax=40)
+    d = inputs.make_dag(n, [(u, int(v)) for u in range(n) for v in d.col_idx[d.row_ptr[u]:d.row_ptr[u + 1]]],
+                        d.c_cpu, d.c_gpu, type=rng.integers(0, 3, n))
+    med = int(np.sort(d.c_gpu)[(n - 1) // 2])
+    lay = brute.layers(d)
+    target = min(len({(lay[i], int(d.type[i])) for i in range(n)}), len(set(brute.ia(d))))
+    want = None
+    for k in range(12):
+        if len(set(brute.ie(d, med << k))) >= target:
+            want = (med << k, k)
+            break
+    assert want is not None
+    assert oracle.unit_time_search(d, 11) == want
