@@ -167,6 +167,19 @@ int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int
 int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
                         int64_t *start, int64_t *end, int64_t *makespan, void *stream);
 
+/* Automatic unit time per DAG (Sec. 4.3 tunes T by hand, iteratively; this
+ * search replaces the hand tuning): candidates T_k = med * 2^k for
+ * k = 0..k_max (med = the lower median GPU cost, so T_2 is the default;
+ * saturating at 2^62); the chosen T is the smallest candidate whose IE takes at
+ * least min(#distinct (topological layer, type) pairs, #distinct IA) distinct
+ * values over the DAG's tasks, else T_{k_max}.  The topological layer of a
+ * task is the most edges on a path reaching it from a source.  An empty DAG
+ * gets T = 1.  unit_time_ns: int64[ndag] (device or host), ready to pass to
+ * insp_attributes_batch / insp_evaluate_batch.  Synchronous; allocates its
+ * scratch for the call.  Errors: INSP_EINVAL (k_max outside 0..62),
+ * INSP_ENOMEM, INSP_ECUDA, INSP_ETIMEOUT. */
+int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_time_ns, void *stream);
+
 /* Bottom level of every task, the static priority of INSP_POLICY_DMDAP_BL:
  * HEFT's upward rank (Topcuoglu et al. 2002, cited in Sec. 2) over the
  * machine's mean costs, ids being a topological order:

@@ -107,6 +107,13 @@ class DagBatch:
                                  stream or torch.cuda.current_stream())
         return sch, tr
 
+    def unit_time_search(self, k_max: int = 16, stream=None):
+        """int64 CUDA tensor [ndag]: the searched unit time of every DAG."""
+        import torch
+        ut = self._out(self.ndag, torch.int64)
+        _lib.insp_unit_time_search(self.handle, k_max, ut, stream or torch.cuda.current_stream())
+        return ut
+
     def bottom_level(self, stream=None):
         """int64 CUDA tensor: each task's bottom level (static priority of INSP_POLICY_DMDAP_BL)."""
         import torch

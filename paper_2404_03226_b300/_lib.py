@@ -62,6 +62,7 @@ _PROTOS = {
     "insp_evaluate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(insp_trace), _vp]),
     "insp_bottom_level_batch": (ctypes.c_int, [_vp, _vp, _vp]),
+    "insp_unit_time_search": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -310,3 +311,7 @@ def insp_simulate_trace(b, ia, ie, worker, start, end, makespan, trace: dict, st
 
 def insp_bottom_level_batch(b, bl, stream=None) -> None:
     check(lib().insp_bottom_level_batch(b, ptr(bl), stream_ptr(stream)))
+
+
+def insp_unit_time_search(b, k_max: int, unit_time_ns, stream=None) -> None:
+    check(lib().insp_unit_time_search(b, int(k_max), ptr(unit_time_ns), stream_ptr(stream)))

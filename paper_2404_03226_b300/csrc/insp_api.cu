@@ -936,6 +936,79 @@ INSP_API int insp_simulate_trace(insp_batch *b, const int32_t *ia, const int32_t
     return simulate_impl(b, ia, ie, worker, start, end, makespan, stream, false, Rollout(), trace);
 }
 
+INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_time_ns, void *stream) {
+    if (!b || !unit_time_ns) return fail(INSP_EINVAL, "NULL argument");
+    if (k_max < 0 || k_max > 62) return fail(INSP_EINVAL, "k_max must be in 0..62");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    b->last_stream = s;
+    const int nd = b->ndag;
+    if (nd == 0) return INSP_OK;
+    int rc;
+    DeviceInfo di;
+    if ((rc = device_info(di))) return rc;
+    Scratch &S = *b->sc;
+    const int64_t N = std::max<int64_t>(b->n_total, 1);
+    // the DAGs' bitmap slices: n * n_types bits each (the IA and IE marks use the first n)
+    std::vector<int64_t> bm_base(nd + 1, 0);
+    for (int d = 0; d < nd; ++d) {
+        const int64_t n = b->h_task_base[d + 1] - b->h_task_base[d];
+        bm_base[d + 1] = bm_base[d] + (n * std::max(b->n_types, 1) + 31) / 32;
+    }
+    DBuf ia, ie, layer, bm, bmb, target, done, chosen, ut, ctr;
+    if ((rc = ia.alloc(N * 4)) || (rc = ie.alloc(N * 4)) || (rc = layer.alloc(N * 4)) ||
+        (rc = bm.alloc(std::max<int64_t>(bm_base[nd], 1) * 4)) || (rc = target.alloc(nd * 8)) ||
+        (rc = done.alloc(nd * 4)) || (rc = chosen.alloc(nd * 8)) || (rc = ut.alloc(nd * 8)) || (rc = ctr.alloc(256)) ||
+        (rc = copy_in(bmb, bm_base.data(), bm_base.size() * 8)))
+        return rc;
+    if (!b->pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
+    CU(cudaMemsetAsync(done.p, 0, size_t(nd) * 4, s));
+    CU(cudaMemsetAsync(ctr.p, 0, 256, s));
+    CU(cudaMemsetAsync(b->status.p, 0, size_t(nd) * 4, s));
+    const insp::DevBatch B = b->dev();
+    insp::StepCounters *sc = S.step.as<insp::StepCounters>();
+    int32_t *c = ctr.as<int32_t>();  // 0: ability, 1: targets, 8 + 4k..: per candidate, 63: decided DAGs
+    const int32_t *order = b->order.as<int32_t>();
+    const int grid = std::max(1, std::min(di.sms * 8, (nd + 7) / 8));
+    insp::launch_step_begin(sc, b->n_items, s);
+    insp::launch_ia(B, order, nd, c + 0, S.ia_bits.as<uint32_t>(), b->ia_slot, S.ia_done.as<int32_t>(), &sc->epoch,
+                    ia.as<int32_t>(), b->status.as<int32_t>(), std::min(b->grid_ia, nd), b->tun.ia_warps, s);
+    insp::launch_search_target(B, order, c + 1, ia.as<int32_t>(), layer.as<int32_t>(), bm.as<uint32_t>(),
+                               bmb.as<int64_t>(), target.as<int64_t>(), grid, s);
+    const int64_t max_med = std::max<int64_t>(1, b->max_unit_def / 4), cap = int64_t(1) << 62;
+    for (int32_t k = 0; k <= k_max; ++k) {
+        int32_t *ck = c + 8 + 4 * (k % 12);
+        CU(cudaMemsetAsync(ck, 0, 16, s));
+        insp::launch_search_ut(nd, k, b->unit_time_def.as<int64_t>(), done.as<int32_t>(), ut.as<int64_t>(), s);
+        const int64_t t_max = max_med > (cap >> k) ? cap : max_med << k;
+        const bool wide = t_max >= 0x7fffffffLL;
+        insp::launch_step_begin(sc, b->n_items, s);
+        if (b->pull && !wide) {
+            const int wpc = b->tun.ie_warps;
+            insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base_lpt.as<int64_t>(),
+                                 b->item_dag_lpt.as<int32_t>(), 0, b->n_items, ck + 0, ut.as<int64_t>(), b->W,
+                                 S.ie_ring.as<int32_t>(), ie.as<int32_t>(), b->grid_ie_pull, wpc, s);
+        } else {
+            if (!b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
+            insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ck + 0, ut.as<int64_t>(), S.ie_rec.as<uint4>(),
+                            b->ie_rec_stride, S.ie_acc.p, b->W, wide, &sc->tag_base, ie.as<int32_t>(), b->grid_ie, s);
+        }
+        insp::launch_search_step(B, order, ck + 1, ie.as<int32_t>(), bm.as<uint32_t>(), bmb.as<int64_t>(),
+                                 target.as<int64_t>(), ut.as<int64_t>(), done.as<int32_t>(), chosen.as<int64_t>(),
+                                 c + 63, grid, s);
+        CU(cudaGetLastError());
+        int32_t n_done = 0;
+        CU(cudaMemcpyAsync(&n_done, c + 63, 4, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (n_done >= nd) break;
+    }
+    insp::launch_search_final(nd, k_max, b->unit_time_def.as<int64_t>(), done.as<int32_t>(), chosen.as<int64_t>(), s);
+    CU(cudaGetLastError());
+    CU(cudaMemcpyAsync(unit_time_ns, chosen.p, size_t(nd) * 8, cudaMemcpyDefault, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<int32_t> st;
+    return first_status(b, st);
+}
+
 INSP_API int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream) {
     if (!b || !bl) return fail(INSP_EINVAL, "NULL argument");
     cudaStream_t s = static_cast<cudaStream_t>(stream);

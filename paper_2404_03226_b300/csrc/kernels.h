@@ -85,6 +85,17 @@ void launch_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int3
                   float eps, float wd, cudaStream_t s);
 void launch_quantize(int64_t nw, const float *w, uint16_t *out, cudaStream_t s);
 void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s);
+// Unit-time search (k_search.cu).
+void launch_search_target(const DevBatch &B, const int32_t *order, int32_t *counter, const int32_t *ia,
+                          int32_t *layer, uint32_t *bitmap, const int64_t *bm_base, int64_t *target, int grid,
+                          cudaStream_t s);
+void launch_search_ut(int32_t ndag, int32_t k, const int64_t *unit_time_def, const int32_t *done, int64_t *ut,
+                      cudaStream_t s);
+void launch_search_step(const DevBatch &B, const int32_t *order, int32_t *counter, const int32_t *ie,
+                        uint32_t *bitmap, const int64_t *bm_base, const int64_t *target, const int64_t *ut,
+                        int32_t *done, int64_t *chosen, int32_t *n_done, int grid, cudaStream_t s);
+void launch_search_final(int32_t ndag, int32_t k_max, const int64_t *unit_time_def, const int32_t *done,
+                         int64_t *chosen, cudaStream_t s);
 // Bottom levels (HEFT upward rank over mean costs) of every task; cbar = the mean
 // transfer cost (computed by the host).  One warp per DAG, DAGs in size order.
 void launch_blevel(const DevBatch &B, int32_t n_cpu, int32_t n_gpu, int64_t cbar, const int32_t *order,
