@@ -224,6 +224,59 @@ def run_reference(args, rank):
           flush=True)
 
 
+def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5):
+    """Throughput of the evaluation step and mean makespan under DMDA (FIFO pop)
+    and the DMDAP baselines (static IA / bottom-level priority), beside INSPIRIT,
+    all through the same kernels on the same DAGs; and the unit-time search:
+    its duration and INSPIRIT's mean makespan with the searched unit times."""
+    import torch
+
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    out = {"inspirit": {"mean_makespan_ns": float(mk_main.double().mean())}}
+    n, nd = batch.n_total, batch.ndag
+    bufs = [torch.empty(n, dtype=t, device=dev) for t in (torch.int32, torch.int32, torch.int32, torch.int64,
+                                                           torch.int64)] + [torch.empty(nd, dtype=torch.int64,
+                                                                                        device=dev)]
+    stream = torch.cuda.current_stream(dev)
+    for name, pid in (("dmda_fifo", P.INSP_POLICY_FIFO), ("dmdap_ia", P.INSP_POLICY_DMDAP_IA),
+                      ("dmdap_bottom_level", P.INSP_POLICY_DMDAP_BL)):
+        pol = P.insp_policy()
+        pol.policy = pid
+        m = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns, pol)
+        bb = P.DagBatch(m, batch)
+        _lib.insp_batch_set_tuning(bb.handle, t_struct)
+        for _ in range(2):
+            _lib.insp_evaluate_batch(bb.handle, None, *bufs, stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            _lib.insp_evaluate_batch(bb.handle, None, *bufs, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if _lib.insp_batch_status(bb.handle) != 0:
+            raise RuntimeError(f"{name}: device-side status not OK: " + _lib.last_error())
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        out[name] = {"value": n / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                     "mean_makespan_ns": float(bufs[5].double().mean())}
+        del bb, m
+    # unit-time search (k = 0..16) on the main batch, then INSPIRIT with the searched T
+    ut = torch.empty(nd, dtype=torch.int64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _lib.insp_unit_time_search(b_main.handle, 16, ut, stream)
+    t_search = time.perf_counter() - t0
+    _lib.insp_evaluate_batch(b_main.handle, ut, *bufs, stream)
+    torch.cuda.synchronize()
+    out["unit_time_search"] = {"seconds": t_search, "k_max": 16,
+                               "mean_makespan_ns_inspirit_searched_T": float(bufs[5].double().mean()),
+                               "median_searched_T_ns": float(ut.double().median())}
+    base = out["inspirit"]["mean_makespan_ns"]
+    for k in ("dmda_fifo", "dmdap_ia", "dmdap_bottom_level"):
+        out[k]["makespan_vs_inspirit"] = out[k]["mean_makespan_ns"] / base
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -412,6 +465,11 @@ def run_ours(args, rank, world, local_rank):
         e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": t_e2e * 1e3, "steps": k_e2e}
 
+    # ---- the baselines and the unit-time search on the same batch (same tuning, same step)
+    policies = None
+    if rank == 0 and not args.profile and not args.no_policies:
+        policies = compare_policies(args, batch, mach, t_struct, b, mk, dev)
+
     cb = cpu_baseline(batch, mach) if (rank == 0 and world == 1 and not args.profile) else None
 
     if rank == 0:
@@ -425,6 +483,7 @@ def run_ours(args, rank, world, local_rank):
                        "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
                              f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
             "per_dag_form": per_dag,
+            "policies": policies,
             "cuda_graph": graph,
             "e2e": e2e,
             "roofline": roofline,
@@ -456,6 +515,8 @@ def main():
     ap.add_argument("--tuning", default=None,
                     help='explicit tuning as JSON, e.g. \'{"groups": 1, "attr_overlap": 0, "ia_warps": 32, '
                          '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64}\'')
+    ap.add_argument("--no-policies", dest="no_policies", action="store_true",
+                    help="skip the DMDA / DMDAP baselines and the unit-time search leg")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
     args = ap.parse_args()
