@@ -36,7 +36,8 @@ __host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) / 16 * 16;
 
-__global__ void __launch_bounds__(PULL_MAX_WARPS * 32)
+// At most 40 registers (3 CTAs of 16 warps per SM): 48 resident warps instead of 32.
+__global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
               const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
@@ -87,17 +88,19 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32)
                 __syncwarp();
                 e0 = c_pp[0];
                 const int32_t ne = min(c_pp[PCH] - e0, PCOL);
-                // all loads of the chunk first, then the conversions and stores
-                int32_t qv[PCOL / 32];
+                // loads in rounds of 8 per lane (8 in flight), then the conversions and stores
+                for (int r0 = 0; r0 < PCOL / 32 && 32 * r0 < ne; r0 += 8) {
+                    int32_t qv[8];
 #pragma unroll
-                for (int r = 0; r < PCOL / 32; ++r) {
-                    const int32_t i = lane + 32 * r;
-                    qv[r] = i < ne ? __ldg(pc + e0 + i) : 0;
-                }
+                    for (int r = 0; r < 8; ++r) {
+                        const int32_t i = lane + 32 * (r0 + r);
+                        qv[r] = i < ne ? __ldg(pc + e0 + i) : 0;
+                    }
 #pragma unroll
-                for (int r = 0; r < PCOL / 32; ++r) {
-                    const int32_t i = lane + 32 * r;
-                    if (i < ne) c_off[i] = (qv[r] >= v0 ? (qv[r] & wmask) : W) * 32;
+                    for (int r = 0; r < 8; ++r) {
+                        const int32_t i = lane + 32 * (r0 + r);
+                        if (i < ne) c_off[i] = (qv[r] >= v0 ? (qv[r] & wmask) : W) * 32;
+                    }
                 }
                 __syncwarp();
             }
