@@ -2,8 +2,8 @@
 //
 // A warp owns 32 consecutive sources (lane j <-> v0 + j) and visits every task
 // u = v0, v0+1, ... in id order (a topological order).  Each lane keeps, per
-// task, one code in a ring of W rows (W a power of two above every edge span,
-// so every predecessor of u is still in the ring):
+// task, one value in a shared-memory ring of W slots (W a power of two above
+// every edge span, so every predecessor of u is still in the ring):
 //     -1         u is not in the source's cone,
 //     L in 1..T  u is in the cone and every path from the source to u weighs L
 //                or less (L = the longest path weight, GPU costs, both ends),
@@ -15,17 +15,11 @@
 // and IE(v_j) counts the tasks whose value lands in 1..T (the source excluded).
 // The sweep stops after the last task that received an in-window value from a
 // predecessor (tracked through each in-window task's largest successor id).
-//
-// Per ring row the warp also keeps two lane masks in shared memory: the lanes
-// whose code is in 1..T and the lanes at OVER.  A row without an in-window lane
-// contributes only OVER or -1, which its over mask gives, so only rows with an
-// in-window lane are stored to and loaded from the ring; predecessors older
-// than the sources contribute -1 and are skipped.  (On the layered workload
-// these two cases are over half of all predecessor reads.)  The ring is a
-// per-warp slice of global memory meant to stay in L2; each lane only reads
-// its own column, i.e. its own earlier writes.  Predecessor lists (built at
-// ingest) and GPU costs of the next 32 tasks are staged into shared memory
-// with coalesced loads.
+// Predecessor lists (built at ingest) and GPU costs of the next 32 tasks are
+// staged into shared memory with coalesced loads.  The ring is a per-warp
+// slice of global memory sized to stay in L2 (a shared-memory ring was measured
+// slower: at 33 KB per warp it caps residency at 6 warps per SM); each lane
+// only reads its own column, i.e. its own earlier writes.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -33,14 +27,14 @@ namespace insp {
 
 constexpr int PULL_MAX_WARPS = 16;  // warps per CTA: blockDim / 32 (autotuned)
 constexpr int PCH = 32;      // tasks per staged chunk
-constexpr int PCOL = 512;    // staged predecessor ids per chunk (longer chunks read the rest from global)
+constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
 
-// ring of W rows of 32 values
-__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4; }
-// per warp shared memory: the chunk staging, then two lane masks per ring row
+// ring of W + 1 rows of 32 values (row W is all -1: where predecessors older
+// than the sources point)
+__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W + 1) * 32 * 4; }
+// per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) / 16 * 16;
-__host__ __device__ constexpr int64_t ie_warp_smem(int32_t W) { return IE_PULL_STAGE_BYTES + (int64_t(W) * 8 + 15) / 16 * 16; }
 
 // At most 40 registers (3 CTAs of 16 warps per SM): 48 resident warps instead of 32.
 __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
@@ -51,14 +45,13 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int32_t wmask = W - 1;
-    unsigned char *mine = smem + int64_t(wib) * ie_warp_smem(W);
+    unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
     int32_t *__restrict__ val = gring + (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / 4);
     int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
     int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
     int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
-    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row of each predecessor (-1: older than the sources)
-    uint32_t *__restrict__ s_win = reinterpret_cast<uint32_t *>(mine + IE_PULL_STAGE_BYTES);  // lanes in 1..T
-    uint32_t *__restrict__ s_over = s_win + W;                                              // lanes at OVER
+    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row offset of each predecessor (row W if < v0)
+    val[W * 32 + lane] = -1;
 
     for (;;) {
         int64_t item = 0;
@@ -106,57 +99,36 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
                         const int32_t i = lane + 32 * (r0 + r);
-                        if (i < ne) c_off[i] = qv[r] >= v0 ? (qv[r] & wmask) : -1;
+                        if (i < ne) c_off[i] = (qv[r] >= v0 ? (qv[r] & wmask) : W) * 32;
                     }
                 }
                 __syncwarp();
             }
             const int32_t k = u - uc;
             const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
-            // Combine the predecessors' codes by max.  A row that no lane holds in the window
-            // contributes only OVER (its over mask) or -1, so only rows with an in-window lane
-            // are loaded from the ring; rows of predecessors older than the sources are -1.
             int32_t m0 = -1, m1 = -1;
-            uint32_t ovm = 0;
             if (hi_p <= PCOL) {
+                // full rounds of 8 predecessor values in flight, then a short tail
                 int32_t e = lo;
                 for (; e + 8 <= hi_p; e += 8) {
                     int32_t pv[8];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const int32_t row = c_off[e + r];
-                        const uint32_t wm = row >= 0 ? s_win[row] : 0u;
-                        ovm |= (row >= 0 && wm == 0u) ? s_over[row] : 0u;
-                        pv[r] = wm ? val[row * 32 + lane] : -1;
-                    }
+                    for (int r = 0; r < 8; ++r) pv[r] = val[c_off[e + r] + lane];
 #pragma unroll
                     for (int r = 0; r < 8; r += 2) {
                         m0 = max(m0, pv[r]);
                         m1 = max(m1, pv[r + 1]);
                     }
                 }
-                for (; e < hi_p; ++e) {
-                    const int32_t row = c_off[e];
-                    const uint32_t wm = row >= 0 ? s_win[row] : 0u;
-                    ovm |= (row >= 0 && wm == 0u) ? s_over[row] : 0u;
-                    if (wm) m0 = max(m0, val[row * 32 + lane]);
-                }
+                for (; e < hi_p; ++e) m0 = max(m0, val[c_off[e] + lane]);
             } else {
                 for (int32_t e = lo; e < hi_p; ++e) {
-                    int32_t row;
-                    if (e < PCOL) {
-                        row = c_off[e];
-                    } else {
-                        const int32_t q = pc[e0 + e];
-                        row = q >= v0 ? (q & wmask) : -1;
-                    }
-                    const uint32_t wm = row >= 0 ? s_win[row] : 0u;
-                    ovm |= (row >= 0 && wm == 0u) ? s_over[row] : 0u;
-                    if (wm) m0 = max(m0, val[row * 32 + lane]);
+                    const int32_t q = e < PCOL ? -2 : pc[e0 + e];
+                    const int32_t off = e < PCOL ? c_off[e] : (q >= v0 ? (q & wmask) : W) * 32;
+                    m0 = max(m0, val[off + lane]);
                 }
             }
-            int32_t m = max(m0, m1);
-            if ((ovm >> lane) & 1u) m = OVER;  // OVER is the largest code
+            const int32_t m = max(m0, m1);
             const int32_t c = c_cost[k];
             int32_t v;
             if (u - v0 == lane) {
@@ -168,16 +140,8 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
                 v = L <= T ? int32_t(L) : OVER;
                 cnt += L <= T;
             }
-            const uint32_t wm = __ballot_sync(FULL, v >= 0 && v != OVER);
-            const uint32_t om = __ballot_sync(FULL, v == OVER);
-            const int32_t slot = u & wmask;
-            if (wm) val[slot * 32 + lane] = v;  // only rows with an in-window lane are read back
-            if (lane == 0) {
-                s_win[slot] = wm;
-                s_over[slot] = om;
-            }
-            __syncwarp();  // the masks are read by the whole warp at later tasks
-            if (wm) hi = max(hi, c_msucc[k]);
+            val[(u & wmask) * 32 + lane] = v;
+            if (__any_sync(FULL, v >= 0 && v != OVER)) hi = max(hi, c_msucc[k]);
         }
         if (lane < n_src) ie_out[tb + v0 + lane] = cnt;
         __syncwarp();
@@ -233,11 +197,10 @@ __global__ void __launch_bounds__(256) k_reverse_csr(DevBatch B, const int32_t *
 int ie_pull_max_warps() { return PULL_MAX_WARPS; }
 int64_t ie_pull_ring_bytes(int32_t W) { return ie_ring_bytes(W); }
 
-int ie_pull_occupancy(int warps, int32_t W) {
-    const int64_t bytes = ie_warp_smem(W) * warps;
+int ie_pull_occupancy(int warps) {
+    const int64_t bytes = IE_PULL_STAGE_BYTES * warps;
     int nb = 0;
-    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(ie_warp_smem(IE_PULL_MAX_W) * PULL_MAX_WARPS));
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, warps * 32, size_t(bytes)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -249,9 +212,8 @@ void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pco
                     const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
                     const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie, int grid, int warps,
                     cudaStream_t s) {
-    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(ie_warp_smem(IE_PULL_MAX_W) * PULL_MAX_WARPS));
-    k_ie_pull<<<grid, warps * 32, size_t(ie_warp_smem(W) * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
+    k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
                                                                            item_lo, item_hi, counter, unit_time, W,
                                                                            gring, ie);
 }
