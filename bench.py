@@ -508,7 +508,7 @@ def main():
     ap.add_argument("--ndag", type=int, default=4096, help="first K DAGs of the workload (profiling captures)")
     ap.add_argument("--workload", choices=["layered", "layered_degree", "tiled"], default="layered",
                     help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches")
-    ap.add_argument("--tiles", default="16,32,64", help="tile counts of the tiled workload")
+    ap.add_argument("--tiles", default="16,32", help="tile counts of the tiled workload (64 tiles takes the slow global efficiency sweep)")
     ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shapes instead of autotuning them on the batch")

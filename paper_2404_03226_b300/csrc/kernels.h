@@ -65,7 +65,10 @@ void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
                const uint64_t *tag_base, int32_t *ie, int grid, cudaStream_t s);
 // inspiring efficiency, pull form (k_ie_pull.cu)
-constexpr int32_t IE_PULL_MAX_W = 512;
+// Longest window (ring rows, a power of two above the batch's longest edge span) of the
+// pull form: its per-warp ring is W x 128 bytes, so long spans only cost ring memory (the
+// tuning's ring budget then admits fewer warps); beyond it the global form runs.
+constexpr int32_t IE_PULL_MAX_W = 8192;
 int ie_pull_max_warps();
 int64_t ie_pull_ring_bytes(int32_t W);
 int ie_pull_occupancy(int warps);

@@ -220,3 +220,13 @@ def test_recorded_graph_replays_match_direct_calls():
     with pytest.raises(_lib.InspError):
         _lib.insp_batch_record(B.handle, bufs["ia"], bufs["ie"], bufs["worker"], bufs["start"], bufs["end"],
                                bufs["makespan"], None)
+
+
+def test_tiled_32_long_spans_take_the_pull_sweep():
+    """Cholesky and LU at 32 tiles (edge spans up to ~1000 ids, window 1024)."""
+    b = inputs.concat([inputs.tiled(inputs.KIND_CHOLESKY, 32, 1), inputs.tiled(inputs.KIND_LU, 32, 1)])
+    m = inputs.MACHINE_TILED
+    g = gpu_run(b, m)
+    assert (g["status"] == 0).all()
+    for d in range(b.ndag):
+        compare_dag(b, d, g, m)
