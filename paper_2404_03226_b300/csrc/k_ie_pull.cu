@@ -16,7 +16,8 @@
 // The sweep stops after the last task that received an in-window value from a
 // predecessor (tracked through each in-window task's largest successor id).
 // Predecessor lists (built at ingest) and GPU costs of the next 32 tasks are
-// staged into shared memory with coalesced loads.  The ring is a per-warp
+// staged into shared memory with coalesced loads; predecessors older than the
+// sources (-1 for every source) are dropped while staging.  The ring is a per-warp
 // slice of global memory sized to stay in L2 (a shared-memory ring was measured
 // slower: at 33 KB per warp it caps residency at 6 warps per SM); each lane
 // only reads its own column, i.e. its own earlier writes.
@@ -30,11 +31,10 @@ constexpr int PCH = 32;      // tasks per staged chunk
 constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
 
-// ring of W + 1 rows of 32 values (row W is all -1: where predecessors older
-// than the sources point)
-__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W + 1) * 32 * 4; }
+// ring of W rows of 32 values
+__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4; }
 // per warp shared memory: the chunk staging
-constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL) * 4 + 15) / 16 * 16;
+constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
 
 // At most 40 registers (3 CTAs of 16 warps per SM): 48 resident warps instead of 32.
 __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
@@ -50,8 +50,8 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
     int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
     int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
     int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
-    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row offset of each predecessor (row W if < v0)
-    val[W * 32 + lane] = -1;
+    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row offsets of the staged predecessors >= v0
+    int32_t *__restrict__ c_kp = c_off + PCOL;        // per task: its first entry in c_off
 
     for (;;) {
         int64_t item = 0;
@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
 
         int32_t cnt = 0;
         int32_t hi = v0 + n_src - 1;
-        int32_t uc = -1, e0 = 0;  // first task and first predecessor edge of the staged chunk
+        int32_t uc = -1, e0 = 0, ne = 0;  // first task, first predecessor edge and staged entries of the chunk
         for (int32_t u = v0; u <= hi; ++u) {
             if (uc < 0 || u - uc >= PCH) {
                 __syncwarp();
@@ -87,30 +87,42 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
                 }
                 __syncwarp();
                 e0 = c_pp[0];
-                const int32_t ne = min(c_pp[PCH] - e0, PCOL);
-                // loads in rounds of 8 per lane (8 in flight), then the conversions and stores
+                ne = min(c_pp[PCH] - e0, PCOL);
+                // Stage the first ne predecessor ids of the chunk, keeping only those >= v0 (older
+                // ones are -1 for every source) in order, compacted by ballot; each task's first
+                // kept entry is found from its boundary b_k (lane k; lane 0 also the chunk's end).
+                const int32_t b_k = c_pp[lane] - e0;
+                int32_t kp = 0, base = 0;
                 for (int r0 = 0; r0 < PCOL / 32 && 32 * r0 < ne; r0 += 8) {
                     int32_t qv[8];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
                         const int32_t i = lane + 32 * (r0 + r);
-                        qv[r] = i < ne ? __ldg(pc + e0 + i) : 0;
+                        qv[r] = i < ne ? __ldg(pc + e0 + i) : -1;
                     }
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
-                        const int32_t i = lane + 32 * (r0 + r);
-                        if (i < ne) c_off[i] = (qv[r] >= v0 ? (qv[r] & wmask) : W) * 32;
+                        const int32_t i0 = 32 * (r0 + r);
+                        const bool keep = qv[r] >= v0;  // -1 past ne
+                        const uint32_t bal = __ballot_sync(FULL, keep);
+                        if (keep) c_off[base + __popc(bal & ((1u << lane) - 1))] = (qv[r] & wmask) * 32;
+                        if (b_k >= i0 && b_k < i0 + 32) kp = base + __popc(bal & ((1u << (b_k - i0)) - 1));
+                        base += __popc(bal);
                     }
                 }
+                c_kp[lane] = b_k >= ne ? base : kp;
+                if (lane == 0) c_kp[PCH] = base;
                 __syncwarp();
             }
             const int32_t k = u - uc;
             const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
+            // staged entries of this task (compacted), then any beyond the staging from global
+            const int32_t clo = c_kp[k], chi = hi_p <= ne ? c_kp[k + 1] : c_kp[PCH];
             int32_t m0 = -1, m1 = -1;
-            if (hi_p <= PCOL) {
+            {
                 // full rounds of 8 predecessor values in flight, then a short tail
-                int32_t e = lo;
-                for (; e + 8 <= hi_p; e += 8) {
+                int32_t e = clo;
+                for (; e + 8 <= chi; e += 8) {
                     int32_t pv[8];
 #pragma unroll
                     for (int r = 0; r < 8; ++r) pv[r] = val[c_off[e + r] + lane];
@@ -120,13 +132,11 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
                         m1 = max(m1, pv[r + 1]);
                     }
                 }
-                for (; e < hi_p; ++e) m0 = max(m0, val[c_off[e] + lane]);
-            } else {
-                for (int32_t e = lo; e < hi_p; ++e) {
-                    const int32_t q = e < PCOL ? -2 : pc[e0 + e];
-                    const int32_t off = e < PCOL ? c_off[e] : (q >= v0 ? (q & wmask) : W) * 32;
-                    m0 = max(m0, val[off + lane]);
-                }
+                for (; e < chi; ++e) m0 = max(m0, val[c_off[e] + lane]);
+            }
+            for (int32_t e = max(lo, ne); e < hi_p; ++e) {
+                const int32_t q = pc[e0 + e];
+                if (q >= v0) m0 = max(m0, val[(q & wmask) * 32 + lane]);
             }
             const int32_t m = max(m0, m1);
             const int32_t c = c_cost[k];
