@@ -66,14 +66,10 @@ struct Pool {
             g_idw[j] = idw_; g_seq[j] = seq_; g_ia[j] = ia_; g_ie[j] = ie_; g_dr[j] = dr_; g_cost[j] = cost_;
         }
     }
-    // copy entry `from` into slot `to`, lanes 0..5 one field each
+    // copy entry `from` into slot `to`: one lane, its six independent loads in flight together
+    // (one lane per field would serialise six divergent paths)
     __device__ __forceinline__ void move(int from, int to, int lane) const {
-        if (lane == 0) { int32_t v = idw(from); if (to < POOL_C) sm->idw[to] = v; else g_idw[to - POOL_C] = v; }
-        if (lane == 1) { int32_t v = seq(from); if (to < POOL_C) sm->seq[to] = v; else g_seq[to - POOL_C] = v; }
-        if (lane == 2) { int32_t v = ia(from); if (to < POOL_C) sm->ia[to] = v; else g_ia[to - POOL_C] = v; }
-        if (lane == 3) { int32_t v = ie(from); if (to < POOL_C) sm->ie[to] = v; else g_ie[to - POOL_C] = v; }
-        if (lane == 4) { int64_t v = dr(from); if (to < POOL_C) sm->dr[to] = v; else g_dr[to - POOL_C] = v; }
-        if (lane == 5) { int64_t v = cost(from); if (to < POOL_C) sm->cost[to] = v; else g_cost[to - POOL_C] = v; }
+        if (lane == 0) set(to, idw(from), seq(from), ia(from), ie(from), dr(from), cost(from));
     }
 };
 
@@ -233,6 +229,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         const int32_t w0 = lane, w1 = lane + 32;
         int64_t busy0 = 0, busy1 = 0, qc0 = 0, qc1 = 0;
         int32_t run0 = -1, run1 = -1, qn0 = 0, qn1 = 0;
+        // successor-row bounds of the running task, loaded when it starts (used at its completion)
+        int32_t rlo0 = 0, rhi0 = 0, rlo1 = 0, rhi1 = 0;
         int32_t nready = 0, seq = 0, done = 0, npop = 0;
         int64_t now = 0;
         Ctrl ctl{0, 0, 0, 0, MODE_FIFO, ST_INC};
@@ -429,8 +427,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             npop += 1;
             const int64_t s = max(now, dr), e = s + c;
             if (lane == (w & 31)) {
-                if (w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; }
-                else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; }
+                if (w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; }
+                else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; rlo0 = rp[t]; rhi0 = rp[t + 1]; }
             }
             if (lane == 0) {
                 A.worker[tb + t] = w;
@@ -484,7 +482,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                     const int32_t w = wl + 32 * half;
                     const int32_t p = __shfl_sync(FULL, half ? run1 : run0, wl);
                     const int32_t nd = node_of(w, n_cpu);
-                    const int32_t lo = rp[p], hi = rp[p + 1];
+                    const int32_t lo = __shfl_sync(FULL, half ? rlo1 : rlo0, wl);
+                    const int32_t hi = __shfl_sync(FULL, half ? rhi1 : rhi0, wl);
                     for (int32_t base = lo; base < hi; base += 32) {
                         const int32_t i = base + lane;
                         bool ready = false;
