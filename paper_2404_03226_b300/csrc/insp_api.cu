@@ -849,7 +849,7 @@ int launch_sim_part(insp_batch *b, const insp::SimArgs &A, cudaStream_t s) {
     if (rc) return rc;
     const bool learned = A.policy == INSP_POLICY_LEARNED;
     const int wpc = b->tun.sim_warps;
-    const int occ = std::max(1, insp::sim_occupancy(learned, wpc, b->tun.sim_queue));
+    const int occ = std::max(1, insp::sim_occupancy(learned, b->mach.n_cpu + b->mach.n_gpu, wpc, b->tun.sim_queue));
     const int grid = std::max(1, std::min(di.sms * occ, (A.n_order + wpc - 1) / wpc));
     insp::launch_sim(A, grid, wpc, b->tun.sim_queue, s);
     CU(cudaGetLastError());

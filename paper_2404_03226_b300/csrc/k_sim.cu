@@ -154,7 +154,9 @@ struct LearnSmem {
     int32_t cidx[32];
 };
 
-template <bool LEARNED, int POOL_C>
+// TWO: more than 32 workers, so every lane owns a second worker (lane + 32); with 32 or
+// fewer that slot and all its code drop out at compile time.
+template <bool LEARNED, int POOL_C, bool TWO>
 __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     __shared__ WarpSmem<POOL_C> smem_all[SIM_WARPS];
     extern __shared__ __align__(16) unsigned char dyn[];
@@ -179,9 +181,17 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (iter > 0 || blockIdx.x != 0 || wib != 0) return;
             d = A.single_dag;
         } else {
+            // first DAG of every warp transposed over the grid (warp j of every CTA takes the j-th
+            // stripe of gridDim DAGs), so the largest DAGs start on different SMs instead of filling
+            // one CTA; later DAGs through the work counter
+            const int nw = gridDim.x * (blockDim.x >> 5);
             int k = 0;
-            if (lane == 0) k = atomicAdd(A.counter, 1);
-            k = __shfl_sync(FULL, k, 0);
+            if (iter == 0) {
+                k = wib * gridDim.x + blockIdx.x;
+            } else {
+                if (lane == 0) k = nw + atomicAdd(A.counter, 1);
+                k = __shfl_sync(FULL, k, 0);
+            }
             if (k >= A.n_order) return;
             d = A.order[k];
         }
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 const int64_t ef = max(avail, dr0) + (w0 < n_cpu ? cc : cg);
                 k0 = (uint64_t(ef) << 6) | uint64_t(w0);
             }
-            if (w1 < P) {
+            if (TWO && w1 < P) {
                 const int32_t nd = node_of(w1, n_cpu);
                 dr1 = a.y == NODE_NONE ? 0 : (nd == a.y ? max(b.x, b.y + xfer) : b.x + xfer);
                 const int64_t avail = max(now, busy1) + qc1;
@@ -270,7 +280,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (lane == (ws & 31)) {
                 const bool hi = ws >= 32;
                 const int64_t c = ws < n_cpu ? cc : cg;
-                if (hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
+                if (TWO && hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
                 pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
                 if (A.tr_push_time) {
                     const int64_t r = tb + seq;
@@ -301,7 +311,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 ctrl_step(ctl, cur, now, tw, s_inc, s_dec, dec_step, cslack, kt, kns);
                 mode = ctl.mode;
             }
-            const int32_t qlen = __shfl_sync(FULL, w >= 32 ? qn1 : qn0, w & 31);
+            const int32_t qlen = __shfl_sync(FULL, (TWO && w >= 32) ? qn1 : qn0, w & 31);
             // rollouts: candidate features in push order
             if (A.feat_pop != nullptr && npop == A.feat_pop[d]) {
                 int32_t last = -1, nd = 0;
@@ -427,7 +437,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             npop += 1;
             const int64_t s = max(now, dr), e = s + c;
             if (lane == (w & 31)) {
-                if (w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; }
+                if (TWO && w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; }
                 else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; rlo0 = rp[t]; rhi0 = rp[t + 1]; }
             }
             if (lane == 0) {
@@ -449,7 +459,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
 
         auto dispatch = [&]() -> bool {
             const uint32_t m0 = __ballot_sync(FULL, w0 < P && run0 < 0 && qn0 > 0);
-            const uint32_t m1 = __ballot_sync(FULL, w1 < P && run1 < 0 && qn1 > 0);
+            const uint32_t m1 = TWO ? __ballot_sync(FULL, w1 < P && run1 < 0 && qn1 > 0) : 0u;
             bool ok = true;
             for (uint32_t m = m0; m && ok; m &= m - 1) ok = pop(__ffs(m) - 1);
             for (uint32_t m = m1; m && ok; m &= m - 1) ok = pop(32 + __ffs(m) - 1);
@@ -469,14 +479,14 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (++guard > 2 * int64_t(n) + 2) { bad = true; break; }
             // next event: earliest completion
             const int64_t e0 = (w0 < P && run0 >= 0) ? busy0 : INT64_MAX;
-            const int64_t e1 = (w1 < P && run1 >= 0) ? busy1 : INT64_MAX;
+            const int64_t e1 = (TWO && w1 < P && run1 >= 0) ? busy1 : INT64_MAX;
             now = warp_min_i64(min(e0, e1));
             if (now == INT64_MAX) { bad = true; break; }
             const uint32_t c0 = __ballot_sync(FULL, w0 < P && run0 >= 0 && busy0 == now);
-            const uint32_t c1 = __ballot_sync(FULL, w1 < P && run1 >= 0 && busy1 == now);
+            const uint32_t c1 = TWO ? __ballot_sync(FULL, w1 < P && run1 >= 0 && busy1 == now) : 0u;
             // release successors of every completed task; one run of released ids per completion
             int32_t nl = 0, nruns = 0;
-            for (int half = 0; half < 2; ++half) {
+            for (int half = 0; half < (TWO ? 2 : 1); ++half) {
                 for (uint32_t m = half ? c1 : c0; m; m &= m - 1) {
                     const int32_t wl = __ffs(m) - 1;
                     const int32_t w = wl + 32 * half;
@@ -561,49 +571,62 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
 
 constexpr size_t LEARN_SMEM = sizeof(ScorerPacked) + SIM_WARPS * sizeof(LearnSmem);
 
-template <bool L, int Q>
+template <bool L, int Q, bool TWO>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
     if (L) {
-        cudaFuncSetAttribute(k_sim<L, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-        k_sim<L, Q><<<grid, threads, LEARN_SMEM, s>>>(A);
+        cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+        k_sim<L, Q, TWO><<<grid, threads, LEARN_SMEM, s>>>(A);
     } else {
-        k_sim<L, Q><<<grid, threads, 0, s>>>(A);
+        k_sim<L, Q, TWO><<<grid, threads, 0, s>>>(A);
     }
 }
 
-template <bool L>
+template <bool L, bool TWO>
 static void launch_l(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
-    if (queue <= 32) launch_q<L, 32>(A, grid, threads, s);
-    else if (queue <= 64) launch_q<L, 64>(A, grid, threads, s);
-    else launch_q<L, 128>(A, grid, threads, s);
+    if (queue <= 32) launch_q<L, 32, TWO>(A, grid, threads, s);
+    else if (queue <= 64) launch_q<L, 64, TWO>(A, grid, threads, s);
+    else launch_q<L, 128, TWO>(A, grid, threads, s);
+}
+
+static void launch_any(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
+    const bool two = A.n_cpu + A.n_gpu > 32;
+    if (A.policy == INSP_POLICY_LEARNED) {
+        if (two) launch_l<true, true>(A, grid, threads, queue, s);
+        else launch_l<true, false>(A, grid, threads, queue, s);
+    } else {
+        if (two) launch_l<false, true>(A, grid, threads, queue, s);
+        else launch_l<false, false>(A, grid, threads, queue, s);
+    }
 }
 
 void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s) {
-    const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));
-    if (A.policy == INSP_POLICY_LEARNED) launch_l<true>(A, grid, threads, queue, s);
-    else launch_l<false>(A, grid, threads, queue, s);
+    launch_any(A, grid, 32 * std::max(1, std::min(warps, SIM_WARPS)), queue, s);
 }
 // The unbatched form: one launch, one warp, one DAG.
-void launch_sim_single(const SimArgs &A, cudaStream_t s) {
-    if (A.policy == INSP_POLICY_LEARNED) launch_l<true>(A, 1, 32, 64, s);
-    else launch_l<false>(A, 1, 32, 64, s);
-}
+void launch_sim_single(const SimArgs &A, cudaStream_t s) { launch_any(A, 1, 32, 64, s); }
 int sim_max_warps() { return SIM_WARPS; }
 
-template <bool L, int Q>
+template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
-    if (L) cudaFuncSetAttribute(k_sim<L, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q>, threads, L ? LEARN_SMEM : 0) != cudaSuccess) {
+    if (L) cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO>, threads, L ? LEARN_SMEM : 0) !=
+        cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return nb;
 }
-int sim_occupancy(bool learned, int warps, int queue) {
+template <bool L, bool TWO>
+static int occ_l(int threads, int queue) {
+    return queue <= 32 ? occ_q<L, 32, TWO>(threads) : queue <= 64 ? occ_q<L, 64, TWO>(threads)
+                                                                   : occ_q<L, 128, TWO>(threads);
+}
+int sim_occupancy(bool learned, int n_workers, int warps, int queue) {
     const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));
-    if (learned) return queue <= 32 ? occ_q<true, 32>(threads) : queue <= 64 ? occ_q<true, 64>(threads) : occ_q<true, 128>(threads);
-    return queue <= 32 ? occ_q<false, 32>(threads) : queue <= 64 ? occ_q<false, 64>(threads) : occ_q<false, 128>(threads);
+    const bool two = n_workers > 32;
+    if (learned) return two ? occ_l<true, true>(threads, queue) : occ_l<true, false>(threads, queue);
+    return two ? occ_l<false, true>(threads, queue) : occ_l<false, false>(threads, queue);
 }
 
 }  // namespace insp

@@ -103,7 +103,7 @@ void launch_search_final(int32_t ndag, int32_t k_max, const int64_t *unit_time_d
 // transfer cost (computed by the host).  One warp per DAG, DAGs in size order.
 void launch_blevel(const DevBatch &B, int32_t n_cpu, int32_t n_gpu, int64_t cbar, const int32_t *order,
                    int32_t *counter, int64_t *bl, int grid, cudaStream_t s);
-int sim_occupancy(bool learned, int warps, int queue);
+int sim_occupancy(bool learned, int n_workers, int warps, int queue);
 int sim_max_warps();
 void launch_sim_single(const SimArgs &A, cudaStream_t s);
 int ia_max_warps();
