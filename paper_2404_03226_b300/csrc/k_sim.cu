@@ -503,15 +503,13 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                             int2 a = st_a[s];
                             longlong2 b = st_b[s];
                             a.x -= 1;
-                            if (a.y == nd) {
-                                b.x = now;
-                            } else if (now > b.x) {
-                                b.y = b.x;
-                                a.y = nd;
-                                b.x = now;
-                            } else {
-                                b.y = now;
-                            }
+                            // latest completion per node, top two nodes (now never decreases):
+                            // same node -> new latest; another node and later -> the old latest
+                            // becomes the runner-up; another node at the same time -> runner-up
+                            const bool same = a.y == nd, later = now > b.x;
+                            b.y = same ? b.y : (later ? b.x : now);
+                            a.y = (same || !later) ? a.y : nd;
+                            b.x = (same || later) ? now : b.x;
                             st_a[s] = a;
                             st_b[s] = b;
                             ready = (a.x == 0);
