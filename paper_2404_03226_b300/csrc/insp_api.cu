@@ -164,7 +164,8 @@ struct insp_batch {
     std::vector<int64_t> h_rank_item;  // first item (size-order numbering) of the DAG at each rank
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
-    int64_t max_unit_def = 1, n_items = 0;
+    int64_t max_unit_def = 1, n_items = 0;  // 32-source items (global efficiency sweep)
+    int64_t n_items_pull = 0;                 // IE_PULL_SOURCES-source items (pull sweep)
     std::unique_ptr<Scratch> sc;
     int64_t ie_rec_stride = 0;
     // tuning and the launch shapes derived from it
@@ -240,7 +241,8 @@ int alloc_pull_ring(insp_batch *b) {
     if (occ < 1) return fail(INSP_ECUDA, "occupancy query failed");
     const int64_t ring = insp::ie_pull_ring_bytes(b->W);
     const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(b->tun.ie_ring_mb) << 20) / (ring * wpc));
-    b->grid_ie_pull = int(std::max<int64_t>(1, std::min({int64_t(di.sms) * occ, (b->n_items + wpc - 1) / wpc, l2_ctas})));
+    b->grid_ie_pull =
+        int(std::max<int64_t>(1, std::min({int64_t(di.sms) * occ, (b->n_items_pull + wpc - 1) / wpc, l2_ctas})));
     // (the kernel writes every ring row before reading it, row W included)
     return b->sc->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring);
 }
@@ -574,16 +576,20 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     std::vector<int32_t> idag(std::max<int64_t>(b->n_items, 1));
     for (int d = 0; d < ndag; ++d)
         for (int64_t k = items[d]; k < items[d + 1]; ++k) idag[k] = d;
-    // the same items numbered along the size order: a size group's items are a contiguous range
+    // the pull sweep's items (IE_PULL_SOURCES sources each) numbered along the size order: a
+    // size group's items are a contiguous range
     b->h_rank_item.assign(ndag + 1, 0);
     std::vector<int64_t> base_lpt(std::max(ndag, 1), 0);
-    std::vector<int32_t> idag_lpt(std::max<int64_t>(b->n_items, 1));
     for (int r = 0; r < ndag; ++r) {
         const int d = order[r];
+        const int64_t nd = b->h_task_base[d + 1] - b->h_task_base[d];
         base_lpt[d] = b->h_rank_item[r];
-        b->h_rank_item[r + 1] = b->h_rank_item[r] + (items[d + 1] - items[d]);
-        for (int64_t k = b->h_rank_item[r]; k < b->h_rank_item[r + 1]; ++k) idag_lpt[k] = d;
+        b->h_rank_item[r + 1] = b->h_rank_item[r] + (nd + insp::IE_PULL_SOURCES - 1) / insp::IE_PULL_SOURCES;
     }
+    b->n_items_pull = b->h_rank_item[ndag];
+    std::vector<int32_t> idag_lpt(std::max<int64_t>(b->n_items_pull, 1));
+    for (int r = 0; r < ndag; ++r)
+        for (int64_t k = b->h_rank_item[r]; k < b->h_rank_item[r + 1]; ++k) idag_lpt[k] = order[r];
     if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4)) ||
         (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)) ||
         (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)) ||
@@ -985,7 +991,7 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
         if (b->pull && !wide) {
             const int wpc = b->tun.ie_warps;
             insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base_lpt.as<int64_t>(),
-                                 b->item_dag_lpt.as<int32_t>(), 0, b->n_items, ck + 0, ut.as<int64_t>(), b->W,
+                                 b->item_dag_lpt.as<int32_t>(), 0, b->n_items_pull, ck + 0, ut.as<int64_t>(), b->W,
                                  S.ie_ring.as<int32_t>(), ie.as<int32_t>(), b->grid_ie_pull, wpc, s);
         } else {
             if (!b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;

@@ -1,6 +1,7 @@
 // Inspiring efficiency (Sec. 4.2 / Sec. 4.3), "pull" form of the window sweep.
 //
-// A warp owns 32 consecutive sources (lane j <-> v0 + j) and visits every task
+// A warp owns 64 consecutive sources (lane j <-> v0 + j and v0 + 32 + j, two
+// codes per lane) and visits every task
 // u = v0, v0+1, ... in id order (a topological order).  Each lane keeps, per
 // task, one value in a shared-memory ring of W slots (W a power of two above
 // every edge span, so every predecessor of u is still in the ring):
@@ -30,14 +31,15 @@ constexpr int PULL_MAX_WARPS = 16;  // warps per CTA: blockDim / 32 (autotuned)
 constexpr int PCH = 32;      // tasks per staged chunk
 constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
+constexpr int SPW = IE_PULL_SOURCES;  // sources per warp: lane j owns v0 + j and v0 + 32 + j
 
-// ring of W rows of 32 values
-__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4; }
+// ring of W rows of 32 lanes x 2 values
+__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 8; }
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
 
-// At most 40 registers (3 CTAs of 16 warps per SM): 48 resident warps instead of 32.
-__global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
+// At most 48 registers: 40 resident warps per SM (64 registers would allow 32).
+__global__ void __maxnreg__(48)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
               const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
@@ -46,7 +48,7 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
     const int wib = threadIdx.x >> 5;
     const int32_t wmask = W - 1;
     unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
-    int32_t *__restrict__ val = gring + (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / 4);
+    int2 *__restrict__ val = reinterpret_cast<int2 *>(gring) + (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / 8);
     int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
     int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
     int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
@@ -61,15 +63,15 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
         const int d = item_dag[item];
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];
         const int32_t n = int32_t(B.task_base[d + 1] - tb);
-        const int32_t v0 = int32_t(item - item_base[d]) * 32;
-        const int32_t n_src = min(32, n - v0);
+        const int32_t v0 = int32_t(item - item_base[d]) * SPW;
+        const int32_t n_src = min(SPW, n - v0);
         const int32_t *rp = B.row_ptr + tb + d;
         const int32_t *col = B.col_idx + eb;
         const int32_t *pp = pr_ptr + tb + d;
         const int32_t *pc = pcol + eb;
         const int64_t T = unit_time[d];
 
-        int32_t cnt = 0;
+        int32_t cnt_x = 0, cnt_y = 0;  // sources v0 + lane and v0 + 32 + lane
         int32_t hi = v0 + n_src - 1;
         int32_t uc = -1, e0 = 0, ne = 0;  // first task, first predecessor edge and staged entries of the chunk
         for (int32_t u = v0; u <= hi; ++u) {
@@ -118,42 +120,52 @@ __global__ void __launch_bounds__(PULL_MAX_WARPS * 32, 3)
             const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
             // staged entries of this task (compacted), then any beyond the staging from global
             const int32_t clo = c_kp[k], chi = hi_p <= ne ? c_kp[k + 1] : c_kp[PCH];
-            int32_t m0 = -1, m1 = -1;
+            int2 ma = make_int2(-1, -1), mb = make_int2(-1, -1);
             {
-                // full rounds of 8 predecessor values in flight, then a short tail
+                // full rounds of 4 predecessor pairs in flight, then a short tail
                 int32_t e = clo;
-                for (; e + 8 <= chi; e += 8) {
-                    int32_t pv[8];
+                for (; e + 4 <= chi; e += 4) {
+                    int2 pv[4];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) pv[r] = val[c_off[e + r] + lane];
-#pragma unroll
-                    for (int r = 0; r < 8; r += 2) {
-                        m0 = max(m0, pv[r]);
-                        m1 = max(m1, pv[r + 1]);
-                    }
+                    for (int r = 0; r < 4; ++r) pv[r] = val[c_off[e + r] + lane];
+                    ma.x = max(ma.x, max(pv[0].x, pv[1].x));
+                    ma.y = max(ma.y, max(pv[0].y, pv[1].y));
+                    mb.x = max(mb.x, max(pv[2].x, pv[3].x));
+                    mb.y = max(mb.y, max(pv[2].y, pv[3].y));
                 }
-                for (; e < chi; ++e) m0 = max(m0, val[c_off[e] + lane]);
+                for (; e < chi; ++e) {
+                    const int2 x = val[c_off[e] + lane];
+                    ma.x = max(ma.x, x.x);
+                    ma.y = max(ma.y, x.y);
+                }
             }
             for (int32_t e = max(lo, ne); e < hi_p; ++e) {
                 const int32_t q = pc[e0 + e];
-                if (q >= v0) m0 = max(m0, val[(q & wmask) * 32 + lane]);
+                if (q >= v0) {
+                    const int2 x = val[(q & wmask) * 32 + lane];
+                    ma.x = max(ma.x, x.x);
+                    ma.y = max(ma.y, x.y);
+                }
             }
-            const int32_t m = max(m0, m1);
+            const int32_t mx = max(ma.x, mb.x), my = max(ma.y, mb.y);
             const int32_t c = c_cost[k];
-            int32_t v;
-            if (u - v0 == lane) {
-                v = (int64_t(c) <= T) ? c : OVER;
-            } else if (m < 0 || m == OVER) {
-                v = m;
-            } else {
-                const int64_t L = int64_t(m) + c;
-                v = L <= T ? int32_t(L) : OVER;
-                cnt += L <= T;
-            }
-            val[(u & wmask) * 32 + lane] = v;
-            if (__any_sync(FULL, v >= 0 && v != OVER)) hi = max(hi, c_msucc[k]);
+            // branch-free: T < 2^31 here, so m + c (both <= T + 1) fits in 32 unsigned bits.  A
+            // source's own m is -1 (tasks before a source are outside its cone).
+            const bool live_x = mx >= 0 && mx != OVER, live_y = my >= 0 && my != OVER;
+            const uint32_t Lx = uint32_t(mx) + uint32_t(c), Ly = uint32_t(my) + uint32_t(c);
+            const bool fits_x = live_x && Lx <= uint32_t(T), fits_y = live_y && Ly <= uint32_t(T);
+            const int32_t own = c <= int32_t(T) ? c : OVER;
+            int32_t vx = live_x ? (fits_x ? int32_t(Lx) : OVER) : mx;
+            int32_t vy = live_y ? (fits_y ? int32_t(Ly) : OVER) : my;
+            if (u - v0 == lane) vx = own;
+            if (u - v0 == lane + 32) vy = own;
+            cnt_x += fits_x;
+            cnt_y += fits_y;
+            val[(u & wmask) * 32 + lane] = make_int2(vx, vy);
+            if (__any_sync(FULL, (vx >= 0 && vx != OVER) || (vy >= 0 && vy != OVER))) hi = max(hi, c_msucc[k]);
         }
-        if (lane < n_src) ie_out[tb + v0 + lane] = cnt;
+        if (lane < n_src) ie_out[tb + v0 + lane] = cnt_x;
+        if (lane + 32 < n_src) ie_out[tb + v0 + 32 + lane] = cnt_y;
         __syncwarp();
     }
 }
