@@ -1,7 +1,7 @@
 // Inspiring efficiency (Sec. 4.2 / Sec. 4.3), "pull" form of the window sweep.
 //
-// A warp owns 64 consecutive sources (lane j <-> v0 + j and v0 + 32 + j, two
-// codes per lane) and visits every task
+// A warp owns IE_PULL_SOURCES (64 or 128) consecutive sources (lane j <->
+// v0 + j + 32 q, several codes per lane) and visits every task
 // u = v0, v0+1, ... in id order (a topological order).  Each lane keeps, per
 // task, one value in a shared-memory ring of W slots (W a power of two above
 // every edge span, so every predecessor of u is still in the ring):
@@ -31,15 +31,26 @@ constexpr int PULL_MAX_WARPS = 16;  // warps per CTA: blockDim / 32 (autotuned)
 constexpr int PCH = 32;      // tasks per staged chunk
 constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks read the rest from global)
 constexpr int32_t OVER = 0x7fffffff;
-constexpr int SPW = IE_PULL_SOURCES;  // sources per warp: lane j owns v0 + j and v0 + 32 + j
+constexpr int SPW = IE_PULL_SOURCES;  // sources per warp: lane j owns v0 + j + 32 q, q < NV
+constexpr int NV = SPW / 32;          // codes per lane
 
-// ring of W rows of 32 lanes x 2 values
-__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 8; }
+// NV codes per lane, moved as one vector
+template <int V> struct CodeVec;
+template <> struct CodeVec<2> { using T = int2; };
+template <> struct CodeVec<4> { using T = int4; };
+using Codes = CodeVec<NV>::T;
+__device__ __forceinline__ int32_t cget(const int2 &a, int q) { return q == 0 ? a.x : a.y; }
+__device__ __forceinline__ int32_t cget(const int4 &a, int q) { return q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w; }
+__device__ __forceinline__ int2 cmake(const int32_t (&v)[2]) { return make_int2(v[0], v[1]); }
+__device__ __forceinline__ int4 cmake(const int32_t (&v)[4]) { return make_int4(v[0], v[1], v[2], v[3]); }
+
+// ring of W rows of 32 lanes x NV values
+__host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4 * NV; }
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
 
-// At most 48 registers: 40 resident warps per SM (64 registers would allow 32).
-__global__ void __maxnreg__(48)
+// A register cap keeps more warps resident (48 registers: 40 warps per SM instead of 32).
+__global__ void __maxnreg__(NV == 2 ? 48 : 64)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
               const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
@@ -48,7 +59,8 @@ __global__ void __maxnreg__(48)
     const int wib = threadIdx.x >> 5;
     const int32_t wmask = W - 1;
     unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
-    int2 *__restrict__ val = reinterpret_cast<int2 *>(gring) + (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / 8);
+    Codes *__restrict__ val = reinterpret_cast<Codes *>(gring) +
+                              (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / sizeof(Codes));
     int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
     int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
     int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
@@ -71,7 +83,9 @@ __global__ void __maxnreg__(48)
         const int32_t *pc = pcol + eb;
         const int64_t T = unit_time[d];
 
-        int32_t cnt_x = 0, cnt_y = 0;  // sources v0 + lane and v0 + 32 + lane
+        int32_t cnt[NV];  // per source v0 + lane + 32 q
+#pragma unroll
+        for (int q = 0; q < NV; ++q) cnt[q] = 0;
         int32_t hi = v0 + n_src - 1;
         int32_t uc = -1, e0 = 0, ne = 0;  // first task, first predecessor edge and staged entries of the chunk
         for (int32_t u = v0; u <= hi; ++u) {
@@ -120,52 +134,64 @@ __global__ void __maxnreg__(48)
             const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
             // staged entries of this task (compacted), then any beyond the staging from global
             const int32_t clo = c_kp[k], chi = hi_p <= ne ? c_kp[k + 1] : c_kp[PCH];
-            int2 ma = make_int2(-1, -1), mb = make_int2(-1, -1);
-            {
-                // full rounds of 4 predecessor pairs in flight, then a short tail
-                int32_t e = clo;
-                for (; e + 4 <= chi; e += 4) {
-                    int2 pv[4];
+            constexpr int U = NV == 2 ? 4 : 2;  // predecessor rows in flight per round
+            int32_t ma[NV], mb[NV];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) pv[r] = val[c_off[e + r] + lane];
-                    ma.x = max(ma.x, max(pv[0].x, pv[1].x));
-                    ma.y = max(ma.y, max(pv[0].y, pv[1].y));
-                    mb.x = max(mb.x, max(pv[2].x, pv[3].x));
-                    mb.y = max(mb.y, max(pv[2].y, pv[3].y));
+            for (int q = 0; q < NV; ++q) ma[q] = mb[q] = -1;
+            {
+                int32_t e = clo;
+                for (; e + U <= chi; e += U) {
+                    Codes pv[U];
+#pragma unroll
+                    for (int r = 0; r < U; ++r) pv[r] = val[c_off[e + r] + lane];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        ma[q] = max(ma[q], cget(pv[0], q));
+                        mb[q] = max(mb[q], cget(pv[1], q));
+                        if (U == 4) {
+                            ma[q] = max(ma[q], cget(pv[U == 4 ? 2 : 0], q));
+                            mb[q] = max(mb[q], cget(pv[U == 4 ? 3 : 1], q));
+                        }
+                    }
                 }
                 for (; e < chi; ++e) {
-                    const int2 x = val[c_off[e] + lane];
-                    ma.x = max(ma.x, x.x);
-                    ma.y = max(ma.y, x.y);
+                    const Codes x = val[c_off[e] + lane];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
                 }
             }
             for (int32_t e = max(lo, ne); e < hi_p; ++e) {
-                const int32_t q = pc[e0 + e];
-                if (q >= v0) {
-                    const int2 x = val[(q & wmask) * 32 + lane];
-                    ma.x = max(ma.x, x.x);
-                    ma.y = max(ma.y, x.y);
+                const int32_t qd = pc[e0 + e];
+                if (qd >= v0) {
+                    const Codes x = val[(qd & wmask) * 32 + lane];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
                 }
             }
-            const int32_t mx = max(ma.x, mb.x), my = max(ma.y, mb.y);
             const int32_t c = c_cost[k];
+            const int32_t own = c <= int32_t(T) ? c : OVER;
             // branch-free: T < 2^31 here, so m + c (both <= T + 1) fits in 32 unsigned bits.  A
             // source's own m is -1 (tasks before a source are outside its cone).
-            const bool live_x = mx >= 0 && mx != OVER, live_y = my >= 0 && my != OVER;
-            const uint32_t Lx = uint32_t(mx) + uint32_t(c), Ly = uint32_t(my) + uint32_t(c);
-            const bool fits_x = live_x && Lx <= uint32_t(T), fits_y = live_y && Ly <= uint32_t(T);
-            const int32_t own = c <= int32_t(T) ? c : OVER;
-            int32_t vx = live_x ? (fits_x ? int32_t(Lx) : OVER) : mx;
-            int32_t vy = live_y ? (fits_y ? int32_t(Ly) : OVER) : my;
-            if (u - v0 == lane) vx = own;
-            if (u - v0 == lane + 32) vy = own;
-            cnt_x += fits_x;
-            cnt_y += fits_y;
-            val[(u & wmask) * 32 + lane] = make_int2(vx, vy);
-            if (__any_sync(FULL, (vx >= 0 && vx != OVER) || (vy >= 0 && vy != OVER))) hi = max(hi, c_msucc[k]);
+            int32_t vv[NV];
+            bool any_in = false;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const int32_t m = max(ma[q], mb[q]);
+                const bool live = m >= 0 && m != OVER;
+                const uint32_t L = uint32_t(m) + uint32_t(c);
+                const bool fits = live && L <= uint32_t(T);
+                int32_t v = live ? (fits ? int32_t(L) : OVER) : m;
+                if (u - v0 == lane + 32 * q) v = own;
+                cnt[q] += fits;
+                vv[q] = v;
+                any_in |= v >= 0 && v != OVER;
+            }
+            val[(u & wmask) * 32 + lane] = cmake(vv);
+            if (__any_sync(FULL, any_in)) hi = max(hi, c_msucc[k]);
         }
-        if (lane < n_src) ie_out[tb + v0 + lane] = cnt_x;
-        if (lane + 32 < n_src) ie_out[tb + v0 + 32 + lane] = cnt_y;
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+            if (lane + 32 * q < n_src) ie_out[tb + v0 + 32 * q + lane] = cnt[q];
         __syncwarp();
     }
 }

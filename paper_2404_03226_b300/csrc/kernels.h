@@ -69,7 +69,9 @@ void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int
 // pull form: its per-warp ring is W x 128 bytes, so long spans only cost ring memory (the
 // tuning's ring budget then admits fewer warps); beyond it the global form runs.
 constexpr int32_t IE_PULL_MAX_W = 8192;
-// Sources per work item of the pull form (one warp, two per lane).
+// Sources per work item of the pull form (one warp; 64 = two per lane).  128 (four per lane,
+// int4 ring rows) runs 24 % fewer instructions but was measured 1.5x slower: the ring
+// traffic then bounds the sweep.
 constexpr int32_t IE_PULL_SOURCES = 64;
 int ie_pull_max_warps();
 int64_t ie_pull_ring_bytes(int32_t W);
