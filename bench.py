@@ -514,7 +514,7 @@ def main():
                     help="keep the library's default launch shapes instead of autotuning them on the batch")
     ap.add_argument("--tuning", default=None,
                     help='explicit tuning as JSON, e.g. \'{"groups": 1, "attr_overlap": 0, "ia_warps": 32, '
-                         '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64}\'')
+                         '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64, "group_split": 0}\'')
     ap.add_argument("--no-policies", dest="no_policies", action="store_true",
                     help="skip the DMDA / DMDAP baselines and the unit-time search leg")
     ap.add_argument("--profile", action="store_true",

@@ -83,13 +83,24 @@ int device_info(DeviceInfo &di) {
 }
 
 constexpr int MAX_GROUPS = 16;
-const insp_tuning kDefaultTuning = {4, 0, 32, 16, 512, 4, 64};
+const insp_tuning kDefaultTuning = {1, 1, 16, 16, 512, 4, 64, 0};
 
 bool tuning_ok(const insp_tuning &t) {
     return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
            t.ia_warps >= 1 && t.ia_warps <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
            t.ie_ring_mb <= 65536 && t.sim_warps >= 1 && t.sim_warps <= 8 &&
-           (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128);
+           (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128) && (t.group_split == 0 || t.group_split == 1);
+}
+
+// First DAG rank of size group g of G (g = G: ndag), equal DAG counts or geometric (group g
+// holds 4x the DAGs of group g - 1).
+int group_begin(int g, int G, int ndag, int split) {
+    if (g <= 0) return 0;
+    if (g >= G) return ndag;
+    if (split == 0) return int(int64_t(g) * ndag / G);
+    int64_t denom = 1;
+    for (int k = g; k < G; ++k) denom *= 4;
+    return int(int64_t(ndag) / denom);
 }
 
 }  // namespace
@@ -1073,7 +1084,8 @@ INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int
     // simulation of group g starts on its own stream as soon as the attributes of
     // group g are done, while the attributes of the later groups still run
     for (int g = 0; g < G; ++g) {
-        const int r0 = int(int64_t(g) * b->ndag / G), r1 = int(int64_t(g + 1) * b->ndag / G);
+        const int r0 = group_begin(g, G, b->ndag, b->tun.group_split);
+        const int r1 = group_begin(g + 1, G, b->ndag, b->tun.group_split);
         int32_t *cg = ctr + 16 + 4 * g;
         if ((rc = launch_attr(b, r0, r1, cg, ut, pull, wide, d_ia, d_ie, s, s_ie))) return rc;
         A.order = b->order.as<int32_t>() + r0;
@@ -1324,12 +1336,18 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     // 4. pipelining: size groups and concurrent attribute sweeps
     if (rc == INSP_OK) {
         c.clear();
-        for (int g : {1, 2, 4, 8, 16})
-            for (int ov : {0, 1}) {
+        for (int ov : {0, 1}) {
+            for (int g : {1, 2, 4, 8, 16}) {
                 insp_tuning t = best;
-                t.groups = g; t.attr_overlap = ov;
+                t.groups = g; t.attr_overlap = ov; t.group_split = 0;
                 c.push_back(t);
             }
+            for (int g : {2, 3, 4}) {
+                insp_tuning t = best;
+                t.groups = g; t.attr_overlap = ov; t.group_split = 1;
+                c.push_back(t);
+            }
+        }
         rc = search(c);
     }
     cudaEventDestroy(e0);

@@ -11,11 +11,13 @@ from helpers import compare_dag, edge_case_dags
 pytestmark = pytest.mark.gpu
 
 TUNINGS = [
-    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64),
-    dict(groups=3, attr_overlap=1, ia_warps=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32),
-    dict(groups=16, attr_overlap=0, ia_warps=32, ie_warps=16, ie_ring_mb=2048, sim_warps=8, sim_queue=128),
-    dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128),
-    dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32),
+    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64, group_split=0),
+    dict(groups=3, attr_overlap=1, ia_warps=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32, group_split=0),
+    dict(groups=16, attr_overlap=0, ia_warps=32, ie_warps=16, ie_ring_mb=2048, sim_warps=8, sim_queue=128,
+         group_split=0),
+    dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128, group_split=1),
+    dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32, group_split=0),
+    dict(groups=3, attr_overlap=0, ia_warps=16, ie_warps=16, ie_ring_mb=512, sim_warps=4, sim_queue=64, group_split=1),
 ]
 
 
@@ -101,7 +103,7 @@ def test_tuning_rejects_out_of_range():
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
     good = B.tuning
     for field, bad in (("groups", 0), ("groups", 17), ("attr_overlap", 2), ("ia_warps", 0), ("ia_warps", 33),
-                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48)):
+                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48), ("group_split", 2)):
         t = dict(good, **{field: bad})
         with pytest.raises(P.InspError):
             B.tuning = t
