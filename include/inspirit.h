@@ -313,6 +313,14 @@ int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t);
 int insp_batch_get_tuning(const insp_batch *b, insp_tuning *t);
 int insp_machine_set_tuning(insp_machine *m, const insp_tuning *t);
 
+/* Self-test of failure detection, no GPU fault involved: one warp waits, with
+ * the library's bounded device-side wait (the one the ability sweep uses for
+ * its done flags), until a device flag holding flag_value equals wait_value,
+ * polling at most `limit` times.  Returns INSP_OK when the values match and
+ * INSP_ETIMEOUT when the wait gave up (the context stays usable).  No
+ * counterpart in the paper.  Synchronous.  Errors: INSP_EINVAL (limit < 1). */
+int insp_selftest_wait(int32_t flag_value, int32_t wait_value, int32_t limit, void *stream);
+
 /* Kernel timing, a tracing aid.  While enabled, every attributes / simulate
  * call on the batch records CUDA events on its stream around each kernel.
  * insp_batch_timing waits for them and returns the summed milliseconds and

@@ -63,6 +63,7 @@ _PROTOS = {
     "insp_simulate_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(insp_trace), _vp]),
     "insp_bottom_level_batch": (ctypes.c_int, [_vp, _vp, _vp]),
     "insp_unit_time_search": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
+    "insp_selftest_wait": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _vp]),
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
@@ -315,3 +316,7 @@ def insp_bottom_level_batch(b, bl, stream=None) -> None:
 
 def insp_unit_time_search(b, k_max: int, unit_time_ns, stream=None) -> None:
     check(lib().insp_unit_time_search(b, int(k_max), ptr(unit_time_ns), stream_ptr(stream)))
+
+
+def insp_selftest_wait(flag_value: int, wait_value: int, limit: int, stream=None) -> None:
+    check(lib().insp_selftest_wait(int(flag_value), int(wait_value), int(limit), stream_ptr(stream)))

@@ -60,6 +60,21 @@ __device__ __forceinline__ int64_t warp_min_i64(int64_t v) {
 __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const volatile int32_t *)p; }
 __device__ __forceinline__ void st_volatile(int32_t *p, int v) { *(volatile int32_t *)p = v; }
 
+// Bounded wait until *flag == value: gives up (returns false) after `limit` polls, or at
+// once when *abort is set (another waiter gave up), and then sets *abort.  Every
+// device-side wait of the library goes through here, so none can hang the GPU.
+__device__ __forceinline__ bool wait_flag(const int32_t *flag, int32_t value, int32_t *abort, int limit) {
+    int it = 0;
+    while (ld_volatile(flag) != value) {
+        if (++it > limit || ld_volatile(abort)) {
+            st_volatile(abort, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
 // Index of the last element of a[0..n) that is <= x (a ascending, a[0] <= x).
 __device__ __forceinline__ int upper_index(const int64_t *a, int n, int64_t x) {
     int lo = 0, hi = n - 1;

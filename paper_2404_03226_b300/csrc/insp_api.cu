@@ -1359,6 +1359,24 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     return first_status(b, st);
 }
 
+INSP_API int insp_selftest_wait(int32_t flag_value, int32_t wait_value, int32_t limit, void *stream) {
+    if (limit < 1) return fail(INSP_EINVAL, "limit must be >= 1");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    DBuf buf;
+    int rc = buf.alloc(8);
+    if (rc) return rc;
+    int32_t *d = buf.as<int32_t>();
+    const int32_t h[2] = {flag_value, -1};
+    CU(cudaMemcpyAsync(d, h, 8, cudaMemcpyHostToDevice, s));
+    insp::launch_wait_probe(d, wait_value, limit, d + 1, s);
+    CU(cudaGetLastError());
+    int32_t st = -1;
+    CU(cudaMemcpyAsync(&st, d + 1, 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if (st == INSP_ETIMEOUT) return fail(INSP_ETIMEOUT, "a bounded device-side wait gave up");
+    return st == INSP_OK ? INSP_OK : fail(INSP_ECUDA, "wait probe wrote no status");
+}
+
 INSP_API int insp_batch_set_timing(insp_batch *b, int32_t enable) {
     if (!b) return fail(INSP_EINVAL, "batch is NULL");
     b->timing = enable != 0;

@@ -59,15 +59,7 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
             // wait until every successor's row is published (bounded)
             for (int32_t i = lane; i < deg; i += 32) {
                 const int32_t s = col[lo + i];
-                int it = 0;
-                while (ld_volatile(done + tb + s) != epoch) {
-                    if (++it > SPIN_LIMIT || ld_volatile(&s_abort)) {
-                        timed_out = true;
-                        st_volatile(&s_abort, 1);
-                        break;
-                    }
-                    __nanosleep(64);
-                }
+                if (!wait_flag(done + tb + s, epoch, &s_abort, SPIN_LIMIT)) timed_out = true;
             }
             __syncwarp();
             __threadfence_block();
@@ -203,6 +195,21 @@ __global__ void __launch_bounds__(256) k_ie(DevBatch B, const int64_t *item_base
         if (lane < n_src) ie_out[tb + v0 + lane] = cnt;
         __syncwarp();
     }
+}
+
+// Self-test of the bounded wait (failure detection without a GPU fault): one
+// warp waits for flag == value with at most `limit` polls; status gets
+// INSP_ETIMEOUT if the wait gave up.
+__global__ void k_wait_probe(const int32_t *flag, int32_t value, int32_t limit, int32_t *status) {
+    __shared__ int32_t s_abort;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    const bool ok = wait_flag(flag, value, &s_abort, limit);
+    if (threadIdx.x == 0) *status = ok ? INSP_OK : INSP_ETIMEOUT;
+}
+
+void launch_wait_probe(const int32_t *flag, int32_t value, int32_t limit, int32_t *status, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(flag, value, limit, status);
 }
 
 // Start of an attributes step: the done-flag epoch and the record tags advance
