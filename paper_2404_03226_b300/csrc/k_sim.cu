@@ -66,10 +66,11 @@ struct Pool {
             g_idw[j] = idw_; g_seq[j] = seq_; g_ia[j] = ia_; g_ie[j] = ie_; g_dr[j] = dr_; g_cost[j] = cost_;
         }
     }
-    // copy entry `from` into slot `to`: one lane, its six independent loads in flight together
-    // (one lane per field would serialise six divergent paths)
-    __device__ __forceinline__ void move(int from, int to, int lane) const {
-        if (lane == 0) set(to, idw(from), seq(from), ia(from), ie(from), dr(from), cost(from));
+    // copy entry `from` into slot `to`: one lane (lane 0, or the caller's lane when `mine`),
+    // its six independent loads in flight together (one lane per field would serialise six
+    // divergent paths)
+    __device__ __forceinline__ void move(int from, int to, int lane, bool mine = false) const {
+        if (mine || lane == 0) set(to, idw(from), seq(from), ia(from), ie(from), dr(from), cost(from));
     }
 };
 
@@ -428,19 +429,18 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (wl == 0) return false;
             const int32_t src_lane = __ffs(wl) - 1;
             const int32_t idx = __shfl_sync(FULL, bi, src_lane);
-            const int32_t t = pool.idw(idx) & 0xffffff;
-            const int64_t dr = pool.dr(idx), c = pool.cost(idx);
-            __syncwarp();
             const int32_t last = nready - 1;
-            if (idx != last) pool.move(last, idx, lane);
             nready -= 1;
             npop += 1;
-            const int64_t s = max(now, dr), e = s + c;
+            // the rest by the lane that owns worker w: read the entry, fill its slot with the
+            // last entry, start the task, write its schedule
             if (lane == (w & 31)) {
+                const int32_t t = pool.idw(idx) & 0xffffff;
+                const int64_t dr = pool.dr(idx), c = pool.cost(idx);
+                if (idx != last) pool.move(last, idx, lane, true);
+                const int64_t s = max(now, dr), e = s + c;
                 if (TWO && w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; }
                 else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; rlo0 = rp[t]; rhi0 = rp[t + 1]; }
-            }
-            if (lane == 0) {
                 A.worker[tb + t] = w;
                 A.start[tb + t] = s;
                 A.end[tb + t] = e;
