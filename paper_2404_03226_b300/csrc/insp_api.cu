@@ -181,7 +181,7 @@ struct insp_batch {
     int64_t ie_rec_stride = 0;
     // tuning and the launch shapes derived from it
     insp_tuning tun = kDefaultTuning;
-    int64_t ia_slot = 1;  // bitset words per CTA slot of the ability sweep
+    int64_t ia_slot = 1;  // 64-bit bitset words per CTA slot of the ability sweep
     int grid_ia = 0;
     bool ie_global_ready = false;
     int grid_ie = 1;
@@ -233,13 +233,13 @@ int alloc_ia(insp_batch *b) {
     int rc = device_info(di);
     if (rc) return rc;
     const int64_t n = b->max_n;
-    b->ia_slot = std::max<int64_t>(n * ((n + 31) / 32), 1);
+    b->ia_slot = std::max<int64_t>(n * ((n + 63) / 64), 1);  // 64-bit words
     const int occ = std::max(1, insp::ia_occupancy(b->tun.ia_warps));
     const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
     int64_t g = std::min<int64_t>(int64_t(di.sms) * occ, b->ndag);
-    g = std::max<int64_t>(1, std::min(g, budget / (b->ia_slot * 4)));
+    g = std::max<int64_t>(1, std::min(g, budget / (b->ia_slot * 8)));
     b->grid_ia = int(g);
-    return b->sc->ia_bits.alloc(size_t(g * b->ia_slot) * 4 + 16);
+    return b->sc->ia_bits.alloc(size_t(g * b->ia_slot) * 8 + 16);
 }
 
 // Window rings of the pull efficiency sweep for the current tuning (L2 budget).
@@ -706,7 +706,7 @@ int launch_attr(insp_batch *b, int r0, int r1, int32_t *ctr, const int64_t *ut, 
     if (nd <= 0) return INSP_OK;
     {
         TimedLaunch tl(b, TK_IA, s_ia);
-        insp::launch_ia(B, b->order.as<int32_t>() + r0, nd, ctr + 0, S.ia_bits.as<uint32_t>(), b->ia_slot,
+        insp::launch_ia(B, b->order.as<int32_t>() + r0, nd, ctr + 0, S.ia_bits.as<uint64_t>(), b->ia_slot,
                         S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(),
                         std::min(b->grid_ia, nd), b->tun.ia_warps, s_ia);
     }
@@ -987,7 +987,7 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
     const int32_t *order = b->order.as<int32_t>();
     const int grid = std::max(1, std::min(di.sms * 8, (nd + 7) / 8));
     insp::launch_step_begin(sc, b->n_items, s);
-    insp::launch_ia(B, order, nd, c + 0, S.ia_bits.as<uint32_t>(), b->ia_slot, S.ia_done.as<int32_t>(), &sc->epoch,
+    insp::launch_ia(B, order, nd, c + 0, S.ia_bits.as<uint64_t>(), b->ia_slot, S.ia_done.as<int32_t>(), &sc->epoch,
                     ia.as<int32_t>(), b->status.as<int32_t>(), std::min(b->grid_ia, nd), b->tun.ia_warps, s);
     insp::launch_search_target(B, order, c + 1, ia.as<int32_t>(), layer.as<int32_t>(), bm.as<uint32_t>(),
                                bmb.as<int64_t>(), target.as<int64_t>(), grid, s);

@@ -22,16 +22,17 @@ namespace insp {
 // --------------------------------------------------------- inspiring ability
 constexpr int IA_MAX_WARPS = 32;  // warps per CTA: blockDim / 32, up to 32 (per size bin, autotuned)
 
+// Descendant rows are bitsets of 64-bit words (half the word operations of 32-bit ones).
 __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t n_order,
-                                                          int32_t *counter,
-                                                      uint32_t *bits, int64_t slot_words, int32_t *done,
-                                                      const int32_t *epoch_ptr, int32_t *ia_out, int32_t *status) {
+                                                          int32_t *counter, uint64_t *bits, int64_t slot_words,
+                                                          int32_t *done, const int32_t *epoch_ptr, int32_t *ia_out,
+                                                          int32_t *status) {
     const int32_t epoch = *epoch_ptr;  // this step's value of the done flags
     __shared__ int32_t s_dag;
     __shared__ int32_t s_next;
     __shared__ int32_t s_abort;  // a wait gave up: later waits of this DAG return at once
     const int lane = threadIdx.x & 31;
-    uint32_t *slot = bits + int64_t(blockIdx.x) * slot_words;
+    uint64_t *slot = bits + int64_t(blockIdx.x) * slot_words;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -46,7 +47,7 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
         if (d < 0) return;
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];
         const int32_t n = int32_t(B.task_base[d + 1] - tb);
-        const int32_t NW = (n + 31) >> 5;
+        const int32_t NW = (n + 63) >> 6;
         const int32_t *rp = B.row_ptr + tb + d;
         const int32_t *col = B.col_idx + eb;
         bool timed_out = false;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
             // Words wlo..NW-1 of the row are needed.  The warp splits into
             // 32/g groups of g lanes (g = words per chunk, a power of two);
             // groups OR different successors, then combine by shuffle-xor.
-            const int32_t wlo = (v + 1) >> 5;
+            const int32_t wlo = (v + 1) >> 6;
             const int32_t span_w = NW - wlo;
             int32_t g = 32;
             if (span_w < 32) {
@@ -74,22 +75,22 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
                 while (g < span_w) g <<= 1;
             }
             const int32_t G = 32 / g, grp = lane / g, wl = lane % g;
-            uint32_t *row_v = slot + int64_t(v) * NW;
+            uint64_t *row_v = slot + int64_t(v) * NW;
             int32_t count = 0;
             for (int32_t cw = wlo; cw < NW; cw += g) {
                 const int32_t w = cw + wl;
-                uint32_t acc = 0;
+                uint64_t acc = 0;
 #pragma unroll 4
                 for (int32_t i = grp; i < deg; i += G) {
                     const int32_t s = col[lo + i];
-                    const int32_t ws = (s + 1) >> 5;
+                    const int32_t ws = (s + 1) >> 6;
                     if (w >= ws && w < NW) acc |= slot[int64_t(s) * NW + w];
-                    if (w == (s >> 5)) acc |= 1u << (s & 31);
+                    if (w == (s >> 6)) acc |= 1ull << (s & 63);
                 }
                 for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
                 if (grp == 0 && w < NW) {
                     row_v[w] = acc;
-                    count += __popc(acc);
+                    count += __popcll(acc);
                 }
             }
             count = __reduce_add_sync(FULL, count);
@@ -221,7 +222,7 @@ __global__ void k_step_begin(StepCounters *c, int64_t n_items) {
 
 void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s) { k_step_begin<<<1, 1, 0, s>>>(c, n_items); }
 
-void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint32_t *bits,
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint64_t *bits,
                int64_t slot_words, int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid,
                int warps, cudaStream_t s) {
     k_ia<<<grid, 32 * warps, 0, s>>>(B, order, n_order, counter, bits, slot_words, done, epoch, ia, status);

@@ -59,7 +59,7 @@ struct StepCounters {
 };
 void launch_step_begin(StepCounters *c, int64_t n_items, cudaStream_t s);
 void launch_wait_probe(const int32_t *flag, int32_t value, int32_t limit, int32_t *status, cudaStream_t s);
-void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint32_t *bits,
+void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t *counter, uint64_t *bits,
                int64_t slot_words, int32_t *done, const int32_t *epoch, int32_t *ia, int32_t *status, int grid,
                int warps, cudaStream_t s);
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
