@@ -33,6 +33,15 @@ constexpr int PCOL = 768;    // staged predecessor ids per chunk (longer chunks 
 constexpr int32_t OVER = 0x7fffffff;
 constexpr int SPW = IE_PULL_SOURCES;  // sources per warp: lane j owns v0 + j + 32 q, q < NV
 constexpr int NV = SPW / 32;          // codes per lane
+// Predecessor rows loaded per round before they are combined, and the register cap that
+// holds them (8 rows at 56 registers, 36 resident warps per SM, measured best of 4/48,
+// 6/56, 8/56 and 8/64 on the layered workload).
+#ifndef IE_PULL_MAXREG
+#define IE_PULL_MAXREG 56
+#endif
+#ifndef IE_PULL_INFLIGHT
+#define IE_PULL_INFLIGHT 8
+#endif
 
 // NV codes per lane, moved as one vector
 template <int V> struct CodeVec;
@@ -49,8 +58,8 @@ __host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
 
-// A register cap keeps more warps resident (48 registers: 40 warps per SM instead of 32).
-__global__ void __maxnreg__(NV == 2 ? 48 : 64)
+// A register cap keeps more warps resident than the 64 registers a free compile takes.
+__global__ void __maxnreg__(IE_PULL_MAXREG)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
               const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
@@ -134,7 +143,7 @@ __global__ void __maxnreg__(NV == 2 ? 48 : 64)
             const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
             // staged entries of this task (compacted), then any beyond the staging from global
             const int32_t clo = c_kp[k], chi = hi_p <= ne ? c_kp[k + 1] : c_kp[PCH];
-            constexpr int U = NV == 2 ? 4 : 2;  // predecessor rows in flight per round
+            constexpr int U = IE_PULL_INFLIGHT;  // predecessor rows in flight per round
             int32_t ma[NV], mb[NV];
 #pragma unroll
             for (int q = 0; q < NV; ++q) ma[q] = mb[q] = -1;
@@ -145,14 +154,12 @@ __global__ void __maxnreg__(NV == 2 ? 48 : 64)
 #pragma unroll
                     for (int r = 0; r < U; ++r) pv[r] = val[c_off[e + r] + lane];
 #pragma unroll
-                    for (int q = 0; q < NV; ++q) {
-                        ma[q] = max(ma[q], cget(pv[0], q));
-                        mb[q] = max(mb[q], cget(pv[1], q));
-                        if (U == 4) {
-                            ma[q] = max(ma[q], cget(pv[U == 4 ? 2 : 0], q));
-                            mb[q] = max(mb[q], cget(pv[U == 4 ? 3 : 1], q));
+                    for (int r = 0; r < U; r += 2)
+#pragma unroll
+                        for (int q = 0; q < NV; ++q) {
+                            ma[q] = max(ma[q], cget(pv[r], q));
+                            mb[q] = max(mb[q], cget(pv[r + 1], q));
                         }
-                    }
                 }
                 for (; e < chi; ++e) {
                     const Codes x = val[c_off[e] + lane];
