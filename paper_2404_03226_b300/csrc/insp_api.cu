@@ -145,6 +145,16 @@ struct Scratch {
     }
 };
 
+// Device copies of a batch's inputs and what the load derives from them.  A batch borrows
+// one set from its machine at load and hands it back when destroyed (like Scratch), so
+// loading batch after batch reuses the allocations instead of paying cudaMalloc / cudaFree.
+struct BatchBufs {
+    DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
+    DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
+    DBuf pr_ptr, pcol, cursor;
+    DBuf item_dag, item_dag_lpt, item_base_lpt;
+};
+
 struct insp_machine {
     int32_t n_cpu = 0, n_gpu = 0;
     int64_t xfer = 0;
@@ -152,6 +162,7 @@ struct insp_machine {
     bool has_scorer = false;
     DBuf scorer;  // insp::ScorerPacked in device memory
     std::vector<std::unique_ptr<Scratch>> spare;
+    std::vector<std::unique_ptr<BatchBufs>> spare_bufs;
     insp_tuning tun = kDefaultTuning;  // the tuning batches loaded on this machine start with
 };
 
@@ -159,19 +170,24 @@ enum { TK_IA = 0, TK_IE = 1, TK_SIM = 2, TK_SIM_SINGLE = 3, TK_N = 4 };
 
 struct insp_batch {
     insp_machine *owner = nullptr;
+    std::unique_ptr<BatchBufs> bufs;  // declared before the references into it
     insp_machine mach_params;
     const insp_machine &mach = mach_params;
     int32_t ndag = 0, n_types = 1;
     int64_t n_total = 0, m_total = 0;
     std::vector<int64_t> h_task_base, h_edge_base;
     std::vector<int32_t> h_order;  // DAGs by descending size
-    DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
-    DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
-    DBuf pr_ptr, pcol;      // predecessor lists (pull form of the efficiency sweep)
+    DBuf &task_base = bufs->task_base, &edge_base = bufs->edge_base, &row_ptr = bufs->row_ptr,
+         &col_idx = bufs->col_idx, &type = bufs->type, &type_cost = bufs->type_cost, &task_cost = bufs->task_cost;
+    DBuf &indeg0 = bufs->indeg0, &unit_time_def = bufs->unit_time_def, &unit_time_user = bufs->unit_time_user,
+         &order = bufs->order, &item_base = bufs->item_base, &status = bufs->status, &max_span = bufs->max_span,
+         &counters = bufs->counters;
+    DBuf &pr_ptr = bufs->pr_ptr, &pcol = bufs->pcol;  // predecessor lists (pull form of the efficiency sweep)
     bool pull = false;      // predecessor lists built: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
     int grid_ie_pull = 0;   // its grid for the current tuning
-    DBuf item_dag;          // DAG of every 32-source work item (items numbered by DAG id)
-    DBuf item_dag_lpt, item_base_lpt;  // the same items numbered along the size order (pull sweep)
+    DBuf &item_dag = bufs->item_dag;  // DAG of every 32-source work item (items numbered by DAG id)
+    // the pull sweep's items numbered along the size order
+    DBuf &item_dag_lpt = bufs->item_dag_lpt, &item_base_lpt = bufs->item_base_lpt;
     std::vector<int64_t> h_rank_item;  // first item (size-order numbering) of the DAG at each rank
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
@@ -194,10 +210,15 @@ struct insp_batch {
     int64_t launches[TK_N] = {0, 0, 0, 0};
     cudaGraphExec_t graph = nullptr;  // recorded evaluation step (insp_batch_record)
 
+    explicit insp_batch(std::unique_ptr<BatchBufs> bb) : bufs(std::move(bb)) {}
+    insp_batch(const insp_batch &) = delete;
+    insp_batch &operator=(const insp_batch &) = delete;
+
     ~insp_batch() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
+        if (owner && bufs && owner->spare_bufs.size() < 2) owner->spare_bufs.push_back(std::move(bufs));
     }
 
     insp::DevBatch dev() const {
@@ -494,7 +515,15 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (ndag < 0 || !task_base || !edge_base) return fail(INSP_EINVAL, "bad ndag or base arrays");
     if (n_types < 1 || n_types > 64) return fail(INSP_EINVAL, "n_types must be in 1..64");
     if (!type_cost && !task_cost) return fail(INSP_EINVAL, "need type_cost or task_cost");
-    auto *b = new (std::nothrow) insp_batch;
+    std::unique_ptr<BatchBufs> bb;
+    if (!m->spare_bufs.empty()) {
+        bb = std::move(m->spare_bufs.back());
+        m->spare_bufs.pop_back();
+    } else {
+        bb.reset(new (std::nothrow) BatchBufs);
+        if (!bb) return fail(INSP_ENOMEM, "host allocation");
+    }
+    auto *b = new (std::nothrow) insp_batch(std::move(bb));
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
     b->owner = m;
@@ -609,7 +638,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
         return bail(rc);
     // pull form of the efficiency sweep when its window is at most IE_PULL_MAX_W
     if (b->W <= insp::IE_PULL_MAX_W && ndag > 0) {
-        DBuf cursor;
+        DBuf &cursor = b->bufs->cursor;
         if ((rc = b->pr_ptr.alloc((b->n_total + ndag) * 4)) || (rc = b->pcol.alloc(std::max<int64_t>(b->m_total, 1) * 4)) ||
             (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
             return bail(rc);
