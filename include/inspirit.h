@@ -92,7 +92,8 @@ typedef struct insp_batch insp_dag;       /* a batch holding exactly one DAG */
 int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy,
                         insp_machine **out);
 /* Destroy a machine after every batch loaded on it: a destroyed batch hands its
- * kernel scratch back to its machine for reuse by the next load. */
+ * kernel scratch and its device buffers back to its machine for reuse by the
+ * next load (up to two sets are kept; they are freed here). */
 void insp_machine_destroy(insp_machine *m);
 
 /* Install the learned proposal scorer used by INSP_POLICY_LEARNED: an MLP
