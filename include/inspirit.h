@@ -294,7 +294,8 @@ typedef struct {
     int32_t ie_ring_mb;    /* device memory for the efficiency sweep's window rings, MB (1..65536); it
                               bounds the warps in flight, and rings beyond L2 spill to HBM */
     int32_t sim_warps;     /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
-    int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64 or 128 */
+    int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64, 128, 256 or 512
+                              (more spill to global memory) */
     int32_t group_split;   /* 0: groups of equal DAG counts; 1: geometric, each group 4x the DAGs of the
                               one before (the largest DAGs, whose simulations take longest, start first) */
 } insp_tuning;

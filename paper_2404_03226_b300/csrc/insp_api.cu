@@ -89,7 +89,9 @@ bool tuning_ok(const insp_tuning &t) {
     return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
            t.ia_warps >= 1 && t.ia_warps <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
            t.ie_ring_mb <= 65536 && t.sim_warps >= 1 && t.sim_warps <= 8 &&
-           (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128) && (t.group_split == 0 || t.group_split == 1);
+           (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128 || t.sim_queue == 256 ||
+            t.sim_queue == 512) &&
+           (t.group_split == 0 || t.group_split == 1);
 }
 
 // First DAG rank of size group g of G (g = G: ndag), equal DAG counts or geometric (group g
@@ -1335,7 +1337,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     std::vector<insp_tuning> c;
     // 1. simulation: DAGs per CTA and queue capacity
     for (int w : {2, 4, 8})
-        for (int q : {32, 64, 128}) {
+        for (int q : {32, 64, 128, 256, 512}) {
             insp_tuning t = best;
             t.sim_warps = w; t.sim_queue = q;
             c.push_back(t);

@@ -159,13 +159,15 @@ struct LearnSmem {
 // fewer that slot and all its code drop out at compile time.
 template <bool LEARNED, int POOL_C, bool TWO>
 __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
-    __shared__ WarpSmem<POOL_C> smem_all[SIM_WARPS];
+    // dynamic shared memory: every warp's pool and buffers, then the learned scorer's
+    // weights and per-warp tiles (sized by the warps actually launched)
     extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WarpSmem<POOL_C> *sm = &smem_all[wib];
-    ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn);
-    LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn + sizeof(ScorerPacked)) + wib;
+    WarpSmem<POOL_C> *sm = reinterpret_cast<WarpSmem<POOL_C> *>(dyn) + wib;
+    unsigned char *dyn_l = dyn + (size_t(blockDim.x >> 5) * sizeof(WarpSmem<POOL_C>) + 15) / 16 * 16;
+    ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn_l);
+    LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn_l + sizeof(ScorerPacked)) + wib;
     if (LEARNED) {
         for (int i = threadIdx.x; i < int(sizeof(ScorerPacked) / 4); i += blockDim.x)
             reinterpret_cast<uint32_t *>(SP)[i] = reinterpret_cast<const uint32_t *>(A.scorer)[i];
@@ -567,23 +569,27 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     }
 }
 
-constexpr size_t LEARN_SMEM = sizeof(ScorerPacked) + SIM_WARPS * sizeof(LearnSmem);
+// dynamic shared memory of a launch with `warps` warps per CTA
+template <bool L, int Q>
+static size_t sim_dyn_bytes(int warps) {
+    return (size_t(warps) * sizeof(WarpSmem<Q>) + 15) / 16 * 16 +
+           (L ? sizeof(ScorerPacked) + warps * sizeof(LearnSmem) : 0);
+}
 
 template <bool L, int Q, bool TWO>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
-    if (L) {
-        cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-        k_sim<L, Q, TWO><<<grid, threads, LEARN_SMEM, s>>>(A);
-    } else {
-        k_sim<L, Q, TWO><<<grid, threads, 0, s>>>(A);
-    }
+    cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
+    k_sim<L, Q, TWO><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
 }
 
 template <bool L, bool TWO>
 static void launch_l(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
     if (queue <= 32) launch_q<L, 32, TWO>(A, grid, threads, s);
     else if (queue <= 64) launch_q<L, 64, TWO>(A, grid, threads, s);
-    else launch_q<L, 128, TWO>(A, grid, threads, s);
+    else if (queue <= 128) launch_q<L, 128, TWO>(A, grid, threads, s);
+    else if (queue <= 256) launch_q<L, 256, TWO>(A, grid, threads, s);
+    else launch_q<L, 512, TWO>(A, grid, threads, s);
 }
 
 static void launch_any(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
@@ -607,9 +613,10 @@ int sim_max_warps() { return SIM_WARPS; }
 template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
-    if (L) cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(LEARN_SMEM));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO>, threads, L ? LEARN_SMEM : 0) !=
-        cudaSuccess) {
+    cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO>, threads,
+                                                      sim_dyn_bytes<L, Q>(threads / 32)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -617,8 +624,11 @@ static int occ_q(int threads) {
 }
 template <bool L, bool TWO>
 static int occ_l(int threads, int queue) {
-    return queue <= 32 ? occ_q<L, 32, TWO>(threads) : queue <= 64 ? occ_q<L, 64, TWO>(threads)
-                                                                   : occ_q<L, 128, TWO>(threads);
+    return queue <= 32    ? occ_q<L, 32, TWO>(threads)
+           : queue <= 64  ? occ_q<L, 64, TWO>(threads)
+           : queue <= 128 ? occ_q<L, 128, TWO>(threads)
+           : queue <= 256 ? occ_q<L, 256, TWO>(threads)
+                          : occ_q<L, 512, TWO>(threads);
 }
 int sim_occupancy(bool learned, int n_workers, int warps, int queue) {
     const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));

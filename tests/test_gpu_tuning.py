@@ -18,6 +18,8 @@ TUNINGS = [
     dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128, group_split=1),
     dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32, group_split=0),
     dict(groups=3, attr_overlap=0, ia_warps=16, ie_warps=16, ie_ring_mb=512, sim_warps=4, sim_queue=64, group_split=1),
+    dict(groups=2, attr_overlap=1, ia_warps=16, ie_warps=8, ie_ring_mb=256, sim_warps=8, sim_queue=512, group_split=0),
+    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=3, sim_queue=256, group_split=0),
 ]
 
 
@@ -91,7 +93,7 @@ def test_autotune_keeps_results():
     r0 = _run(B)
     t = B.autotune()
     assert t == B.tuning
-    assert t["sim_queue"] in (32, 64, 128) and 1 <= t["sim_warps"] <= 8 and 1 <= t["ie_warps"] <= 8
+    assert t["sim_queue"] in (32, 64, 128, 256, 512) and 1 <= t["sim_warps"] <= 8 and 1 <= t["ie_warps"] <= 8
     r1 = _run(B)
     for f in r0:
         np.testing.assert_array_equal(r0[f], r1[f], err_msg=f)
@@ -122,3 +124,17 @@ def test_machine_tuning_applies_to_later_batches():
         compare_dag(b, d, out, m)
     with pytest.raises(P.InspError):
         M.set_tuning(dict(TUNINGS[0], sim_queue=7))
+
+
+@pytest.mark.parametrize("queue", [32, 512])
+def test_large_ready_pools(queue):
+    """Tiled DAGs hold hundreds of ready tasks at once: a 512-entry pool keeps them in
+    shared memory, a 32-entry one spills most of them; both give the oracle's schedule."""
+    import paper_2404_03226_b300 as P
+    b = inputs.concat([inputs.tiled(inputs.KIND_CHOLESKY, 16, 2), inputs.tiled(inputs.KIND_QR, 12, 1)])
+    m = inputs.MACHINE_TILED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = dict(TUNINGS[0], sim_queue=queue, sim_warps=2)
+    out = _run(B, True)
+    for d in range(b.ndag):
+        compare_dag(b, d, out, m)
