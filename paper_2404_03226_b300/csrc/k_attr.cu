@@ -67,7 +67,10 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
             // Words wlo..NW-1 of the row are needed.  The warp splits into
             // 32/g groups of g lanes (g = words per chunk, a power of two);
             // groups OR different successors, then combine by shuffle-xor.
-            const int32_t wlo = (v + 1) >> 6;
+            // Stored rows hold the task itself too: row(s) = {s} and its descendants, so a row is
+            // the plain OR of its successors' rows plus its own bit, and IA = popcount - 1.
+            // Words v/64 .. NW-1 of the row are needed.
+            const int32_t wlo = v >> 6;
             const int32_t span_w = NW - wlo;
             int32_t g = 32;
             if (span_w < 32) {
@@ -79,13 +82,11 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
             int32_t count = 0;
             for (int32_t cw = wlo; cw < NW; cw += g) {
                 const int32_t w = cw + wl;
-                uint64_t acc = 0;
+                uint64_t acc = (grp == 0 && w == wlo) ? (1ull << (v & 63)) : 0ull;
 #pragma unroll 4
                 for (int32_t i = grp; i < deg; i += G) {
                     const int32_t s = col[lo + i];
-                    const int32_t ws = (s + 1) >> 6;
-                    if (w >= ws && w < NW) acc |= slot[int64_t(s) * NW + w];
-                    if (w == (s >> 6)) acc |= 1ull << (s & 63);
+                    if (w >= (s >> 6) && w < NW) acc |= slot[int64_t(s) * NW + w];
                 }
                 for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
                 if (grp == 0 && w < NW) {
@@ -93,7 +94,7 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
                     count += __popcll(acc);
                 }
             }
-            count = __reduce_add_sync(FULL, count);
+            count = __reduce_add_sync(FULL, count) - 1;  // the task's own bit
             __threadfence_block();
             __syncwarp();
             if (lane == 0) {
