@@ -26,13 +26,6 @@ namespace insp {
 
 constexpr int SIM_WARPS = 8;  // most warps per CTA (the autotuner may launch fewer)
 constexpr int NL_C = 128;     // released-task buffer per warp in shared memory
-// Per-worker lists of pool indices (shared memory), so that a pop scans only its worker's
-// entries: 32 workers x 64 entries, or 64 x 32 with more than 32 workers.  A longer queue
-// switches the DAG to scanning the whole pool.
-template <bool TWO> struct WList {
-    static constexpr int ROWS = TWO ? 64 : 32, CAP = TWO ? 32 : 64;
-    int32_t idx[ROWS][CAP];
-};
 constexpr int NODE_NONE = 0xff;
 
 enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
@@ -60,14 +53,6 @@ struct Pool {
     int64_t *g_dr, *g_cost;
     __device__ __forceinline__ int32_t idw(int i) const { return i < POOL_C ? sm->idw[i] : g_idw[i - POOL_C]; }
     __device__ __forceinline__ int32_t seq(int i) const { return i < POOL_C ? sm->seq[i] : g_seq[i - POOL_C]; }
-    // the seq field packs the push sequence number (< 2^24) and, in its top byte, the
-    // entry's position in its worker's list
-    __device__ __forceinline__ int32_t sq(int i) const { return seq(i) & 0xffffff; }
-    __device__ __forceinline__ int32_t pos(int i) const { return int32_t(uint32_t(seq(i)) >> 24); }
-    __device__ __forceinline__ void set_pos(int i, int32_t p) const {
-        const int32_t v = (seq(i) & 0xffffff) | (p << 24);
-        if (i < POOL_C) sm->seq[i] = v; else g_seq[i - POOL_C] = v;
-    }
     __device__ __forceinline__ int32_t ia(int i) const { return i < POOL_C ? sm->ia[i] : g_ia[i - POOL_C]; }
     __device__ __forceinline__ int32_t ie(int i) const { return i < POOL_C ? sm->ie[i] : g_ie[i - POOL_C]; }
     __device__ __forceinline__ int64_t dr(int i) const { return i < POOL_C ? sm->dr[i] : g_dr[i - POOL_C]; }
@@ -180,9 +165,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     WarpSmem<POOL_C> *sm = reinterpret_cast<WarpSmem<POOL_C> *>(dyn) + wib;
-    unsigned char *dyn_w = dyn + (size_t(blockDim.x >> 5) * sizeof(WarpSmem<POOL_C>) + 15) / 16 * 16;
-    WList<TWO> *wlist = reinterpret_cast<WList<TWO> *>(dyn_w) + wib;
-    unsigned char *dyn_l = dyn_w + size_t(blockDim.x >> 5) * sizeof(WList<TWO>);
+    unsigned char *dyn_l = dyn + (size_t(blockDim.x >> 5) * sizeof(WarpSmem<POOL_C>) + 15) / 16 * 16;
     ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn_l);
     LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn_l + sizeof(ScorerPacked)) + wib;
     if (LEARNED) {
@@ -261,7 +244,6 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         int32_t run0 = -1, run1 = -1, qn0 = 0, qn1 = 0;
         // successor-row bounds of the running task, loaded when it starts (used at its completion)
         int32_t rlo0 = 0, rhi0 = 0, rlo1 = 0, rhi1 = 0;
-        bool ovf = false;  // this lane's worker list overflowed (sticky for the DAG)
         int32_t nready = 0, seq = 0, done = 0, npop = 0;
         int64_t now = 0;
         Ctrl ctl{0, 0, 0, 0, MODE_FIFO, ST_INC};
@@ -301,12 +283,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (lane == (ws & 31)) {
                 const bool hi = ws >= 32;
                 const int64_t c = ws < n_cpu ? cc : cg;
-                const int32_t k = (TWO && hi) ? qn1 : qn0;  // position in the worker's list
-                if (k < WList<TWO>::CAP) wlist->idx[ws][k] = nready;
-                else ovf = true;
                 if (TWO && hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
-                pool.set(nready, t | (ws << 24), seq | ((k < WList<TWO>::CAP ? k : 0) << 24), tia, tie,
-                         hi ? dr1 : dr0, c);
+                pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
                 if (A.tr_push_time) {
                     const int64_t r = tb + seq;
                     A.tr_push_time[r] = now;
@@ -324,7 +302,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         auto features_of = [&](int32_t i, int32_t w, int64_t cur, int32_t qlen, int32_t *f) {
             const int32_t t = pool.idw(i) & 0xffffff;
             cand_features(f, pool.ia(i), pool.ie(i), cost_of(t, 0), cost_of(t, 1), w >= n_cpu, pool.dr(i), now, cur,
-                          qlen, ctl.mode, ctl.state, ctl.peak, rp[t + 1] - rp[t], int64_t(seq) - pool.sq(i));
+                          qlen, ctl.mode, ctl.state, ctl.peak, rp[t + 1] - rp[t], int64_t(seq) - pool.seq(i));
         };
 
         // pop(w): controller judgement, then the pick (forced / learned / mode key).
@@ -344,7 +322,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                     int32_t ms = 0x7fffffff, mi = -1;
                     for (int32_t i = lane; i < nready; i += 32) {
                         if ((pool.idw(i) >> 24) != w) continue;
-                        const int32_t sq = pool.sq(i);
+                        const int32_t sq = pool.seq(i);
                         if (sq > last && sq < ms) { ms = sq; mi = i; }
                     }
                     const int32_t wm = int32_t(__reduce_min_sync(FULL, uint32_t(ms)));
@@ -413,28 +391,29 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                         }
                         __syncwarp();
                     }
-                } else {
-                    // the worker's own entries through its list, or every pool entry after an
-                    // overflow; keys as below, the best per lane first
-                    const bool lists = !__any_sync(FULL, ovf);
-                    const int32_t cnt = lists ? qlen : nready;
-                    uint32_t lo_best = 0;  // MODE_PRIO: the id key of the lane's best
-                    for (int32_t k = lane; k < cnt; k += 32) {
-                        const int32_t i = lists ? wlist->idx[w][k] : k;
+                } else if (mode == MODE_PRIO) {
+                    // highest bottom level (54 bits), then lowest id: the lane's best by both, then
+                    // a warp max of the level and, among the lanes holding it, of the id key
+                    uint32_t lo_best = 0;
+                    for (int32_t i = lane; i < nready; i += 32) {
                         const int32_t e = pool.idw(i);
-                        if (!lists && (e >> 24) != w) continue;
+                        if ((e >> 24) != w) continue;
+                        const uint64_t lvl = (1ull << 63) | (uint64_t(uint32_t(pool.ia(i))) << 31) |
+                                             uint64_t(uint32_t(pool.ie(i)));
+                        const uint32_t lo = 0x7fffffffu - uint32_t(e & 0xffffff);
+                        if (lvl > best || (lvl == best && lo > lo_best)) { best = lvl; lo_best = lo; bi = i; }
+                    }
+                    const uint64_t top = warp_max_u64(best);
+                    const uint32_t lo_top = __reduce_max_sync(FULL, best == top ? lo_best : 0u);
+                    if (best != top || lo_best != lo_top) { best = 0; bi = -1; }
+                } else {
+                    for (int32_t i = lane; i < nready; i += 32) {
+                        const int32_t e = pool.idw(i);
+                        if ((e >> 24) != w) continue;
                         const uint32_t id = uint32_t(e & 0xffffff);
-                        if (mode == MODE_PRIO) {
-                            // highest bottom level (54 bits), then lowest id
-                            const uint64_t lvl = (1ull << 63) | (uint64_t(uint32_t(pool.ia(i))) << 31) |
-                                                 uint64_t(uint32_t(pool.ie(i)));
-                            const uint32_t lo = 0x7fffffffu - id;
-                            if (lvl > best || (lvl == best && lo > lo_best)) { best = lvl; lo_best = lo; bi = i; }
-                            continue;
-                        }
                         uint64_t key;
                         if (mode == MODE_FIFO) {
-                            key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.sq(i)));
+                            key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.seq(i)));
                         } else {
                             const uint64_t tie_lo = uint64_t(0x7fffffffu - id);
                             uint64_t hi_part;
@@ -444,12 +423,6 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                             key = (1ull << 63) | hi_part | tie_lo;
                         }
                         if (key > best) { best = key; bi = i; }
-                    }
-                    if (mode == MODE_PRIO) {
-                        // a warp max of the level and, among the lanes holding it, of the id key
-                        const uint64_t top = warp_max_u64(best);
-                        const uint32_t lo_top = __reduce_max_sync(FULL, best == top ? lo_best : 0u);
-                        if (best != top || lo_best != lo_top) { best = 0; bi = -1; }
                     }
                 }
             }
@@ -463,22 +436,10 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             npop += 1;
             // the rest by the lane that owns worker w: read the entry, fill its slot with the
             // last entry, start the task, write its schedule
-            const bool lists = !__any_sync(FULL, ovf);
             if (lane == (w & 31)) {
                 const int32_t t = pool.idw(idx) & 0xffffff;
                 const int64_t dr = pool.dr(idx), c = pool.cost(idx);
-                if (lists) {  // the worker's last list entry fills the popped one's position
-                    const int32_t k = pool.pos(idx), kl = ((TWO && w >= 32) ? qn1 : qn0) - 1;
-                    if (k != kl) {
-                        const int32_t mv = wlist->idx[w][kl];
-                        wlist->idx[w][k] = mv;
-                        pool.set_pos(mv, k);
-                    }
-                }
-                if (idx != last) {  // the pool's last entry fills the popped slot
-                    pool.move(last, idx, lane, true);
-                    if (lists) wlist->idx[pool.idw(idx) >> 24][pool.pos(idx)] = idx;
-                }
+                if (idx != last) pool.move(last, idx, lane, true);
                 const int64_t s = max(now, dr), e = s + c;
                 if (TWO && w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; }
                 else { qc0 -= c; qn0 -= 1; run0 = t; busy0 = e; rlo0 = rp[t]; rhi0 = rp[t + 1]; }
@@ -609,17 +570,17 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
 }
 
 // dynamic shared memory of a launch with `warps` warps per CTA
-template <bool L, int Q, bool TWO>
+template <bool L, int Q>
 static size_t sim_dyn_bytes(int warps) {
-    return (size_t(warps) * sizeof(WarpSmem<Q>) + 15) / 16 * 16 + size_t(warps) * sizeof(WList<TWO>) +
+    return (size_t(warps) * sizeof(WarpSmem<Q>) + 15) / 16 * 16 +
            (L ? sizeof(ScorerPacked) + warps * sizeof(LearnSmem) : 0);
 }
 
 template <bool L, int Q, bool TWO>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
     cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sim_dyn_bytes<L, Q, TWO>(SIM_WARPS)));
-    k_sim<L, Q, TWO><<<grid, threads, sim_dyn_bytes<L, Q, TWO>(threads / 32), s>>>(A);
+                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
+    k_sim<L, Q, TWO><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
 }
 
 template <bool L, bool TWO>
@@ -653,9 +614,9 @@ template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
     cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sim_dyn_bytes<L, Q, TWO>(SIM_WARPS)));
+                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO>, threads,
-                                                      sim_dyn_bytes<L, Q, TWO>(threads / 32)) != cudaSuccess) {
+                                                      sim_dyn_bytes<L, Q>(threads / 32)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
