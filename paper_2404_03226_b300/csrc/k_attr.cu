@@ -20,7 +20,7 @@
 namespace insp {
 
 // --------------------------------------------------------- inspiring ability
-constexpr int IA_MAX_WARPS = 32;  // warps per CTA: blockDim / 32, up to 32 (per size bin, autotuned)
+constexpr int IA_MAX_WARPS = 32;  // warps per CTA: blockDim / 32, up to 32 (autotuned)
 
 // Descendant rows are bitsets of 64-bit words (half the word operations of 32-bit ones).
 __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int32_t *order, int32_t n_order,
