@@ -156,8 +156,9 @@ struct LearnSmem {
 };
 
 // TWO: more than 32 workers, so every lane owns a second worker (lane + 32); with 32 or
-// fewer that slot and all its code drop out at compile time.
-template <bool LEARNED, int POOL_C, bool TWO>
+// fewer that slot and all its code drop out at compile time.  EX: rollout controls or the
+// push/pop trace are in use; without them their checks drop out too.
+template <bool LEARNED, int POOL_C, bool TWO, bool EX>
 __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     // dynamic shared memory: every warp's pool and buffers, then the learned scorer's
     // weights and per-warp tiles (sized by the warps actually launched)
@@ -285,7 +286,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 const int64_t c = ws < n_cpu ? cc : cg;
                 if (TWO && hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
                 pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
-                if (A.tr_push_time) {
+                if (EX && A.tr_push_time) {
                     const int64_t r = tb + seq;
                     A.tr_push_time[r] = now;
                     A.tr_push_task[r] = t;
@@ -316,7 +317,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             }
             const int32_t qlen = __shfl_sync(FULL, (TWO && w >= 32) ? qn1 : qn0, w & 31);
             // rollouts: candidate features in push order
-            if (A.feat_pop != nullptr && npop == A.feat_pop[d]) {
+            if (EX && A.feat_pop != nullptr && npop == A.feat_pop[d]) {
                 int32_t last = -1, nd = 0;
                 for (int k = 0; k < A.feat_cap; ++k) {
                     int32_t ms = 0x7fffffff, mi = -1;
@@ -344,7 +345,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             }
             uint64_t best = 0;
             int32_t bi = -1;
-            const bool forcing = A.force_pop != nullptr && npop == A.force_pop[d];
+            const bool forcing = EX && A.force_pop != nullptr && npop == A.force_pop[d];
             if (forcing) {
                 const int32_t ft = A.force_task[d];
                 for (int32_t i = lane; i < nready; i += 32) {
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                     if ((e >> 24) == w && (e & 0xffffff) == ft) { best = 1; bi = i; }
                 }
             }
-            if (__ballot_sync(FULL, bi >= 0) == 0) {
+            if (!EX || __ballot_sync(FULL, bi >= 0) == 0) {
                 if (LEARNED) {
                     // score w's candidates 32 at a time on the tensor cores
                     for (int32_t base = 0; base < nready; base += 32) {
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 A.worker[tb + t] = w;
                 A.start[tb + t] = s;
                 A.end[tb + t] = e;
-                if (A.tr_pop_time) {
+                if (EX && A.tr_pop_time) {
                     const int64_t r = tb + npop - 1;
                     A.tr_pop_time[r] = now;
                     A.tr_pop_task[r] = t;
@@ -576,31 +577,38 @@ static size_t sim_dyn_bytes(int warps) {
            (L ? sizeof(ScorerPacked) + warps * sizeof(LearnSmem) : 0);
 }
 
-template <bool L, int Q, bool TWO>
+template <bool L, int Q, bool TWO, bool EX>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
-    cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
-    k_sim<L, Q, TWO><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
+    k_sim<L, Q, TWO, EX><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
 }
 
-template <bool L, bool TWO>
+template <bool L, bool TWO, bool EX>
 static void launch_l(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
-    if (queue <= 32) launch_q<L, 32, TWO>(A, grid, threads, s);
-    else if (queue <= 64) launch_q<L, 64, TWO>(A, grid, threads, s);
-    else if (queue <= 128) launch_q<L, 128, TWO>(A, grid, threads, s);
-    else if (queue <= 256) launch_q<L, 256, TWO>(A, grid, threads, s);
-    else launch_q<L, 512, TWO>(A, grid, threads, s);
+    if (queue <= 32) launch_q<L, 32, TWO, EX>(A, grid, threads, s);
+    else if (queue <= 64) launch_q<L, 64, TWO, EX>(A, grid, threads, s);
+    else if (queue <= 128) launch_q<L, 128, TWO, EX>(A, grid, threads, s);
+    else if (queue <= 256) launch_q<L, 256, TWO, EX>(A, grid, threads, s);
+    else launch_q<L, 512, TWO, EX>(A, grid, threads, s);
+}
+
+template <bool EX>
+static void launch_ex(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
+    const bool two = A.n_cpu + A.n_gpu > 32;
+    if (A.policy == INSP_POLICY_LEARNED) {
+        if (two) launch_l<true, true, EX>(A, grid, threads, queue, s);
+        else launch_l<true, false, EX>(A, grid, threads, queue, s);
+    } else {
+        if (two) launch_l<false, true, EX>(A, grid, threads, queue, s);
+        else launch_l<false, false, EX>(A, grid, threads, queue, s);
+    }
 }
 
 static void launch_any(const SimArgs &A, int grid, int threads, int queue, cudaStream_t s) {
-    const bool two = A.n_cpu + A.n_gpu > 32;
-    if (A.policy == INSP_POLICY_LEARNED) {
-        if (two) launch_l<true, true>(A, grid, threads, queue, s);
-        else launch_l<true, false>(A, grid, threads, queue, s);
-    } else {
-        if (two) launch_l<false, true>(A, grid, threads, queue, s);
-        else launch_l<false, false>(A, grid, threads, queue, s);
-    }
+    const bool ex = A.feat_pop || A.force_pop || A.tr_push_time || A.tr_pop_time;
+    if (ex) launch_ex<true>(A, grid, threads, queue, s);
+    else launch_ex<false>(A, grid, threads, queue, s);
 }
 
 void launch_sim(const SimArgs &A, int grid, int warps, int queue, cudaStream_t s) {
@@ -613,9 +621,9 @@ int sim_max_warps() { return SIM_WARPS; }
 template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
-    cudaFuncSetAttribute(k_sim<L, Q, TWO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO>, threads,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO, false>, threads,
                                                       sim_dyn_bytes<L, Q>(threads / 32)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
