@@ -408,22 +408,28 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                     const uint32_t lo_top = __reduce_max_sync(FULL, best == top ? lo_best : 0u);
                     if (best != top || lo_best != lo_top) { best = 0; bi = -1; }
                 } else {
-                    for (int32_t i = lane; i < nready; i += 32) {
-                        const int32_t e = pool.idw(i);
-                        if ((e >> 24) != w) continue;
-                        const uint32_t id = uint32_t(e & 0xffffff);
-                        uint64_t key;
-                        if (mode == MODE_FIFO) {
-                            key = (1ull << 63) | uint64_t(0xffffffffu - uint32_t(pool.seq(i)));
-                        } else {
-                            const uint64_t tie_lo = uint64_t(0x7fffffffu - id);
-                            uint64_t hi_part;
-                            if (mode == MODE_ABILITY) hi_part = uint64_t(uint32_t(pool.ia(i))) << 31;
-                            else if (mode == MODE_EFI) hi_part = uint64_t(uint32_t(pool.ie(i))) << 31;
-                            else hi_part = (uint64_t(pool.dr(i) <= now) << 62) | (uint64_t(uint32_t(pool.ie(i))) << 31);
-                            key = (1ull << 63) | hi_part | tie_lo;
+                    // one loop per pick mode (the mode is fixed for the pop): the entries of
+                    // worker w, keyed by the mode's priority, ties to the lowest id (FIFO: the
+                    // oldest push)
+                    auto scan = [&](auto key_of) {
+                        for (int32_t i = lane; i < nready; i += 32) {
+                            const int32_t e = pool.idw(i);
+                            if ((e >> 24) != w) continue;
+                            const uint64_t key = key_of(i, uint64_t(0x7fffffffu - uint32_t(e & 0xffffff)));
+                            if (key > best) { best = key; bi = i; }
                         }
-                        if (key > best) { best = key; bi = i; }
+                    };
+                    constexpr uint64_t TOP = 1ull << 63;
+                    if (mode == MODE_FIFO) {
+                        scan([&](int32_t i, uint64_t) { return TOP | uint64_t(0xffffffffu - uint32_t(pool.seq(i))); });
+                    } else if (mode == MODE_ABILITY) {
+                        scan([&](int32_t i, uint64_t lo) { return TOP | (uint64_t(uint32_t(pool.ia(i))) << 31) | lo; });
+                    } else if (mode == MODE_EFI) {
+                        scan([&](int32_t i, uint64_t lo) { return TOP | (uint64_t(uint32_t(pool.ie(i))) << 31) | lo; });
+                    } else {
+                        scan([&](int32_t i, uint64_t lo) {
+                            return TOP | (uint64_t(pool.dr(i) <= now) << 62) | (uint64_t(uint32_t(pool.ie(i))) << 31) | lo;
+                        });
                     }
                 }
             }
