@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -73,12 +74,22 @@ struct DeviceInfo {
     int occ_ie = 0;  // the global-memory efficiency sweep
 };
 
+// SM count and occupancy of the current device, queried once per device.
 int device_info(DeviceInfo &di) {
+    constexpr int MAX_DEV = 64;
+    static DeviceInfo cache[MAX_DEV];
+    static std::mutex mu;
     int dev = 0;
     CU(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < MAX_DEV && cache[dev].sms > 0) {
+        di = cache[dev];
+        return INSP_OK;
+    }
     CU(cudaDeviceGetAttribute(&di.sms, cudaDevAttrMultiProcessorCount, dev));
     di.occ_ie = insp::ie_occupancy();
     if (di.occ_ie < 1) return fail(INSP_ECUDA, "occupancy query failed");
+    if (dev >= 0 && dev < MAX_DEV) cache[dev] = di;
     return INSP_OK;
 }
 
@@ -87,8 +98,9 @@ const insp_tuning kDefaultTuning = {1, 1, 16, 16, 512, 4, 64, 0};
 
 bool tuning_ok(const insp_tuning &t) {
     return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
-           t.ia_warps >= 1 && t.ia_warps <= 32 && t.ie_warps >= 1 && t.ie_warps <= 16 && t.ie_ring_mb >= 1 &&
-           t.ie_ring_mb <= 65536 && t.sim_warps >= 1 && t.sim_warps <= 8 &&
+           t.ia_warps >= 1 && t.ia_warps <= insp::ia_max_warps() && t.ie_warps >= 1 &&
+           t.ie_warps <= insp::ie_pull_max_warps() && t.ie_ring_mb >= 1 && t.ie_ring_mb <= 65536 &&
+           t.sim_warps >= 1 && t.sim_warps <= insp::sim_max_warps() &&
            (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128 || t.sim_queue == 256 ||
             t.sim_queue == 512) &&
            (t.group_split == 0 || t.group_split == 1);
