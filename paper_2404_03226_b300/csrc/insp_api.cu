@@ -164,7 +164,7 @@ struct Scratch {
 // loading batch after batch reuses the allocations instead of paying cudaMalloc / cudaFree.
 struct BatchBufs {
     DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
-    DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters;
+    DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters, dag_span;
     DBuf pr_ptr, pcol, cursor;
     DBuf item_dag, item_dag_lpt, item_base_lpt;
 };
@@ -195,7 +195,7 @@ struct insp_batch {
          &col_idx = bufs->col_idx, &type = bufs->type, &type_cost = bufs->type_cost, &task_cost = bufs->task_cost;
     DBuf &indeg0 = bufs->indeg0, &unit_time_def = bufs->unit_time_def, &unit_time_user = bufs->unit_time_user,
          &order = bufs->order, &item_base = bufs->item_base, &status = bufs->status, &max_span = bufs->max_span,
-         &counters = bufs->counters;
+         &counters = bufs->counters, &dag_span = bufs->dag_span;  // longest edge span per DAG
     DBuf &pr_ptr = bufs->pr_ptr, &pcol = bufs->pcol;  // predecessor lists (pull form of the efficiency sweep)
     bool pull = false;      // predecessor lists built: the pull sweep is used (window ring W <= IE_PULL_MAX_W)
     int grid_ie_pull = 0;   // its grid for the current tuning
@@ -587,7 +587,8 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     }
     if ((rc = b->indeg0.alloc(std::max<int64_t>(b->n_total, 1) * 4)) ||
         (rc = b->unit_time_def.alloc(std::max(ndag, 1) * 8)) || (rc = b->unit_time_user.alloc(std::max(ndag, 1) * 8)) ||
-        (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(512)))
+        (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(512)) ||
+        (rc = b->dag_span.alloc(std::max(ndag, 1) * 4)))
         return bail(rc);
     if (cudaMemset(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4) != cudaSuccess ||
         cudaMemset(b->max_span.p, 0, 4) != cudaSuccess)
@@ -598,7 +599,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     const int grid = std::max(1, std::min(ndag, di.sms * 8));
     if (ndag > 0) {
         insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
-                              b->max_span.as<int32_t>(), grid, 0);
+                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, 0);
         insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, 0);
     }
     if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
@@ -760,7 +761,7 @@ int launch_attr(insp_batch *b, int r0, int r1, int32_t *ctr, const int64_t *ut, 
             const int wpc = b->tun.ie_warps;
             const int grid = int(std::max<int64_t>(1, std::min<int64_t>(b->grid_ie_pull, (i1 - i0 + wpc - 1) / wpc)));
             insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base_lpt.as<int64_t>(),
-                                 b->item_dag_lpt.as<int32_t>(), i0, i1, ctr + 1, ut, b->W, S.ie_ring.as<int32_t>(),
+                                 b->item_dag_lpt.as<int32_t>(), i0, i1, ctr + 1, ut, b->dag_span.as<int32_t>(), b->W, S.ie_ring.as<int32_t>(),
                                  d_ie, grid, wpc, s_ie);
         } else {
             if (r0 != 0 || r1 != b->ndag) return fail(INSP_EINVAL, "internal: global efficiency sweep over a part");
@@ -1045,8 +1046,8 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
         if (b->pull && !wide) {
             const int wpc = b->tun.ie_warps;
             insp::launch_ie_pull(B, b->pr_ptr.as<int32_t>(), b->pcol.as<int32_t>(), b->item_base_lpt.as<int64_t>(),
-                                 b->item_dag_lpt.as<int32_t>(), 0, b->n_items_pull, ck + 0, ut.as<int64_t>(), b->W,
-                                 S.ie_ring.as<int32_t>(), ie.as<int32_t>(), b->grid_ie_pull, wpc, s);
+                                 b->item_dag_lpt.as<int32_t>(), 0, b->n_items_pull, ck + 0, ut.as<int64_t>(),
+                                 b->dag_span.as<int32_t>(), b->W, S.ie_ring.as<int32_t>(), ie.as<int32_t>(), b->grid_ie_pull, wpc, s);
         } else {
             if (!b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
             insp::launch_ie(B, b->item_base.as<int64_t>(), b->n_items, ck + 0, ut.as<int64_t>(), S.ie_rec.as<uint4>(),

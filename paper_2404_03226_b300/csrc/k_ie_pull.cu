@@ -62,11 +62,10 @@ constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) 
 __global__ void __maxnreg__(IE_PULL_MAXREG)
     k_ie_pull(DevBatch B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
               const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
-              const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie_out) {
+              const int64_t *unit_time, const int32_t *dag_span, int32_t W, int32_t *gring, int32_t *ie_out) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    const int32_t wmask = W - 1;
     unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
     Codes *__restrict__ val = reinterpret_cast<Codes *>(gring) +
                               (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / sizeof(Codes));
@@ -91,6 +90,9 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
         const int32_t *pp = pr_ptr + tb + d;
         const int32_t *pc = pcol + eb;
         const int64_t T = unit_time[d];
+        // this DAG's own window: a power of two above its longest edge span (at most W), so a DAG
+        // with short edges touches only the first rows of the ring
+        const int32_t wmask = (1 << (32 - __clz(dag_span[d]))) - 1;
 
         int32_t cnt[NV];  // per source v0 + lane + 32 q
 #pragma unroll
@@ -265,11 +267,11 @@ int ie_pull_occupancy(int warps) {
 
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
-                    const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie, int grid, int warps,
-                    cudaStream_t s) {
+                    const int64_t *unit_time, const int32_t *dag_span, int32_t W, int32_t *gring, int32_t *ie,
+                    int grid, int warps, cudaStream_t s) {
     cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
     k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
-                                                                           item_lo, item_hi, counter, unit_time, W,
+                                                                           item_lo, item_hi, counter, unit_time, dag_span, W,
                                                                            gring, ie);
 }
 

@@ -1,6 +1,6 @@
 // DAG ingest: validation of the CSR and cost tables, in-degrees, the largest
-// edge span (window size of the inspiring-efficiency sweep) and each DAG's
-// default unit time (4 x the lower median of its GPU costs).
+// edge span per DAG and over the batch (window sizes of the inspiring-efficiency
+// sweep) and each DAG's default unit time (4 x the lower median of its GPU costs).
 #include "common.cuh"
 #include "kernels.h"
 
@@ -9,7 +9,7 @@ namespace insp {
 // One CTA per DAG (grid-stride over DAGs).  Error precedence matches the
 // header: INSP_EINVAL, then INSP_ENOTTOPO, then INSP_EOVERFLOW.
 __global__ void __launch_bounds__(256) k_validate(DevBatch B, int64_t xfer, int32_t *status, int32_t *indeg0,
-                                                  int32_t *max_span) {
+                                                  int32_t *max_span, int32_t *dag_span) {
     __shared__ uint32_t s_flags;
     __shared__ unsigned long long s_sum;
     __shared__ int32_t s_span;
@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(256) k_validate(DevBatch B, int64_t xfer, int3
         if (threadIdx.x == 0) {
             status[d] = st;
             atomicMax(max_span, s_span);
+            if (dag_span) dag_span[d] = s_span;
         }
         // in-degrees (only meaningful for valid DAGs)
         if (st == INSP_OK) {
@@ -117,8 +118,9 @@ __global__ void __launch_bounds__(256) k_unit_time(DevBatch B, const int32_t *st
 }
 
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
+                     int32_t *dag_span,
                      int grid, cudaStream_t s) {
-    k_validate<<<grid, 256, 0, s>>>(B, xfer, status, indeg0, max_span);
+    k_validate<<<grid, 256, 0, s>>>(B, xfer, status, indeg0, max_span, dag_span);
 }
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s) {
     k_unit_time<<<grid, 256, 0, s>>>(B, status, unit_time);

@@ -48,6 +48,7 @@ struct SimArgs {
 };
 
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
+                     int32_t *dag_span,
                      int grid, cudaStream_t s);
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s);
 // Device-side step counters of the attribute kernels: the done-flag epoch of
@@ -80,8 +81,8 @@ int ie_pull_occupancy(int warps);
 // gring: per-warp rings of ie_pull_ring_bytes(W) in global memory
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
-                    const int64_t *unit_time, int32_t W, int32_t *gring, int32_t *ie, int grid, int warps,
-                    cudaStream_t s);
+                    const int64_t *unit_time, const int32_t *dag_span, int32_t W, int32_t *gring, int32_t *ie,
+                    int grid, int warps, cudaStream_t s);
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
                         int grid, cudaStream_t s);
 // learned scorer (k_mlp.cu)
