@@ -122,7 +122,13 @@ int insp_dag_load_csr(insp_machine *m, int32_t n, const int32_t *row_ptr, const 
  *   at task_base[d] + d; col_idx[edge_base[ndag]] local successor ids;
  *   type[task_base[ndag]]; type_cost[ndag][n_types][2] (one table per DAG) or
  *   NULL when task_cost[task_base[ndag]][2] is given.
- * The first invalid DAG's error is returned.  Synchronous. */
+ * The first invalid DAG's error is returned.  Synchronous.
+ * Device memory: the inputs, predecessor lists (another m int32) and the
+ * kernels' scratch; the exact ability sweep holds n_max x ceil(n_max / 64)
+ * 64-bit words per concurrent DAG (n_max the largest DAG).  Its concurrency
+ * shrinks to keep that under 24 GB, down to one DAG at a time (a single bitset
+ * passes 24 GB beyond about 450,000 tasks); past the device's free memory the
+ * load fails with INSP_ENOMEM. */
 int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *task_base, const int64_t *edge_base,
                         const int32_t *row_ptr, const int32_t *col_idx, const uint8_t *type, int32_t n_types,
                         const int64_t *type_cost, const int64_t *task_cost, insp_batch **out);
