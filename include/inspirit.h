@@ -50,6 +50,7 @@ extern "C" {
 #define INSP_ECUDA 4     /* a CUDA runtime call failed (message in insp_last_error) */
 #define INSP_ETIMEOUT 5  /* a bounded device-side wait gave up (no GPU hang; the DAG's outputs are invalid) */
 #define INSP_EOVERFLOW 6 /* sum over tasks of (max cost + transfer) exceeds 2^54 ns, so times could overflow */
+#define INSP_ECHECK 7    /* debug builds only (INSP_CHECK): an internal bounds check failed; outputs invalid */
 
 /* ---------------------------------------------------------------- policy */
 #define INSP_POLICY_INSPIRIT 0 /* adaptive priority by the Nready controller (default) */

@@ -1,4 +1,9 @@
-"""Compile the CUDA kernels and the C ABI into libinspirit.so (sm_103a)."""
+"""Compile the CUDA kernels and the C ABI into libinspirit.so (sm_103a).
+
+With INSP_CHECK=1 in the environment the debug variant libinspirit_check.so is
+built (and loaded by the binding) instead: internal bounds checks record
+INSP_ECHECK in the DAG's status word rather than touching memory out of range.
+"""
 from __future__ import annotations
 
 import glob
@@ -8,7 +13,8 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SO = os.path.join(HERE, "libinspirit.so")
+CHECK = os.environ.get("INSP_CHECK", "") not in ("", "0")
+SO = os.path.join(HERE, "libinspirit_check.so" if CHECK else "libinspirit.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -34,7 +40,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
     tmp = SO + f".tmp{os.getpid()}"
     cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
-           "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared", "-o", tmp, *sources()] + (extra or [])
+           "-Xcompiler", "-fPIC,-fvisibility=hidden", "-shared", "-o", tmp, *sources()] + (extra or []) + \
+        (["-DINSP_CHECK"] if CHECK else [])
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd, cwd=HERE)

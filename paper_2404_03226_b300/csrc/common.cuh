@@ -60,6 +60,17 @@ __device__ __forceinline__ int64_t warp_min_i64(int64_t v) {
 __device__ __forceinline__ int ld_volatile(const int32_t *p) { return *(const volatile int32_t *)p; }
 __device__ __forceinline__ void st_volatile(int32_t *p, int v) { *(volatile int32_t *)p = v; }
 
+// Debug bounds checks (built with -DINSP_CHECK): a failed check records INSP_ECHECK in the
+// given status word and the guarded access is skipped.  Release builds compile them away.
+#ifdef INSP_CHECK
+__device__ __forceinline__ bool insp_check(bool ok, int32_t *status) {
+    if (!ok) atomicExch(status, INSP_ECHECK);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool insp_check(bool, int32_t *) { return true; }
+#endif
+
 // Bounded wait until *flag == value: gives up (returns false) after `limit` polls, or at
 // once when *abort is set (another waiter gave up), and then sets *abort.  Every
 // device-side wait of the library goes through here, so none can hang the GPU.

@@ -86,7 +86,9 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
 #pragma unroll 4
                 for (int32_t i = grp; i < deg; i += G) {
                     const int32_t s = col[lo + i];
-                    if (w >= (s >> 6) && w < NW) acc |= slot[int64_t(s) * NW + w];
+                    // successors come after v (topological ids, checked at load) and before n
+                    if (w >= (s >> 6) && w < NW && insp_check(s > v && s < n, status + d))
+                        acc |= slot[int64_t(s) * NW + w];
                 }
                 for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
                 if (grp == 0 && w < NW) {

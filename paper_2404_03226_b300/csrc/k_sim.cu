@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 const bool hi = ws >= 32;
                 const int64_t c = ws < n_cpu ? cc : cg;
                 if (TWO && hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
-                pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
+                if (insp_check(nready < n, A.status + d))  // the pool never holds more than n tasks
+                    pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
                 if (EX && A.tr_push_time) {
                     const int64_t r = tb + seq;
                     A.tr_push_time[r] = now;
@@ -527,7 +528,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                         const uint32_t rm = __ballot_sync(FULL, ready);
                         if (ready) {
                             const int32_t pos = nl + __popc(rm & ((1u << lane) - 1));
-                            if (pos < NL_C) sm->newly[pos] = s; else nl_g[pos - NL_C] = s;
+                            if (pos < NL_C) sm->newly[pos] = s;
+                            else if (insp_check(pos - NL_C < n, A.status + d)) nl_g[pos - NL_C] = s;
                         }
                         nl += __popc(rm);
                     }
