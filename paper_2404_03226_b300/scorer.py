@@ -20,6 +20,8 @@ from __future__ import annotations
 
 from dataclasses import dataclass
 
+import os
+
 import numpy as np
 
 from . import _lib
@@ -105,9 +107,15 @@ def init_weights(seed: int) -> np.ndarray:
 
 
 def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3, seed: int = 0,
-          w0: np.ndarray | None = None, log=None):
+          w0: np.ndarray | None = None, log=None, checkpoint: str | None = None):
     """Quantisation-aware training on the GPU; returns (fp32 master weights,
-    BF16 grid weights as uint16, per-epoch mean loss)."""
+    BF16 grid weights as uint16, per-epoch mean loss).
+
+    checkpoint: a .npz path written after every epoch (fp32 weights, AdamW
+    moments, step, epoch, seed, loss history); if it exists when training
+    starts, training resumes from it.  The gradient reduction is deterministic
+    and the epoch permutations are replayed from the seed, so a resumed run
+    ends with the same bits as an uninterrupted one."""
     import torch
     dev = torch.device("cuda")
     n = len(roll.target)
@@ -123,7 +131,18 @@ def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3,
     rng = np.random.default_rng(seed + 1)
     t = 0
     hist = []
-    for ep in range(epochs):
+    first = 0
+    if checkpoint and os.path.exists(checkpoint):
+        ck = np.load(checkpoint)
+        if int(ck["seed"]) != seed or int(ck["nweights"]) != NW:
+            raise ValueError(f"checkpoint {checkpoint} belongs to another run")
+        w.copy_(torch.from_numpy(ck["w"]))
+        m.copy_(torch.from_numpy(ck["m"]))
+        v.copy_(torch.from_numpy(ck["v"]))
+        t, first, hist = int(ck["step"]), int(ck["epoch"]), [float(x) for x in ck["hist"]]
+        for _ in range(first):  # the permutations of the epochs already done
+            rng.permutation(n)
+    for ep in range(first, epochs):
         perm = torch.from_numpy(rng.permutation(n)).to(dev)
         losses = []
         for s0 in range(0, n - bs + 1, bs):
@@ -138,6 +157,11 @@ def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3,
         hist.append(ep_loss)
         if log:
             log(f"epoch {ep}: loss {ep_loss:.4f}")
+        if checkpoint:
+            tmp = checkpoint + ".tmp.npz"
+            np.savez(tmp, w=w.cpu().numpy(), m=m.cpu().numpy(), v=v.cpu().numpy(), step=t, epoch=ep + 1, seed=seed,
+                     nweights=NW, hist=np.array(hist))
+            os.replace(tmp, checkpoint)
     q = torch.empty(NW, dtype=torch.int16, device=dev)
     _lib.insp_scorer_quantize(NW, w, q)
     torch.cuda.synchronize()
@@ -207,6 +231,7 @@ def main(argv=None) -> None:
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--out", default="")
+    ap.add_argument("--checkpoint", default="", help="training checkpoint (.npz), resumed from if present")
     a = ap.parse_args(argv)
     m = inputs.MACHINE_LAYERED
     t0 = time.time()
@@ -218,7 +243,8 @@ def main(argv=None) -> None:
     roll = Rollouts(np.concatenate([p.feat for p in parts]), np.concatenate([p.target for p in parts]),
                     np.concatenate([p.dag for p in parts]))
     t1 = time.time()
-    w, q, hist = train(roll, epochs=a.epochs, lr=a.lr, seed=a.seed, log=lambda s: print(s, file=sys.stderr))
+    w, q, hist = train(roll, epochs=a.epochs, lr=a.lr, seed=a.seed, log=lambda s: print(s, file=sys.stderr),
+                       checkpoint=a.checkpoint or None)
     t2 = time.time()
     val = evaluate(inputs.layered(a.val, cfg=4, first=1 << 19), m, q)       # seed set A, not trained on
     held = evaluate(inputs.layered(a.eval, cfg=4, first=1 << 20), m, q)     # seed set B

@@ -217,3 +217,18 @@ def test_shipped_scorer_on_held_out_dags():
         assert res["mean_makespan_learned"] <= res["mean_makespan_inspirit"]
     else:
         assert shipped.startswith("inspirit")
+
+
+def test_training_checkpoint_resume_is_exact(tmp_path):
+    """Training interrupted after 2 epochs and resumed from its checkpoint ends
+    with the same bits as 4 uninterrupted epochs."""
+    from paper_2404_03226_b300 import scorer
+    train = inputs.layered(96, cfg=4, first=7, n_max=400)
+    roll = scorer.collect_rollouts(train, inputs.MACHINE_LAYERED, seed=9)
+    w_full, q_full, h_full = scorer.train(roll, epochs=4, batch=512, seed=3)
+    ck = str(tmp_path / "ck.npz")
+    scorer.train(roll, epochs=2, batch=512, seed=3, checkpoint=ck)
+    w_res, q_res, h_res = scorer.train(roll, epochs=4, batch=512, seed=3, checkpoint=ck)
+    np.testing.assert_array_equal(w_res, w_full)
+    np.testing.assert_array_equal(q_res, q_full)
+    assert h_res == h_full
