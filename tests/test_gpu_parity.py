@@ -109,6 +109,17 @@ def test_full_layered_workload_sampled():
     g2 = gpu_run(b, m)
     np.testing.assert_array_equal(g["makespan"], g2["makespan"])
     np.testing.assert_array_equal(g["start"], g2["start"])
+    # the benchmark's configuration: autotuned shapes, the pipelined evaluation step
+    import torch
+    import paper_2404_03226_b300 as P
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.autotune()
+    ia, ie, s = B.evaluate()
+    torch.cuda.synchronize()
+    assert (B.status() == 0).all()
+    for name, got in (("ia", ia), ("ie", ie), ("worker", s.worker), ("start", s.start), ("end", s.end),
+                      ("makespan", s.makespan)):
+        np.testing.assert_array_equal(got.cpu().numpy(), g[name], err_msg=name)
 
 
 def test_load_errors():
