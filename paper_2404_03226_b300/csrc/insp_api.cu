@@ -1340,6 +1340,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
         float best_ms = 1e30f;
         for (const insp_tuning &c : cands) {
             int r = insp_batch_set_tuning(b, &c);
+            if (r == INSP_ENOMEM) continue;  // a candidate that does not fit is skipped
             if (r) return r;
             float ms = 0;
             if ((r = time_step(ms))) return r;
