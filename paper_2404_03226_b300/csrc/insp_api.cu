@@ -1275,7 +1275,16 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
     if (old.ia_warps != t->ia_warps) rc = alloc_ia(b);
     if (rc == INSP_OK && b->pull && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
         rc = alloc_pull_ring(b);
-    if (rc != INSP_OK) b->tun = old;
+    if (rc != INSP_OK) {
+        // back to the old shapes: reallocate what the failed attempt may have released (the
+        // old sizes fitted before); the batch stays usable with its previous tuning
+        const std::string err = g_err;
+        b->tun = old;
+        const int r2 = alloc_ia(b);
+        const int r3 = b->pull ? alloc_pull_ring(b) : INSP_OK;
+        if (r2 || r3) return fail(rc, err + "; restoring the previous tuning failed too");
+        g_err = err;
+    }
     if (b->graph) {  // a recorded step holds the old launch shapes
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
