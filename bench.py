@@ -132,20 +132,47 @@ def algorithmic_bytes(batch):
     }
 
 
-def traffic_from_profile(kernel: str, launches_per_step: float):
-    """dram bytes per launch from the per-step figure an ncu capture recorded in
-    profiles/, if the kernel source has not changed since."""
+def profile_record(kernel: str):
+    """The counters an ncu capture recorded in profiles/ for a kernel (per-step DRAM bytes and
+    warp instructions, scaled to the full workload), if the kernel source has not changed since."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    rec = d.get(kernel)
+    rec = json.load(open(p)).get(kernel)
     if not rec:
         return None
     src = os.path.join(ROOT, "paper_2404_03226_b300", "csrc", rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
         return None
+    return rec
+
+
+def traffic_from_profile(kernel: str, launches_per_step: float):
+    """dram bytes per launch from the per-step figure of the kernel's ncu record."""
+    rec = profile_record(kernel)
+    if rec is None:
+        return None
     return rec["bytes_per_step_full"] / max(launches_per_step, 1.0)
+
+
+def issue_roofline(names, kms, steps, sms: int, sm_mhz: float, dom: str):
+    """Second roofline: SM instruction issue.  achieved = warp instructions per step (ncu
+    smsp__inst_executed.sum of the recorded capture, scaled to the workload) over the kernel's
+    measured time; peak = SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
+    sampled during the timed region."""
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9  # G warp instructions / s
+    per = {}
+    for k, name in enumerate(names):
+        rec = profile_record(name)
+        if rec is None or "inst_per_step_full" not in rec or kms[k] <= 0:
+            per[name] = None
+            continue
+        ach = rec["inst_per_step_full"] * steps / (kms[k] / 1e3) / 1e9
+        per[name] = {"achieved": round(ach, 1), "frac": round(ach / peak, 4)}
+    d = per.get(dom)
+    return {"bound": "issue", "kernel": dom, "achieved": d["achieved"] if d else None, "peak": round(peak, 1),
+            "unit": "G warp-instructions/s", "frac": d["frac"] if d else None, "per_kernel": per,
+            "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (sampled)"}
 
 
 # ------------------------------------------------------------ multi-rank
@@ -167,25 +194,58 @@ def combine_ranks(tasks: float, elapsed_s: float, dist, device) -> tuple[float, 
 
 
 # --------------------------------------------------------------------- arms
-def cpu_baseline(batch, machine, budget_tasks=300000):
-    """The oracle, as it stands, on the first DAGs of the workload (one core)."""
-    import oracle
-    tasks = 0
-    idx = []
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def first_dags(batch, budget_tasks: int):
+    """The first DAGs of the workload holding about budget_tasks tasks."""
+    idx, tasks = [], 0
     for d in range(batch.ndag):
         idx.append(d)
         tasks += int(batch.task_base[d + 1] - batch.task_base[d])
         if tasks >= budget_tasks:
             break
+    return idx, tasks
+
+
+def run_oracle(dags, machine, threads: int) -> None:
+    """The oracle (attributes + simulation) over the DAGs, one DAG per call, on `threads` host
+    threads (its C calls release the interpreter lock)."""
+    import oracle
+    if threads <= 1:
+        for g in dags:
+            assert oracle.simulate(g, machine)["rc"] == 0
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(threads) as ex:
+        assert all(rc == 0 for rc in ex.map(lambda g: oracle.simulate(g, machine)["rc"], dags))
+
+
+def cpu_baseline(batch, machine, per_core_tasks=100000):
+    """The oracle, as it stands, on the first DAGs of the workload: once on one core, and on
+    every host core (DAGs spread over threads)."""
+    import oracle
+    oracle.simulate(batch.dag(0), machine)  # load the library before the threads start
+    idx1, t1 = first_dags(batch, per_core_tasks)
+    dags1 = [batch.dag(d) for d in idx1]
+    s0 = time.perf_counter()
+    run_oracle(dags1, machine, 1)
+    dt1 = time.perf_counter() - s0
+    cores = host_cores()
+    idx, tasks = first_dags(batch, per_core_tasks * cores)
     dags = [batch.dag(d) for d in idx]
-    t0 = time.perf_counter()
-    for g in dags:
-        r = oracle.simulate(g, machine)
-        assert r["rc"] == 0
-    dt = time.perf_counter() - t0
-    return {"value": tasks / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    s0 = time.perf_counter()
+    run_oracle(dags, machine, cores)
+    dt = time.perf_counter() - s0
+    return {"value": tasks / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks), attributes + simulation, "
-                      f"{dt:.1f} s single-threaded"}
+                      f"{dt:.1f} s on {cores} threads (one DAG per oracle call)",
+            "single_core": {"value": t1 / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"first {len(idx1)} DAGs ({t1} tasks), {dt1:.1f} s"}}
 
 
 def run_reference(args, rank):
@@ -196,25 +256,20 @@ def run_reference(args, rank):
         return
     batch = inputs.layered4096()
     machine = inputs.MACHINE_LAYERED
-    budget = 25000
-    idx, tasks = [], 0
-    for d in range(batch.ndag):
-        idx.append(d)
-        tasks += int(batch.task_base[d + 1] - batch.task_base[d])
-        if tasks >= budget:
-            break
+    oracle.simulate(batch.dag(0), machine)  # load the library before the threads start
+    cores = host_cores()
+    idx, tasks = first_dags(batch, 25000 * cores)  # about a second of oracle work per step
     dags = [batch.dag(d) for d in idx]
     times = []
     for s in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        for g in dags:
-            oracle.simulate(g, machine)
+        run_oracle(dags, machine, cores)
         if s >= args.warmup:
             times.append(time.perf_counter() - t0)
     step = float(np.mean(times))
     v = tasks / step
-    cb = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-          "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks) per step, single-threaded"}
+    cb = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks) per step, on {cores} threads"}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
                       "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
@@ -334,14 +389,17 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     torch.cuda.synchronize()
     clocks.mark_start()
+    ev_step = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev0.record(stream)
-    for _ in range(args.steps):
+    for k in range(args.steps):
         step()
+        ev_step[k].record(stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks.mark_end()
     barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
+    step_ms = [(ev0 if k == 0 else ev_step[k - 1]).elapsed_time(ev_step[k]) for k in range(args.steps)]
     _lib.insp_batch_set_timing(b.handle, False)
     kms, klaunch = _lib.insp_batch_timing(b.handle, reset=True)
     clk = clocks.stop()
@@ -372,6 +430,21 @@ def run_ours(args, rank, world, local_rank):
     graph = {"value": n * args.steps / g_elapsed, "unit": UNIT, "ms_per_step": g_elapsed / args.steps * 1e3,
              "launches_per_step": 1}
 
+    # ---- simulation alone (a3-a5), on the attributes the timed steps left resident
+    for _ in range(args.warmup):
+        _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record(stream)
+    for _ in range(args.steps):
+        _lib.insp_simulate_batch(b.handle, ia, ie, worker, start, end, mk, stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    if _lib.insp_batch_status(b.handle) != 0:
+        raise RuntimeError("device-side status not OK after the simulation-only steps: " + _lib.last_error())
+    s_elapsed = s0.elapsed_time(s1) / 1e3
+    sim_only = {"value": n * args.steps / s_elapsed, "unit": UNIT, "ms_per_step": s_elapsed / args.steps * 1e3}
+
     # ---- roofline of the dominant kernel
     names = ["k_ia", "k_ie_pull", "k_sim"]  # the layered and tiled workloads take the pull efficiency sweep
     alg = algorithmic_bytes(batch)
@@ -388,6 +461,8 @@ def run_ours(args, rank, world, local_rank):
                 "kernel_share": {k: round(v, 4) for k, v in share.items()},
                 "step_bytes": int(sum(alg.values())),
                 "step_frac": sum(alg.values()) / (t_max / args.steps) / 1e9 / peak}
+    roofline_issue = issue_roofline(names, kms, args.steps, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                    clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0, dom)
 
     # ---- per-DAG launch form on a sample (same kernels, one DAG per launch)
     per_dag = None
@@ -487,6 +562,10 @@ def run_ours(args, rank, world, local_rank):
             "cuda_graph": graph,
             "e2e": e2e,
             "roofline": roofline,
+            "roofline_issue": roofline_issue,
+            "step_ms": {"best": round(min(step_ms), 4), "median": round(float(np.median(step_ms)), 4),
+                        "mean": round(t_max / args.steps * 1e3, 4)},
+            "simulate_only": sim_only,
             "cpu_baseline": cb,
             "clocks": clk,
             # our kernels in the timed region: ability, efficiency, simulation, plus one

@@ -1,27 +1,33 @@
 // Inspiring efficiency (Sec. 4.2 / Sec. 4.3), "pull" form of the window sweep.
 //
-// A warp owns IE_PULL_SOURCES (64 or 128) consecutive sources (lane j <->
-// v0 + j + 32 q, several codes per lane) and visits every task
-// u = v0, v0+1, ... in id order (a topological order).  Each lane keeps, per
-// task, one value in a shared-memory ring of W slots (W a power of two above
-// every edge span, so every predecessor of u is still in the ring):
-//     -1         u is not in the source's cone,
+// A warp owns IE_PULL_SOURCES = 64 consecutive sources (lane j <-> v0 + j and
+// v0 + j + 32, two codes per lane) and visits every task u = v0, v0+1, ... in id
+// order (a topological order).  Each lane keeps, per task, its codes in a ring of
+// W rows (W a power of two above every edge span, so every predecessor of u is
+// still in the ring):
+//     "out"      u is not in the source's cone,
 //     L in 1..T  u is in the cone and every path from the source to u weighs L
 //                or less (L = the longest path weight, GPU costs, both ends),
 //     OVER       u is in the cone but some path weighs more than T.
-// These codes are ordered so that a plain max over predecessors combines them:
+// The codes are ordered out < 1..T < OVER, so a plain max over predecessors
+// combines them:
 //     val_j(u) = source ? (c(u) <= T ? c(u) : OVER)
 //              : m = max over predecessors q >= v0 of val_j(q);
-//                m < 0 ? -1 : (m == OVER ? OVER : (m + c(u) <= T ? m + c(u) : OVER))
+//                m = out ? out : (m == OVER ? OVER : (m + c(u) <= T ? m + c(u) : OVER))
 // and IE(v_j) counts the tasks whose value lands in 1..T (the source excluded).
+// With T < 2^16 - 1 a code is 16 bits (out = 0, OVER = 0xffff) and a lane's two
+// codes share one word, combined by a packed max; otherwise 32 bits (out = -1,
+// OVER = 2^31 - 1).  The choice is made per work item from its DAG's T.
 // The sweep stops after the last task that received an in-window value from a
 // predecessor (tracked through each in-window task's largest successor id).
 // Predecessor lists (built at ingest) and GPU costs of the next 32 tasks are
 // staged into shared memory with coalesced loads; predecessors older than the
-// sources (-1 for every source) are dropped while staging.  The ring is a per-warp
-// slice of global memory sized to stay in L2 (a shared-memory ring was measured
-// slower: at 33 KB per warp it caps residency at 6 warps per SM); each lane
-// only reads its own column, i.e. its own earlier writes.
+// sources (outside every source's cone) are dropped while staging.  The ring is a
+// per-warp slice of global memory meant to stay in L2 (a shared-memory ring was
+// measured slower: at 33 KB per warp it caps residency at 6 warps per SM); each
+// lane only reads its own column, i.e. its own earlier writes.
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -53,10 +59,183 @@ __device__ __forceinline__ int32_t cget(const int4 &a, int q) { return q == 0 ? 
 __device__ __forceinline__ int2 cmake(const int32_t (&v)[2]) { return make_int2(v[0], v[1]); }
 __device__ __forceinline__ int4 cmake(const int32_t (&v)[4]) { return make_int4(v[0], v[1], v[2], v[3]); }
 
-// ring of W rows of 32 lanes x NV values
+// Narrow codes: when T <= NARROW_T_MAX a code fits 16 bits, unsigned and ordered the same way
+// (0 = outside the cone, 1..T = in the window, 0xffff = OVER), and a lane's two codes share one
+// 32-bit word: half the ring bytes, and one packed max per predecessor row.
+constexpr int64_t NARROW_T_MAX = 0xfffe;
+constexpr uint32_t NOVER = 0xffff;
+static_assert(NV == 2, "narrow codes pack the two codes of a lane into one word");
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
+    uint32_t r;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(b));
+    return r;
+}
+
+// ring of W rows of 32 lanes x NV values (the narrow rows use the first half)
 __host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4 * NV; }
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
+
+// One work item's sweep state and the warp's chunk staging.
+struct PullItem {
+    const int32_t *pp, *pc, *rp, *col;
+    int64_t tb, T;
+    int32_t d, n, v0, n_src, wmask;
+    int32_t *c_pp, *c_cost, *c_msucc, *c_off, *c_kp;
+};
+
+// Stage the chunk of tasks u .. u + PCH - 1: predecessor offsets, GPU costs (clamped to
+// T + 1), largest successor ids, and the first `ne` predecessor ids of the chunk, keeping
+// only those >= v0 (older ones are outside every source's cone) compacted by ballot as ring
+// row offsets; each task's first kept entry is found from its boundary b_k (lane k; lane 0
+// also the chunk's end).  Returns e0 (the chunk's first edge) and ne.
+__device__ __forceinline__ void stage_chunk(const DevBatch &B, const PullItem &I, int32_t u, int lane, int32_t &e0,
+                                            int32_t &ne) {
+    __syncwarp();
+    const int32_t t = min(u + lane, I.n);
+    I.c_pp[lane] = I.pp[t];
+    if (lane == 0) I.c_pp[PCH] = I.pp[min(u + PCH, I.n)];
+    if (u + lane < I.n) {
+        const int64_t cg = task_cost(B, I.d, I.tb + u + lane, 1);
+        I.c_cost[lane] = int32_t(cg > I.T ? I.T + 1 : cg);
+        const int32_t r0 = I.rp[u + lane], r1 = I.rp[u + lane + 1];
+        I.c_msucc[lane] = r1 > r0 ? I.col[r1 - 1] : -1;
+    }
+    __syncwarp();
+    e0 = I.c_pp[0];
+    ne = min(I.c_pp[PCH] - e0, PCOL);
+    const int32_t b_k = I.c_pp[lane] - e0;
+    int32_t kp = 0, base = 0;
+    for (int r0 = 0; r0 < PCOL / 32 && 32 * r0 < ne; r0 += 8) {
+        int32_t qv[8];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int32_t i = lane + 32 * (r0 + r);
+            qv[r] = i < ne ? __ldg(I.pc + e0 + i) : -1;
+        }
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int32_t i0 = 32 * (r0 + r);
+            const bool keep = qv[r] >= I.v0;  // -1 past ne
+            const uint32_t bal = __ballot_sync(FULL, keep);
+            if (keep) I.c_off[base + __popc(bal & ((1u << lane) - 1))] = (qv[r] & I.wmask) * 32;
+            if (b_k >= i0 && b_k < i0 + 32) kp = base + __popc(bal & ((1u << (b_k - i0)) - 1));
+            base += __popc(bal);
+        }
+    }
+    I.c_kp[lane] = b_k >= ne ? base : kp;
+    if (lane == 0) I.c_kp[PCH] = base;
+    __syncwarp();
+}
+
+// The sweep of one work item.  R: the ring's row element per lane (Codes: NV int32 codes;
+// uint32_t: two narrow codes).  Adds each source's count to cnt.
+template <bool NARROW>
+__device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I, void *ring, int lane,
+                                           int32_t (&cnt)[NV]) {
+    using R = typename std::conditional<NARROW, uint32_t, Codes>::type;
+    R *__restrict__ val = reinterpret_cast<R *>(ring);
+    int32_t hi = I.v0 + I.n_src - 1;
+    int32_t uc = -1, e0 = 0, ne = 0;  // first task, first predecessor edge and staged entries of the chunk
+    for (int32_t u = I.v0; u <= hi; ++u) {
+        if (uc < 0 || u - uc >= PCH) {
+            uc = u;
+            stage_chunk(B, I, u, lane, e0, ne);
+        }
+        const int32_t k = u - uc;
+        const int32_t lo = I.c_pp[k] - e0, hi_p = I.c_pp[k + 1] - e0;
+        // staged entries of this task (compacted), then any beyond the staging from global
+        const int32_t clo = I.c_kp[k], chi = hi_p <= ne ? I.c_kp[k + 1] : I.c_kp[PCH];
+        constexpr int U = IE_PULL_INFLIGHT;  // predecessor rows in flight per round
+        const int32_t c = I.c_cost[k];
+        int32_t vv[NV];
+        bool any_in = false;
+        if (NARROW) {
+            uint32_t ma = 0, mb = 0;
+            int32_t e = clo;
+            for (; e + U <= chi; e += U) {
+                uint32_t pv[U];
+#pragma unroll
+                for (int r = 0; r < U; ++r) pv[r] = reinterpret_cast<const uint32_t *>(val)[I.c_off[e + r] + lane];
+#pragma unroll
+                for (int r = 0; r < U; r += 2) {
+                    ma = max_u16x2(ma, pv[r]);
+                    mb = max_u16x2(mb, pv[r + 1]);
+                }
+            }
+            for (; e < chi; ++e) ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[I.c_off[e] + lane]);
+            for (int32_t f = max(lo, ne); f < hi_p; ++f) {
+                const int32_t qd = I.pc[e0 + f];
+                if (qd >= I.v0) ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[(qd & I.wmask) * 32 + lane]);
+            }
+            const uint32_t m2 = max_u16x2(ma, mb);
+            // T <= 0xfffe and c <= T + 1: m + c fits 32 bits and fits the window iff <= T
+            const uint32_t own = uint32_t(c) <= uint32_t(I.T) ? uint32_t(c) : NOVER;
+            uint32_t packed = 0;
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const uint32_t m = (m2 >> (16 * q)) & 0xffffu;
+                const bool live = m != 0 && m != NOVER;
+                const uint32_t L = m + uint32_t(c);
+                const bool fits = live && L <= uint32_t(I.T);
+                uint32_t v = live ? (fits ? L : NOVER) : m;
+                if (u - I.v0 == lane + 32 * q) v = own;
+                cnt[q] += fits;
+                any_in |= v != 0 && v != NOVER;
+                packed |= v << (16 * q);
+            }
+            reinterpret_cast<uint32_t *>(val)[(u & I.wmask) * 32 + lane] = packed;
+            (void)vv;
+        } else {
+            int32_t ma[NV], mb[NV];
+#pragma unroll
+            for (int q = 0; q < NV; ++q) ma[q] = mb[q] = -1;
+            int32_t e = clo;
+            for (; e + U <= chi; e += U) {
+                Codes pv[U];
+#pragma unroll
+                for (int r = 0; r < U; ++r) pv[r] = reinterpret_cast<const Codes *>(val)[I.c_off[e + r] + lane];
+#pragma unroll
+                for (int r = 0; r < U; r += 2)
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        ma[q] = max(ma[q], cget(pv[r], q));
+                        mb[q] = max(mb[q], cget(pv[r + 1], q));
+                    }
+            }
+            for (; e < chi; ++e) {
+                const Codes x = reinterpret_cast<const Codes *>(val)[I.c_off[e] + lane];
+#pragma unroll
+                for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
+            }
+            for (int32_t f = max(lo, ne); f < hi_p; ++f) {
+                const int32_t qd = I.pc[e0 + f];
+                if (qd >= I.v0) {
+                    const Codes x = reinterpret_cast<const Codes *>(val)[(qd & I.wmask) * 32 + lane];
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
+                }
+            }
+            const int32_t own = c <= int32_t(I.T) ? c : OVER;
+            // branch-free: T < 2^31 here, so m + c (both <= T + 1) fits in 32 unsigned bits.  A
+            // source's own m is -1 (tasks before a source are outside its cone).
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                const int32_t m = max(ma[q], mb[q]);
+                const bool live = m >= 0 && m != OVER;
+                const uint32_t L = uint32_t(m) + uint32_t(c);
+                const bool fits = live && L <= uint32_t(I.T);
+                int32_t v = live ? (fits ? int32_t(L) : OVER) : m;
+                if (u - I.v0 == lane + 32 * q) v = own;
+                cnt[q] += fits;
+                vv[q] = v;
+                any_in |= v >= 0 && v != OVER;
+            }
+            reinterpret_cast<Codes *>(val)[(u & I.wmask) * 32 + lane] = cmake(vv);
+        }
+        if (__any_sync(FULL, any_in)) hi = max(hi, I.c_msucc[k]);
+    }
+}
 
 // A register cap keeps more warps resident than the 64 registers a free compile takes.
 __global__ void __maxnreg__(IE_PULL_MAXREG)
@@ -67,140 +246,43 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
-    Codes *__restrict__ val = reinterpret_cast<Codes *>(gring) +
-                              (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * (ie_ring_bytes(W) / sizeof(Codes));
-    int32_t *__restrict__ c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
-    int32_t *__restrict__ c_cost = c_pp + PCH + 1;    // GPU costs, clamped to T + 1
-    int32_t *__restrict__ c_msucc = c_cost + PCH;     // largest successor id (-1: none)
-    int32_t *__restrict__ c_off = c_msucc + PCH;      // ring row offsets of the staged predecessors >= v0
-    int32_t *__restrict__ c_kp = c_off + PCOL;        // per task: its first entry in c_off
+    void *ring = reinterpret_cast<unsigned char *>(gring) +
+                 (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * ie_ring_bytes(W);
+    PullItem I;
+    I.c_pp = reinterpret_cast<int32_t *>(mine);  // chunk predecessor offsets
+    I.c_cost = I.c_pp + PCH + 1;                 // GPU costs, clamped to T + 1
+    I.c_msucc = I.c_cost + PCH;                  // largest successor id (-1: none)
+    I.c_off = I.c_msucc + PCH;                   // ring row offsets of the staged predecessors >= v0
+    I.c_kp = I.c_off + PCOL;                     // per task: its first entry in c_off
 
     for (;;) {
         int64_t item = 0;
         if (lane == 0) item = item_lo + atomicAdd(counter, 1);
         item = __shfl_sync(FULL, item, 0);
         if (item >= item_hi) return;
-        const int d = item_dag[item];
-        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
-        const int32_t n = int32_t(B.task_base[d + 1] - tb);
-        const int32_t v0 = int32_t(item - item_base[d]) * SPW;
-        const int32_t n_src = min(SPW, n - v0);
-        const int32_t *rp = B.row_ptr + tb + d;
-        const int32_t *col = B.col_idx + eb;
-        const int32_t *pp = pr_ptr + tb + d;
-        const int32_t *pc = pcol + eb;
-        const int64_t T = unit_time[d];
+        I.d = item_dag[item];
+        I.tb = B.task_base[I.d];
+        const int64_t eb = B.edge_base[I.d];
+        I.n = int32_t(B.task_base[I.d + 1] - I.tb);
+        I.v0 = int32_t(item - item_base[I.d]) * SPW;
+        I.n_src = min(SPW, I.n - I.v0);
+        I.rp = B.row_ptr + I.tb + I.d;
+        I.col = B.col_idx + eb;
+        I.pp = pr_ptr + I.tb + I.d;
+        I.pc = pcol + eb;
+        I.T = unit_time[I.d];
         // this DAG's own window: a power of two above its longest edge span (at most W), so a DAG
         // with short edges touches only the first rows of the ring
-        const int32_t wmask = (1 << (32 - __clz(dag_span[d]))) - 1;
+        I.wmask = (1 << (32 - __clz(dag_span[I.d]))) - 1;
 
         int32_t cnt[NV];  // per source v0 + lane + 32 q
 #pragma unroll
         for (int q = 0; q < NV; ++q) cnt[q] = 0;
-        int32_t hi = v0 + n_src - 1;
-        int32_t uc = -1, e0 = 0, ne = 0;  // first task, first predecessor edge and staged entries of the chunk
-        for (int32_t u = v0; u <= hi; ++u) {
-            if (uc < 0 || u - uc >= PCH) {
-                __syncwarp();
-                uc = u;
-                const int32_t t = min(u + lane, n);
-                c_pp[lane] = pp[t];
-                if (lane == 0) c_pp[PCH] = pp[min(u + PCH, n)];
-                if (u + lane < n) {
-                    const int64_t cg = task_cost(B, d, tb + u + lane, 1);
-                    c_cost[lane] = int32_t(cg > T ? T + 1 : cg);
-                    const int32_t r0 = rp[u + lane], r1 = rp[u + lane + 1];
-                    c_msucc[lane] = r1 > r0 ? col[r1 - 1] : -1;
-                }
-                __syncwarp();
-                e0 = c_pp[0];
-                ne = min(c_pp[PCH] - e0, PCOL);
-                // Stage the first ne predecessor ids of the chunk, keeping only those >= v0 (older
-                // ones are -1 for every source) in order, compacted by ballot; each task's first
-                // kept entry is found from its boundary b_k (lane k; lane 0 also the chunk's end).
-                const int32_t b_k = c_pp[lane] - e0;
-                int32_t kp = 0, base = 0;
-                for (int r0 = 0; r0 < PCOL / 32 && 32 * r0 < ne; r0 += 8) {
-                    int32_t qv[8];
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const int32_t i = lane + 32 * (r0 + r);
-                        qv[r] = i < ne ? __ldg(pc + e0 + i) : -1;
-                    }
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        const int32_t i0 = 32 * (r0 + r);
-                        const bool keep = qv[r] >= v0;  // -1 past ne
-                        const uint32_t bal = __ballot_sync(FULL, keep);
-                        if (keep) c_off[base + __popc(bal & ((1u << lane) - 1))] = (qv[r] & wmask) * 32;
-                        if (b_k >= i0 && b_k < i0 + 32) kp = base + __popc(bal & ((1u << (b_k - i0)) - 1));
-                        base += __popc(bal);
-                    }
-                }
-                c_kp[lane] = b_k >= ne ? base : kp;
-                if (lane == 0) c_kp[PCH] = base;
-                __syncwarp();
-            }
-            const int32_t k = u - uc;
-            const int32_t lo = c_pp[k] - e0, hi_p = c_pp[k + 1] - e0;
-            // staged entries of this task (compacted), then any beyond the staging from global
-            const int32_t clo = c_kp[k], chi = hi_p <= ne ? c_kp[k + 1] : c_kp[PCH];
-            constexpr int U = IE_PULL_INFLIGHT;  // predecessor rows in flight per round
-            int32_t ma[NV], mb[NV];
-#pragma unroll
-            for (int q = 0; q < NV; ++q) ma[q] = mb[q] = -1;
-            {
-                int32_t e = clo;
-                for (; e + U <= chi; e += U) {
-                    Codes pv[U];
-#pragma unroll
-                    for (int r = 0; r < U; ++r) pv[r] = val[c_off[e + r] + lane];
-#pragma unroll
-                    for (int r = 0; r < U; r += 2)
-#pragma unroll
-                        for (int q = 0; q < NV; ++q) {
-                            ma[q] = max(ma[q], cget(pv[r], q));
-                            mb[q] = max(mb[q], cget(pv[r + 1], q));
-                        }
-                }
-                for (; e < chi; ++e) {
-                    const Codes x = val[c_off[e] + lane];
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
-                }
-            }
-            for (int32_t e = max(lo, ne); e < hi_p; ++e) {
-                const int32_t qd = pc[e0 + e];
-                if (qd >= v0) {
-                    const Codes x = val[(qd & wmask) * 32 + lane];
-#pragma unroll
-                    for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
-                }
-            }
-            const int32_t c = c_cost[k];
-            const int32_t own = c <= int32_t(T) ? c : OVER;
-            // branch-free: T < 2^31 here, so m + c (both <= T + 1) fits in 32 unsigned bits.  A
-            // source's own m is -1 (tasks before a source are outside its cone).
-            int32_t vv[NV];
-            bool any_in = false;
-#pragma unroll
-            for (int q = 0; q < NV; ++q) {
-                const int32_t m = max(ma[q], mb[q]);
-                const bool live = m >= 0 && m != OVER;
-                const uint32_t L = uint32_t(m) + uint32_t(c);
-                const bool fits = live && L <= uint32_t(T);
-                int32_t v = live ? (fits ? int32_t(L) : OVER) : m;
-                if (u - v0 == lane + 32 * q) v = own;
-                cnt[q] += fits;
-                vv[q] = v;
-                any_in |= v >= 0 && v != OVER;
-            }
-            val[(u & wmask) * 32 + lane] = cmake(vv);
-            if (__any_sync(FULL, any_in)) hi = max(hi, c_msucc[k]);
-        }
+        if (I.T <= NARROW_T_MAX) sweep_item<true>(B, I, ring, lane, cnt);
+        else sweep_item<false>(B, I, ring, lane, cnt);
 #pragma unroll
         for (int q = 0; q < NV; ++q)
-            if (lane + 32 * q < n_src) ie_out[tb + v0 + 32 * q + lane] = cnt[q];
+            if (lane + 32 * q < I.n_src) ie_out[I.tb + I.v0 + 32 * q + lane] = cnt[q];
         __syncwarp();
     }
 }

@@ -82,6 +82,27 @@ def test_explicit_unit_times_narrow_and_wide():
             compare_dag(b, d, g, m, unit_time=int(T[d]))
 
 
+@pytest.mark.parametrize("T", [65533, 65534, 65535, 65536])
+def test_unit_times_at_the_16_bit_code_boundary(T):
+    """The efficiency sweep keeps 16-bit codes when T <= 65534 and 32-bit ones above: path
+    weights built to land on T - 1, T and T + 1 on both sides of that switch."""
+    rng = np.random.default_rng(T)
+    shapes = inputs.layered(10, cfg=94, n_min=40, n_max=300)
+    costs = np.array([1, 2, 21844, 21845, 21846, 32766, 32767, 32768, 65533, 65534, 65535, 65536], np.int64)
+    dags = []
+    for d in range(shapes.ndag):
+        g = shapes.dag(d)
+        edges = [(u, int(v)) for u in range(g.n) for v in g.col_idx[g.row_ptr[u]:g.row_ptr[u + 1]]]
+        cg = rng.choice(costs, g.n)
+        dags.append(inputs.make_dag(g.n, edges, cg * 3, cg))
+    b = inputs.concat_dags(dags)
+    m = inputs.MACHINE_LAYERED
+    g = gpu_run(b, m, unit_time=np.full(b.ndag, T))
+    assert (g["status"] == 0).all()
+    for d in range(b.ndag):
+        compare_dag(b, d, g, m, unit_time=T)
+
+
 def test_per_dag_launch_matches_batched():
     b = inputs.layered(16, cfg=93, n_max=600)
     m = inputs.MACHINE_LAYERED
