@@ -167,6 +167,15 @@ struct BatchBufs {
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters, dag_span;
     DBuf pr_ptr, pcol, cursor;
     DBuf item_dag, item_dag_lpt, item_base_lpt;
+    // The load's own non-blocking stream: a load orders its copies and kernels on it and waits
+    // for it alone, so it can run while other batches evaluate on other streams.
+    cudaStream_t ls = nullptr;
+    BatchBufs() = default;
+    BatchBufs(const BatchBufs &) = delete;
+    BatchBufs &operator=(const BatchBufs &) = delete;
+    ~BatchBufs() {
+        if (ls) cudaStreamDestroy(ls);
+    }
 };
 
 struct insp_machine {
@@ -175,6 +184,7 @@ struct insp_machine {
     insp_policy pol{};
     bool has_scorer = false;
     DBuf scorer;  // insp::ScorerPacked in device memory
+    std::mutex mu;  // guards the spare lists: batches of one machine may load and die on several threads
     std::vector<std::unique_ptr<Scratch>> spare;
     std::vector<std::unique_ptr<BatchBufs>> spare_bufs;
     insp_tuning tun = kDefaultTuning;  // the tuning batches loaded on this machine start with
@@ -231,8 +241,10 @@ struct insp_batch {
     ~insp_batch() {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
-        if (owner && sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
-        if (owner && bufs && owner->spare_bufs.size() < 2) owner->spare_bufs.push_back(std::move(bufs));
+        if (!owner) return;
+        std::lock_guard<std::mutex> lk(owner->mu);
+        if (sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
+        if (bufs && owner->spare_bufs.size() < 2) owner->spare_bufs.push_back(std::move(bufs));
     }
 
     insp::DevBatch dev() const {
@@ -252,10 +264,12 @@ struct insp_batch {
 
 namespace {
 
-int copy_in(DBuf &dst, const void *src, size_t bytes) {
+// Stream-ordered copy into dst (grown as needed).  A pageable host source is staged by the
+// driver before the call returns; a pinned or device source must stay valid until s is synced.
+int copy_in(DBuf &dst, const void *src, size_t bytes, cudaStream_t s) {
     int rc = dst.alloc(bytes);
     if (rc) return rc;
-    if (bytes) CU(cudaMemcpy(dst.p, src, bytes, cudaMemcpyDefault));
+    if (bytes) CU(cudaMemcpyAsync(dst.p, src, bytes, cudaMemcpyDefault, s));
     return INSP_OK;
 }
 
@@ -293,18 +307,20 @@ int alloc_pull_ring(insp_batch *b) {
     return b->sc->ie_ring.alloc(size_t(b->grid_ie_pull) * wpc * ring);
 }
 
-int alloc_scratch(insp_batch *b) {
+int alloc_scratch(insp_batch *b, cudaStream_t s) {
     DeviceInfo di;
     int rc = device_info(di);
     if (rc) return rc;
-    if (!b->sc) {
-        if (b->owner && !b->owner->spare.empty()) {
+    if (!b->sc && b->owner) {
+        std::lock_guard<std::mutex> lk(b->owner->mu);
+        if (!b->owner->spare.empty()) {
             b->sc = std::move(b->owner->spare.back());
             b->owner->spare.pop_back();
-        } else {
-            b->sc.reset(new (std::nothrow) Scratch);
-            if (!b->sc) return fail(INSP_ENOMEM, "host allocation");
         }
+    }
+    if (!b->sc) {
+        b->sc.reset(new (std::nothrow) Scratch);
+        if (!b->sc) return fail(INSP_ENOMEM, "host allocation");
     }
     Scratch &S = *b->sc;
     const int64_t N = std::max<int64_t>(b->n_total, 1);
@@ -316,11 +332,12 @@ int alloc_scratch(insp_batch *b) {
         return rc;
     bool fresh = false;
     if ((rc = S.ia_done.alloc(N * 4, &fresh))) return rc;
-    if (fresh) CU(cudaMemset(S.ia_done.p, 0, S.ia_done.bytes));
+    if (fresh) CU(cudaMemsetAsync(S.ia_done.p, 0, S.ia_done.bytes, s));
     if ((rc = S.step.alloc(sizeof(insp::StepCounters), &fresh))) return rc;
     if (fresh) {
         const insp::StepCounters c0{0, 0, 1};  // epoch 0 is never published; tag 0 marks empty records
-        CU(cudaMemcpy(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice));
+        CU(cudaMemcpyAsync(S.step.p, &c0, sizeof(c0), cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));  // c0 is a local
     }
     if ((rc = S.make_streams())) return rc;
     if (b->mach.pol.policy == INSP_POLICY_DMDAP_BL && (rc = S.blevel.alloc(N * 8))) return rc;
@@ -394,9 +411,13 @@ int stage_out(DBuf &buf, T *dst, int64_t count, T *&dev, bool &staged) {
     return INSP_OK;
 }
 
-int first_status(insp_batch *b, std::vector<int32_t> &st) {
+// The batch's per-DAG status words, read on stream s (after the work that wrote them).
+int first_status(insp_batch *b, std::vector<int32_t> &st, cudaStream_t s) {
     st.assign(std::max(b->ndag, 0), 0);
-    if (b->ndag) CU(cudaMemcpy(st.data(), b->status.p, size_t(b->ndag) * 4, cudaMemcpyDeviceToHost));
+    if (b->ndag) {
+        CU(cudaMemcpyAsync(st.data(), b->status.p, size_t(b->ndag) * 4, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
     for (int d = 0; d < b->ndag; ++d)
         if (st[d] != INSP_OK) {
             const char *what = st[d] == INSP_ETIMEOUT ? "a bounded device wait gave up" : "device-side error";
@@ -530,13 +551,23 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (n_types < 1 || n_types > 64) return fail(INSP_EINVAL, "n_types must be in 1..64");
     if (!type_cost && !task_cost) return fail(INSP_EINVAL, "need type_cost or task_cost");
     std::unique_ptr<BatchBufs> bb;
-    if (!m->spare_bufs.empty()) {
-        bb = std::move(m->spare_bufs.back());
-        m->spare_bufs.pop_back();
-    } else {
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        if (!m->spare_bufs.empty()) {
+            bb = std::move(m->spare_bufs.back());
+            m->spare_bufs.pop_back();
+        }
+    }
+    if (!bb) {
         bb.reset(new (std::nothrow) BatchBufs);
         if (!bb) return fail(INSP_ENOMEM, "host allocation");
     }
+    if (!bb->ls && cudaStreamCreateWithFlags(&bb->ls, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        bb->ls = nullptr;
+        return fail(INSP_ECUDA, "creating the load stream");
+    }
+    cudaStream_t ls = bb->ls;
     auto *b = new (std::nothrow) insp_batch(std::move(bb));
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
@@ -551,10 +582,16 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     b->n_types = n_types;
     b->h_task_base.resize(ndag + 1);
     b->h_edge_base.resize(ndag + 1);
-    if (cudaMemcpy(b->h_task_base.data(), task_base, (ndag + 1) * 8, cudaMemcpyDefault) != cudaSuccess ||
-        cudaMemcpy(b->h_edge_base.data(), edge_base, (ndag + 1) * 8, cudaMemcpyDefault) != cudaSuccess) {
-        cudaGetLastError();
-        return bail(fail(INSP_ECUDA, "reading task_base / edge_base"));
+    if (is_device_ptr(task_base) || is_device_ptr(edge_base)) {
+        if (cudaMemcpyAsync(b->h_task_base.data(), task_base, (ndag + 1) * 8, cudaMemcpyDefault, ls) != cudaSuccess ||
+            cudaMemcpyAsync(b->h_edge_base.data(), edge_base, (ndag + 1) * 8, cudaMemcpyDefault, ls) != cudaSuccess ||
+            cudaStreamSynchronize(ls) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(INSP_ECUDA, "reading task_base / edge_base"));
+        }
+    } else {
+        std::memcpy(b->h_task_base.data(), task_base, size_t(ndag + 1) * 8);
+        std::memcpy(b->h_edge_base.data(), edge_base, size_t(ndag + 1) * 8);
     }
     if (b->h_task_base[0] != 0 || b->h_edge_base[0] != 0) return bail(fail(INSP_EINVAL, "bases must start at 0"));
     for (int d = 0; d < ndag; ++d) {
@@ -569,18 +606,18 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (b->n_total > 0 && (!row_ptr || !type)) return bail(fail(INSP_EINVAL, "row_ptr and type are required"));
     if (b->m_total > 0 && !col_idx) return bail(fail(INSP_EINVAL, "col_idx is required"));
     int rc;
-    if ((rc = copy_in(b->task_base, b->h_task_base.data(), (ndag + 1) * 8)) ||
-        (rc = copy_in(b->edge_base, b->h_edge_base.data(), (ndag + 1) * 8)) ||
-        (rc = copy_in(b->row_ptr, row_ptr, (b->n_total + ndag) * 4)) ||
-        (rc = copy_in(b->col_idx, col_idx, b->m_total * 4)) || (rc = copy_in(b->type, type, b->n_total)))
+    if ((rc = copy_in(b->task_base, b->h_task_base.data(), (ndag + 1) * 8, ls)) ||
+        (rc = copy_in(b->edge_base, b->h_edge_base.data(), (ndag + 1) * 8, ls)) ||
+        (rc = copy_in(b->row_ptr, row_ptr, (b->n_total + ndag) * 4, ls)) ||
+        (rc = copy_in(b->col_idx, col_idx, b->m_total * 4, ls)) || (rc = copy_in(b->type, type, b->n_total, ls)))
         return bail(rc);
     if (type_cost) {
-        if ((rc = copy_in(b->type_cost, type_cost, size_t(ndag) * n_types * 16))) return bail(rc);
+        if ((rc = copy_in(b->type_cost, type_cost, size_t(ndag) * n_types * 16, ls))) return bail(rc);
     } else if ((rc = b->type_cost.alloc(16))) {
         return bail(rc);
     }
     if (task_cost) {
-        if ((rc = copy_in(b->task_cost, task_cost, b->n_total * 16))) return bail(rc);
+        if ((rc = copy_in(b->task_cost, task_cost, b->n_total * 16, ls))) return bail(rc);
         b->has_task_cost = true;
     } else if (!type_cost) {
         return bail(fail(INSP_EINVAL, "need type_cost or task_cost"));
@@ -590,8 +627,8 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
         (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(512)) ||
         (rc = b->dag_span.alloc(std::max(ndag, 1) * 4)))
         return bail(rc);
-    if (cudaMemset(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4) != cudaSuccess ||
-        cudaMemset(b->max_span.p, 0, 4) != cudaSuccess)
+    if (cudaMemsetAsync(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4, ls) != cudaSuccess ||
+        cudaMemsetAsync(b->max_span.p, 0, 4, ls) != cudaSuccess)
         return bail(fail(INSP_ECUDA, "memset"));
     DeviceInfo di;
     if ((rc = device_info(di))) return bail(rc);
@@ -599,21 +636,21 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     const int grid = std::max(1, std::min(ndag, di.sms * 8));
     if (ndag > 0) {
         insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
-                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, 0);
-        insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, 0);
+                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, ls);
+        insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, ls);
     }
-    if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return bail(fail(INSP_ECUDA, "validation kernels failed"));
     std::vector<int32_t> st;
-    if ((rc = first_status(b, st))) {
+    if ((rc = first_status(b, st, ls))) {
         g_err = "DAG validation failed: " + g_err;
         return bail(rc);
     }
-    if (cudaMemcpy(&b->max_span_h, b->max_span.p, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bail(fail(INSP_ECUDA, "reading max span"));
     std::vector<int64_t> ut(std::max(ndag, 1), 1);
-    if (ndag && cudaMemcpy(ut.data(), b->unit_time_def.p, ndag * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
-        return bail(fail(INSP_ECUDA, "reading unit times"));
+    if (cudaMemcpyAsync(&b->max_span_h, b->max_span.p, 4, cudaMemcpyDeviceToHost, ls) != cudaSuccess ||
+        (ndag && cudaMemcpyAsync(ut.data(), b->unit_time_def.p, ndag * 8, cudaMemcpyDeviceToHost, ls) != cudaSuccess) ||
+        cudaStreamSynchronize(ls) != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "reading max span and unit times"));
     b->max_unit_def = *std::max_element(ut.begin(), ut.end());
     // window of the efficiency sweep: a power of two above every edge span
     b->W = 1;
@@ -645,11 +682,11 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     std::vector<int32_t> idag_lpt(std::max<int64_t>(b->n_items_pull, 1));
     for (int r = 0; r < ndag; ++r)
         for (int64_t k = b->h_rank_item[r]; k < b->h_rank_item[r + 1]; ++k) idag_lpt[k] = order[r];
-    if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4)) ||
-        (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8)) ||
-        (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4)) ||
-        (rc = copy_in(b->item_base_lpt, base_lpt.data(), base_lpt.size() * 8)) ||
-        (rc = copy_in(b->item_dag_lpt, idag_lpt.data(), idag_lpt.size() * 4)))
+    if ((rc = copy_in(b->order, order.data(), size_t(std::max(ndag, 1)) * 4, ls)) ||
+        (rc = copy_in(b->item_base, items.data(), size_t(ndag + 1) * 8, ls)) ||
+        (rc = copy_in(b->item_dag, idag.data(), idag.size() * 4, ls)) ||
+        (rc = copy_in(b->item_base_lpt, base_lpt.data(), base_lpt.size() * 8, ls)) ||
+        (rc = copy_in(b->item_dag_lpt, idag_lpt.data(), idag_lpt.size() * 4, ls)))
         return bail(rc);
     // pull form of the efficiency sweep when its window is at most IE_PULL_MAX_W
     if (b->W <= insp::IE_PULL_MAX_W && ndag > 0) {
@@ -658,12 +695,13 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
             (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
             return bail(rc);
         insp::launch_reverse_csr(B, b->indeg0.as<int32_t>(), b->pr_ptr.as<int32_t>(), cursor.as<int32_t>(),
-                                 b->pcol.as<int32_t>(), grid, 0);
-        if (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess)
-            return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
+                                 b->pcol.as<int32_t>(), grid, ls);
         b->pull = true;
     }
-    if ((rc = alloc_scratch(b))) return bail(rc);
+    if ((rc = alloc_scratch(b, ls))) return bail(rc);
+    // the host vectors above were staged by the driver; the device-side work of the load ends here
+    if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return bail(fail(INSP_ECUDA, "building predecessor lists failed"));
     *out = b;
     return INSP_OK;
 }
@@ -720,8 +758,10 @@ int prep_unit_time(insp_batch *b, const int64_t *unit_time_ns, cudaStream_t s, c
         std::vector<int64_t> def(std::max(b->ndag, 1));
         bool need_def = false;
         for (auto v : h) need_def |= v <= 0;
-        if (need_def && b->ndag)
-            CU(cudaMemcpy(def.data(), b->unit_time_def.p, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost));
+        if (need_def && b->ndag) {
+            CU(cudaMemcpyAsync(def.data(), b->unit_time_def.p, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+            CU(cudaStreamSynchronize(s));
+        }
         int64_t mx = 1;
         for (int d = 0; d < b->ndag; ++d) {
             if (h[d] <= 0) h[d] = def[d];
@@ -813,7 +853,7 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
         if (st_ie) CU(cudaMemcpyAsync(ie, d_ie, N * 4, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
-        return first_status(b, st);
+        return first_status(b, st, s);
     }
     return INSP_OK;
 }
@@ -972,7 +1012,7 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         if (sm) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
-        return first_status(b, st);
+        return first_status(b, st, s);
     }
     return INSP_OK;
 }
@@ -1019,7 +1059,7 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
     if ((rc = ia.alloc(N * 4)) || (rc = ie.alloc(N * 4)) || (rc = layer.alloc(N * 4)) ||
         (rc = bm.alloc(std::max<int64_t>(bm_base[nd], 1) * 4)) || (rc = target.alloc(nd * 8)) ||
         (rc = done.alloc(nd * 4)) || (rc = chosen.alloc(nd * 8)) || (rc = ut.alloc(nd * 8)) || (rc = ctr.alloc(256)) ||
-        (rc = copy_in(bmb, bm_base.data(), bm_base.size() * 8)))
+        (rc = copy_in(bmb, bm_base.data(), bm_base.size() * 8, s)))
         return rc;
     if (!b->pull && !b->ie_global_ready && (rc = alloc_ie_global(b))) return rc;
     CU(cudaMemsetAsync(done.p, 0, size_t(nd) * 4, s));
@@ -1067,7 +1107,7 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
     CU(cudaMemcpyAsync(unit_time_ns, chosen.p, size_t(nd) * 8, cudaMemcpyDefault, s));
     CU(cudaStreamSynchronize(s));
     std::vector<int32_t> st;
-    return first_status(b, st);
+    return first_status(b, st, s);
 }
 
 INSP_API int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream) {
@@ -1170,7 +1210,7 @@ INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int
         if (h[5]) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
-        return first_status(b, st);
+        return first_status(b, st, s);
     }
     return INSP_OK;
 }
@@ -1213,7 +1253,7 @@ INSP_API int insp_batch_status(insp_batch *b, int32_t *status) {
     if (!b) return fail(INSP_EINVAL, "batch is NULL");
     CU(cudaStreamSynchronize(b->last_stream));
     std::vector<int32_t> st;
-    int rc = first_status(b, st);
+    int rc = first_status(b, st, b->last_stream);
     if (status) std::copy(st.begin(), st.end(), status);
     return rc;
 }
@@ -1410,7 +1450,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     if (rc) return rc;
     if (chosen) *chosen = b->tun;
     std::vector<int32_t> st;
-    return first_status(b, st);
+    return first_status(b, st, s);
 }
 
 INSP_API int insp_selftest_wait(int32_t flag_value, int32_t wait_value, int32_t limit, void *stream) {
