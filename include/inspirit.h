@@ -123,7 +123,13 @@ int insp_dag_load_csr(insp_machine *m, int32_t n, const int32_t *row_ptr, const 
  *   at task_base[d] + d; col_idx[edge_base[ndag]] local successor ids;
  *   type[task_base[ndag]]; type_cost[ndag][n_types][2] (one table per DAG) or
  *   NULL when task_cost[task_base[ndag]][2] is given.
- * The first invalid DAG's error is returned.  Synchronous.
+ * The first invalid DAG's error is returned.  Synchronous for the calling
+ * thread, but its copies and kernels run on the batch's own non-blocking stream
+ * and it waits for that stream alone: a load may run on one host thread while
+ * batches of the same machine evaluate on other streams (their kernels overlap),
+ * and loads and destroys of one machine may come from several threads.  Host
+ * inputs in pinned memory are read by DMA (the fastest path); pageable ones are
+ * staged by the CUDA driver.
  * Device memory: the inputs, predecessor lists (another m int32) and the
  * kernels' scratch; the exact ability sweep holds n_max x ceil(n_max / 64)
  * 64-bit words per concurrent DAG (n_max the largest DAG).  Its concurrency
