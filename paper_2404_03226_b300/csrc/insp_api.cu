@@ -1371,16 +1371,20 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    // one evaluation step, timed after a warm-up step
+    // the fastest of three evaluation steps, after a warm-up step (one step alone varies by a
+    // few per cent, as much as the candidates differ)
     auto time_step = [&](float &ms) -> int {
-        for (int rep = 0; rep < 2; ++rep) {
+        ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
             CU(cudaEventRecord(e0, s));
             const int r = insp_evaluate_batch(b, nullptr, ia, ie, worker, start, end, mk, stream);
             if (r) return r;
             CU(cudaEventRecord(e1, s));
             CU(cudaEventSynchronize(e1));
+            float t = 0;
+            CU(cudaEventElapsedTime(&t, e0, e1));
+            if (rep > 0) ms = std::min(ms, t);
         }
-        CU(cudaEventElapsedTime(&ms, e0, e1));
         return INSP_OK;
     };
     insp_tuning best = b->tun;
@@ -1399,7 +1403,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     };
     std::vector<insp_tuning> c;
     // 1. simulation: DAGs per CTA and queue capacity
-    for (int w : {2, 4, 8})
+    for (int w : {1, 2, 4, 8})
         for (int q : {32, 64, 128, 256, 512}) {
             insp_tuning t = best;
             t.sim_warps = w; t.sim_queue = q;
