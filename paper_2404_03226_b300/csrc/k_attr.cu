@@ -72,12 +72,11 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
             // Words v/64 .. NW-1 of the row are needed.
             const int32_t wlo = v >> 6;
             const int32_t span_w = NW - wlo;
-            int32_t g = 32;
-            if (span_w < 32) {
-                g = 1;
-                while (g < span_w) g <<= 1;
-            }
-            const int32_t G = 32 / g, grp = lane / g, wl = lane % g;
+            // g = the power of two >= span_w, at most 32 (shifts and masks: g is not known to the
+            // compiler to be a power of two, so / and % would be full integer divisions)
+            const int32_t lg = span_w >= 32 ? 5 : (span_w <= 1 ? 0 : 32 - __clz(span_w - 1));
+            const int32_t g = 1 << lg;
+            const int32_t G = 32 >> lg, grp = lane >> lg, wl = lane & (g - 1);
             uint64_t *row_v = slot + int64_t(v) * NW;
             int32_t count = 0;
             for (int32_t cw = wlo; cw < NW; cw += g) {
