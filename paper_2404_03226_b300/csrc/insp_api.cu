@@ -297,7 +297,7 @@ int alloc_pull_ring(insp_batch *b) {
     int rc = device_info(di);
     if (rc) return rc;
     const int wpc = b->tun.ie_warps;
-    const int occ = insp::ie_pull_occupancy(wpc);
+    const int occ = insp::ie_pull_occupancy(wpc, b->W);
     if (occ < 1) return fail(INSP_ECUDA, "occupancy query failed");
     const int64_t ring = insp::ie_pull_ring_bytes(b->W);
     const int64_t l2_ctas = std::max<int64_t>(1, (int64_t(b->tun.ie_ring_mb) << 20) / (ring * wpc));

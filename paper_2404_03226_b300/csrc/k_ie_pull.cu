@@ -75,6 +75,18 @@ __device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b) {
 __host__ __device__ constexpr int64_t ie_ring_bytes(int32_t W) { return int64_t(W) * 32 * 4 * NV; }
 // per warp shared memory: the chunk staging
 constexpr int64_t IE_PULL_STAGE_BYTES = ((PCH + 1 + PCH + PCH + PCOL + PCH + 1) * 4 + 15) / 16 * 16;
+// DAGs whose longest edge spans more tasks than this take the sparse sweep.  With long edges the
+// in-window tasks' far successors stretch the sweep over many tasks outside every cone (tiled LU
+// at 32 tiles: 22 % of the visited tasks in a cone, 83 % of the predecessor rows read all
+// "out").  There a W-bit ring bitmap records which rows hold codes (the task is in some cone);
+// a task reads only those predecessors' rows, and a task with none (not a source) is outside
+// every cone: its row is neither computed nor stored.
+constexpr int32_t SPARSE_SPAN = 256;
+// per warp shared memory of a launch with window W: the staging, then the row bitmap when some
+// DAG may take the sparse sweep (W > SPARSE_SPAN + 1)
+__host__ __device__ constexpr int64_t ie_stage_bytes(int32_t W) {
+    return IE_PULL_STAGE_BYTES + (W > SPARSE_SPAN + 1 ? (int64_t(W) / 8 + 15) / 16 * 16 : 0);
+}
 
 // One work item's sweep state and the warp's chunk staging.
 struct PullItem {
@@ -82,6 +94,7 @@ struct PullItem {
     int64_t tb, T;
     int32_t d, n, v0, n_src, wmask;
     int32_t *c_pp, *c_cost, *c_msucc, *c_off, *c_kp;
+    uint32_t *live;  // sparse sweep: W-bit ring bitmap of the rows that hold codes
 };
 
 // Stage the chunk of tasks u .. u + PCH - 1: predecessor offsets, GPU costs (clamped to
@@ -130,7 +143,7 @@ __device__ __forceinline__ void stage_chunk(const DevBatch &B, const PullItem &I
 
 // The sweep of one work item.  R: the ring's row element per lane (Codes: NV int32 codes;
 // uint32_t: two narrow codes).  Adds each source's count to cnt.
-template <bool NARROW>
+template <bool NARROW, bool SPARSE>
 __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I, void *ring, int lane,
                                            int32_t (&cnt)[NV]) {
     using R = typename std::conditional<NARROW, uint32_t, Codes>::type;
@@ -145,11 +158,38 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
         const int32_t k = u - uc;
         const int32_t lo = I.c_pp[k] - e0, hi_p = I.c_pp[k + 1] - e0;
         // staged entries of this task (compacted), then any beyond the staging from global
-        const int32_t clo = I.c_kp[k], chi = hi_p <= ne ? I.c_kp[k + 1] : I.c_kp[PCH];
+        const int32_t clo = I.c_kp[k];
+        int32_t chi = hi_p <= ne ? I.c_kp[k + 1] : I.c_kp[PCH];
+        const int32_t r_u = u & I.wmask;
+        if (SPARSE) {
+            // keep the staged predecessors whose rows hold codes, compacted in place (a round's
+            // writes land at or below its reads; every row read was visited earlier in this item)
+            int32_t nl = 0;
+            for (int32_t e = clo; e < chi; e += 32) {
+                const int32_t i = e + lane;
+                int32_t off = 0;
+                bool keep = false;
+                if (i < chi) {
+                    off = I.c_off[i];
+                    const int32_t r = off >> 5;
+                    keep = (I.live[r >> 5] >> (r & 31)) & 1u;
+                }
+                const uint32_t bal = __ballot_sync(FULL, keep);
+                if (keep) I.c_off[clo + nl + __popc(bal & ((1u << lane) - 1))] = off;
+                nl += __popc(bal);
+            }
+            __syncwarp();
+            chi = clo + nl;
+            if (nl == 0 && hi_p <= ne && u - I.v0 >= SPW) {  // outside every cone: no row
+                if (lane == 0) I.live[r_u >> 5] &= ~(1u << (r_u & 31));
+                __syncwarp();
+                continue;
+            }
+        }
         constexpr int U = IE_PULL_INFLIGHT;  // predecessor rows in flight per round
         const int32_t c = I.c_cost[k];
         int32_t vv[NV];
-        bool any_in = false;
+        bool any_in = false, any_cone = false;
         if (NARROW) {
             uint32_t ma = 0, mb = 0;
             int32_t e = clo;
@@ -166,7 +206,9 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
             for (; e < chi; ++e) ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[I.c_off[e] + lane]);
             for (int32_t f = max(lo, ne); f < hi_p; ++f) {
                 const int32_t qd = I.pc[e0 + f];
-                if (qd >= I.v0) ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[(qd & I.wmask) * 32 + lane]);
+                const int32_t rq = qd & I.wmask;
+                if (qd >= I.v0 && (!SPARSE || ((I.live[rq >> 5] >> (rq & 31)) & 1u)))
+                    ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[rq * 32 + lane]);
             }
             const uint32_t m2 = max_u16x2(ma, mb);
             // T <= 0xfffe and c <= T + 1: m + c fits 32 bits and fits the window iff <= T
@@ -182,9 +224,10 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                 if (u - I.v0 == lane + 32 * q) v = own;
                 cnt[q] += fits;
                 any_in |= v != 0 && v != NOVER;
+                any_cone |= v != 0;
                 packed |= v << (16 * q);
             }
-            reinterpret_cast<uint32_t *>(val)[(u & I.wmask) * 32 + lane] = packed;
+            if (!SPARSE || __any_sync(FULL, any_cone)) reinterpret_cast<uint32_t *>(val)[r_u * 32 + lane] = packed;
             (void)vv;
         } else {
             int32_t ma[NV], mb[NV];
@@ -210,8 +253,9 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
             }
             for (int32_t f = max(lo, ne); f < hi_p; ++f) {
                 const int32_t qd = I.pc[e0 + f];
-                if (qd >= I.v0) {
-                    const Codes x = reinterpret_cast<const Codes *>(val)[(qd & I.wmask) * 32 + lane];
+                const int32_t rq = qd & I.wmask;
+                if (qd >= I.v0 && (!SPARSE || ((I.live[rq >> 5] >> (rq & 31)) & 1u))) {
+                    const Codes x = reinterpret_cast<const Codes *>(val)[rq * 32 + lane];
 #pragma unroll
                     for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
                 }
@@ -230,8 +274,17 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                 cnt[q] += fits;
                 vv[q] = v;
                 any_in |= v >= 0 && v != OVER;
+                any_cone |= v >= 0;
             }
-            reinterpret_cast<Codes *>(val)[(u & I.wmask) * 32 + lane] = cmake(vv);
+            if (!SPARSE || __any_sync(FULL, any_cone)) reinterpret_cast<Codes *>(val)[r_u * 32 + lane] = cmake(vv);
+        }
+        if (SPARSE) {
+            const bool cone = __any_sync(FULL, any_cone);
+            if (lane == 0) {
+                const uint32_t bit = 1u << (r_u & 31);
+                I.live[r_u >> 5] = cone ? (I.live[r_u >> 5] | bit) : (I.live[r_u >> 5] & ~bit);
+            }
+            __syncwarp();
         }
         if (__any_sync(FULL, any_in)) hi = max(hi, I.c_msucc[k]);
     }
@@ -245,7 +298,7 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    unsigned char *mine = smem + int64_t(wib) * IE_PULL_STAGE_BYTES;
+    unsigned char *mine = smem + int64_t(wib) * ie_stage_bytes(W);
     void *ring = reinterpret_cast<unsigned char *>(gring) +
                  (int64_t(blockIdx.x) * (blockDim.x >> 5) + wib) * ie_ring_bytes(W);
     PullItem I;
@@ -254,6 +307,7 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
     I.c_msucc = I.c_cost + PCH;                  // largest successor id (-1: none)
     I.c_off = I.c_msucc + PCH;                   // ring row offsets of the staged predecessors >= v0
     I.c_kp = I.c_off + PCOL;                     // per task: its first entry in c_off
+    I.live = reinterpret_cast<uint32_t *>(mine + IE_PULL_STAGE_BYTES);
 
     for (;;) {
         int64_t item = 0;
@@ -278,8 +332,14 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
         int32_t cnt[NV];  // per source v0 + lane + 32 q
 #pragma unroll
         for (int q = 0; q < NV; ++q) cnt[q] = 0;
-        if (I.T <= NARROW_T_MAX) sweep_item<true>(B, I, ring, lane, cnt);
-        else sweep_item<false>(B, I, ring, lane, cnt);
+        const bool sparse = dag_span[I.d] > SPARSE_SPAN;  // then W > SPARSE_SPAN + 1: the bitmap exists
+        if (I.T <= NARROW_T_MAX) {
+            if (sparse) sweep_item<true, true>(B, I, ring, lane, cnt);
+            else sweep_item<true, false>(B, I, ring, lane, cnt);
+        } else {
+            if (sparse) sweep_item<false, true>(B, I, ring, lane, cnt);
+            else sweep_item<false, false>(B, I, ring, lane, cnt);
+        }
 #pragma unroll
         for (int q = 0; q < NV; ++q)
             if (lane + 32 * q < I.n_src) ie_out[I.tb + I.v0 + 32 * q + lane] = cnt[q];
@@ -336,10 +396,11 @@ __global__ void __launch_bounds__(256) k_reverse_csr(DevBatch B, const int32_t *
 int ie_pull_max_warps() { return PULL_MAX_WARPS; }
 int64_t ie_pull_ring_bytes(int32_t W) { return ie_ring_bytes(W); }
 
-int ie_pull_occupancy(int warps) {
-    const int64_t bytes = IE_PULL_STAGE_BYTES * warps;
+int ie_pull_occupancy(int warps, int32_t W) {
+    const int64_t bytes = ie_stage_bytes(W) * warps;
     int nb = 0;
-    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(ie_stage_bytes(IE_PULL_MAX_W) * PULL_MAX_WARPS));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ie_pull, warps * 32, size_t(bytes)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -351,10 +412,11 @@ void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pco
                     const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
                     const int64_t *unit_time, const int32_t *dag_span, int32_t W, int32_t *gring, int32_t *ie,
                     int grid, int warps, cudaStream_t s) {
-    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize, int(IE_PULL_STAGE_BYTES * PULL_MAX_WARPS));
-    k_ie_pull<<<grid, warps * 32, size_t(IE_PULL_STAGE_BYTES * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
-                                                                           item_lo, item_hi, counter, unit_time, dag_span, W,
-                                                                           gring, ie);
+    cudaFuncSetAttribute(k_ie_pull, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(ie_stage_bytes(IE_PULL_MAX_W) * PULL_MAX_WARPS));
+    k_ie_pull<<<grid, warps * 32, size_t(ie_stage_bytes(W) * warps), s>>>(B, pr_ptr, pcol, item_base, item_dag,
+                                                                         item_lo, item_hi, counter, unit_time,
+                                                                         dag_span, W, gring, ie);
 }
 
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,

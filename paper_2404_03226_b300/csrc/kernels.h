@@ -77,7 +77,7 @@ constexpr int32_t IE_PULL_MAX_W = 8192;
 constexpr int32_t IE_PULL_SOURCES = 64;
 int ie_pull_max_warps();
 int64_t ie_pull_ring_bytes(int32_t W);
-int ie_pull_occupancy(int warps);
+int ie_pull_occupancy(int warps, int32_t W);
 // gring: per-warp rings of ie_pull_ring_bytes(W) in global memory
 void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pcol, const int64_t *item_base,
                     const int32_t *item_dag, int64_t item_lo, int64_t item_hi, int32_t *counter,
