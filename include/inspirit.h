@@ -307,14 +307,15 @@ typedef struct {
     int32_t ie_ring_mb;    /* device memory for the efficiency sweep's window rings, MB (1..65536); it
                               bounds the warps in flight, and rings beyond L2 spill to HBM */
     int32_t sim_warps;     /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
-    int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64, 128, 256 or 512
-                              (more spill to global memory) */
+    int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64, 128, 256, 512 or
+                              1024 (more spill to global memory); 1024 fits CTAs of at most 6 warps (5 with the
+                              learned scorer): a simulation whose CTA does not fit fails with INSP_EINVAL */
     int32_t group_split;   /* 0: groups of equal DAG counts; 1: geometric, each group 4x the DAGs of the
                               one before (the largest DAGs, whose simulations take longest, start first) */
 } insp_tuning;
 
-/* Time a fixed candidate set of tunings on this batch (one insp_evaluate_batch
- * step each after a warm-up step, CUDA events on `stream`; the library's own
+/* Time a fixed candidate set of tunings on this batch (the fastest of three
+ * insp_evaluate_batch steps each after a warm-up step, CUDA events on `stream`; the library's own
  * scratch holds the outputs), in a coordinate search over the fields, keep the
  * fastest and return it in *chosen (may be NULL).  The results of later calls
  * do not depend on the tuning.  Synchronous. */

@@ -102,7 +102,7 @@ bool tuning_ok(const insp_tuning &t) {
            t.ie_warps <= insp::ie_pull_max_warps() && t.ie_ring_mb >= 1 && t.ie_ring_mb <= 65536 &&
            t.sim_warps >= 1 && t.sim_warps <= insp::sim_max_warps() &&
            (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128 || t.sim_queue == 256 ||
-            t.sim_queue == 512) &&
+            t.sim_queue == 512 || t.sim_queue == 1024) &&
            (t.group_split == 0 || t.group_split == 1);
 }
 
@@ -950,7 +950,9 @@ int launch_sim_part(insp_batch *b, const insp::SimArgs &A, cudaStream_t s) {
     if (rc) return rc;
     const bool learned = A.policy == INSP_POLICY_LEARNED;
     const int wpc = b->tun.sim_warps;
-    const int occ = std::max(1, insp::sim_occupancy(learned, b->mach.n_cpu + b->mach.n_gpu, wpc, b->tun.sim_queue));
+    const int occ = insp::sim_occupancy(learned, b->mach.n_cpu + b->mach.n_gpu, wpc, b->tun.sim_queue);
+    if (occ < 1)
+        return fail(INSP_EINVAL, "the simulation CTA (sim_warps x sim_queue) does not fit in shared memory");
     const int grid = std::max(1, std::min(di.sms * occ, (A.n_order + wpc - 1) / wpc));
     insp::launch_sim(A, grid, wpc, b->tun.sim_queue, s);
     CU(cudaGetLastError());
@@ -1404,7 +1406,8 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     std::vector<insp_tuning> c;
     // 1. simulation: DAGs per CTA and queue capacity
     for (int w : {1, 2, 4, 8})
-        for (int q : {32, 64, 128, 256, 512}) {
+        for (int q : {32, 64, 128, 256, 512, 1024}) {
+            if (q == 1024 && w > 4) continue;  // does not fit in shared memory
             insp_tuning t = best;
             t.sim_warps = w; t.sim_queue = q;
             c.push_back(t);

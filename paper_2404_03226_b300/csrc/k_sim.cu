@@ -38,6 +38,13 @@ constexpr int NODE_NONE = 0xff;
 enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
 enum { ST_INC = 0, ST_DEC = 1 };
 
+// Pools of at least MASK_MIN shared-memory entries keep, per worker (32 workers or fewer), a
+// bitmap of its entries there, so a pop visits only the popping worker's entries instead of
+// the whole pool (the tiled DAGs hold hundreds of ready tasks over 20 workers).
+constexpr int MASK_MIN = 128;
+template <int POOL_C>
+constexpr int mask_words() { return POOL_C >= MASK_MIN ? POOL_C / 32 : 1; }
+
 // POOL_C: ready-pool entries per warp kept in shared memory (the queue
 // capacity the autotuner picks; entries beyond it spill to global memory).
 template <int POOL_C>
@@ -51,6 +58,7 @@ struct WarpSmem {
     int32_t newly[NL_C];
     int32_t run_end[MAX_WORKERS];
     int64_t tcost[MAX_TYPES_SMEM * 2];
+    uint32_t wmask[POOL_C >= MASK_MIN ? 32 : 1][mask_words<POOL_C>()];  // entry bitmaps per worker
 };
 
 template <int POOL_C>
@@ -182,6 +190,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         __syncthreads();
     }
     const DevBatch &B = A.B;
+    constexpr bool USE_MASK = POOL_C >= MASK_MIN && !TWO;
     const int32_t P = A.n_cpu + A.n_gpu, n_cpu = A.n_cpu;
     const int64_t xfer = A.xfer;
     const bool smem_types = (A.B.task_cost == nullptr) && (B.n_types <= MAX_TYPES_SMEM);
@@ -235,6 +244,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         if (smem_types) {
             for (int i = lane; i < B.n_types * 2; i += 32) sm->tcost[i] = B.type_cost[int64_t(d) * B.n_types * 2 + i];
         }
+        if (USE_MASK)
+            for (int i = lane; i < 32 * mask_words<POOL_C>(); i += 32) (&sm->wmask[0][0])[i] = 0u;
         for (int32_t t = lane; t < n; t += 32) {
             st_a[t] = make_int2(A.indeg0[tb + t], NODE_NONE);
             st_b[t] = make_longlong2(NEG_TIME, NEG_TIME);
@@ -295,6 +306,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                 if (TWO && hi) { qc1 += c; qn1 += 1; } else { qc0 += c; qn0 += 1; }
                 if (insp_check(nready < n, A.status + d))  // the pool never holds more than n tasks
                     pool.set(nready, t | (ws << 24), seq, tia, tie, hi ? dr1 : dr0, c);
+                if (USE_MASK && nready < POOL_C) sm->wmask[ws][nready >> 5] |= 1u << (nready & 31);
                 if (EX && A.tr_push_time) {
                     const int64_t r = tb + seq;
                     A.tr_push_time[r] = now;
@@ -421,7 +433,21 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
                     // worker w, keyed by the mode's priority, ties to the lowest id (FIFO: the
                     // oldest push)
                     auto scan = [&](auto key_of) {
-                        for (int32_t i = lane; i < nready; i += 32) {
+                        int32_t i0 = 0;
+                        if (USE_MASK) {
+                            // shared-memory entries: the set bits of w's bitmap, word j by lane j
+                            const int32_t ns = min(nready, POOL_C);
+                            if (lane < ((ns + 31) >> 5)) {
+                                for (uint32_t m = sm->wmask[w][lane]; m; m &= m - 1) {
+                                    const int32_t i = lane * 32 + __ffs(m) - 1;
+                                    const int32_t e = pool.idw(i);
+                                    const uint64_t key = key_of(i, uint64_t(0x7fffffffu - uint32_t(e & 0xffffff)));
+                                    if (key > best) { best = key; bi = i; }
+                                }
+                            }
+                            i0 = POOL_C;  // then the spilled entries
+                        }
+                        for (int32_t i = i0 + lane; i < nready; i += 32) {
                             const int32_t e = pool.idw(i);
                             if ((e >> 24) != w) continue;
                             const uint64_t key = key_of(i, uint64_t(0x7fffffffu - uint32_t(e & 0xffffff)));
@@ -455,6 +481,14 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             if (lane == (w & 31)) {
                 const int32_t t = pool.idw(idx) & 0xffffff;
                 const int64_t dr = pool.dr(idx), c = pool.cost(idx);
+                if (USE_MASK) {  // idx leaves w's bitmap; the last entry moves into idx
+                    if (idx < POOL_C) sm->wmask[w][idx >> 5] &= ~(1u << (idx & 31));
+                    if (idx != last) {
+                        const int32_t w2 = pool.idw(last) >> 24;
+                        if (last < POOL_C) sm->wmask[w2][last >> 5] &= ~(1u << (last & 31));
+                        if (idx < POOL_C) sm->wmask[w2][idx >> 5] |= 1u << (idx & 31);
+                    }
+                }
                 if (idx != last) pool.move(last, idx, lane, true);
                 const int64_t s = max(now, dr), e = s + c;
                 if (TWO && w >= 32) { qc1 -= c; qn1 -= 1; run1 = t; busy1 = e; rlo1 = rp[t]; rhi1 = rp[t + 1]; pf1 = true; }
@@ -595,10 +629,24 @@ static size_t sim_dyn_bytes(int warps) {
            (L ? sizeof(ScorerPacked) + warps * sizeof(LearnSmem) : 0);
 }
 
+// the device's opt-in limit of dynamic shared memory per CTA
+static size_t smem_optin() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 48 * 1024;
+    }
+    return size_t(v);
+}
+// the largest CTA of this variant that fits (large queues hold fewer warps per CTA)
+template <bool L, int Q>
+static size_t sim_dyn_max() {
+    return std::min(sim_dyn_bytes<L, Q>(SIM_WARPS), smem_optin());
+}
+
 template <bool L, int Q, bool TWO, bool EX>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
-    cudaFuncSetAttribute(k_sim<L, Q, TWO, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q>()));
     k_sim<L, Q, TWO, EX><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
 }
 
@@ -608,7 +656,8 @@ static void launch_l(const SimArgs &A, int grid, int threads, int queue, cudaStr
     else if (queue <= 64) launch_q<L, 64, TWO, EX>(A, grid, threads, s);
     else if (queue <= 128) launch_q<L, 128, TWO, EX>(A, grid, threads, s);
     else if (queue <= 256) launch_q<L, 256, TWO, EX>(A, grid, threads, s);
-    else launch_q<L, 512, TWO, EX>(A, grid, threads, s);
+    else if (queue <= 512) launch_q<L, 512, TWO, EX>(A, grid, threads, s);
+    else launch_q<L, 1024, TWO, EX>(A, grid, threads, s);
 }
 
 template <bool EX>
@@ -639,8 +688,8 @@ int sim_max_warps() { return SIM_WARPS; }
 template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
-    cudaFuncSetAttribute(k_sim<L, Q, TWO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sim_dyn_bytes<L, Q>(SIM_WARPS)));
+    if (sim_dyn_bytes<L, Q>(threads / 32) > sim_dyn_max<L, Q>()) return 0;  // the CTA does not fit
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q>()));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO, false>, threads,
                                                       sim_dyn_bytes<L, Q>(threads / 32)) != cudaSuccess) {
         cudaGetLastError();
@@ -654,7 +703,8 @@ static int occ_l(int threads, int queue) {
            : queue <= 64  ? occ_q<L, 64, TWO>(threads)
            : queue <= 128 ? occ_q<L, 128, TWO>(threads)
            : queue <= 256 ? occ_q<L, 256, TWO>(threads)
-                          : occ_q<L, 512, TWO>(threads);
+           : queue <= 512 ? occ_q<L, 512, TWO>(threads)
+                          : occ_q<L, 1024, TWO>(threads);
 }
 int sim_occupancy(bool learned, int n_workers, int warps, int queue) {
     const int threads = 32 * std::max(1, std::min(warps, SIM_WARPS));

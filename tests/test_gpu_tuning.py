@@ -20,6 +20,7 @@ TUNINGS = [
     dict(groups=3, attr_overlap=0, ia_warps=16, ie_warps=16, ie_ring_mb=512, sim_warps=4, sim_queue=64, group_split=1),
     dict(groups=2, attr_overlap=1, ia_warps=16, ie_warps=8, ie_ring_mb=256, sim_warps=8, sim_queue=512, group_split=0),
     dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=3, sim_queue=256, group_split=0),
+    dict(groups=2, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=5, sim_queue=1024, group_split=0),
 ]
 
 
@@ -93,7 +94,7 @@ def test_autotune_keeps_results():
     r0 = _run(B)
     t = B.autotune()
     assert t == B.tuning
-    assert t["sim_queue"] in (32, 64, 128, 256, 512) and 1 <= t["sim_warps"] <= 8 and 1 <= t["ie_warps"] <= 8
+    assert t["sim_queue"] in (32, 64, 128, 256, 512, 1024) and 1 <= t["sim_warps"] <= 8 and 1 <= t["ie_warps"] <= 8
     r1 = _run(B)
     for f in r0:
         np.testing.assert_array_equal(r0[f], r1[f], err_msg=f)
@@ -126,10 +127,11 @@ def test_machine_tuning_applies_to_later_batches():
         M.set_tuning(dict(TUNINGS[0], sim_queue=7))
 
 
-@pytest.mark.parametrize("queue", [32, 512])
+@pytest.mark.parametrize("queue", [32, 128, 512, 1024])
 def test_large_ready_pools(queue):
-    """Tiled DAGs hold hundreds of ready tasks at once: a 512-entry pool keeps them in
-    shared memory, a 32-entry one spills most of them; both give the oracle's schedule."""
+    """Tiled DAGs hold hundreds of ready tasks at once: a 512- or 1024-entry pool keeps them
+    in shared memory, a 32-entry one spills most of them, a 128-entry one keeps per-worker
+    bitmaps of its shared part and spills the rest; all give the oracle's schedule."""
     import paper_2404_03226_b300 as P
     b = inputs.concat([inputs.tiled(inputs.KIND_CHOLESKY, 16, 2), inputs.tiled(inputs.KIND_QR, 12, 1)])
     m = inputs.MACHINE_TILED
@@ -137,4 +139,19 @@ def test_large_ready_pools(queue):
     B.tuning = dict(TUNINGS[0], sim_queue=queue, sim_warps=2)
     out = _run(B, True)
     for d in range(b.ndag):
+        compare_dag(b, d, out, m)
+
+
+def test_simulation_cta_that_does_not_fit_is_an_error():
+    """Eight warps of 1024-entry pools exceed a CTA's shared memory: the evaluation reports
+    INSP_EINVAL instead of launching, and the batch stays usable."""
+    import paper_2404_03226_b300 as P
+    b, m = _batch(), inputs.MACHINE_LAYERED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = dict(TUNINGS[0], sim_warps=8, sim_queue=1024)
+    with pytest.raises(P.InspError):
+        _run(B, True)
+    B.tuning = TUNINGS[0]
+    out = _run(B, True)
+    for d in range(0, b.ndag, 7):
         compare_dag(b, d, out, m)
