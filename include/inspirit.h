@@ -180,6 +180,17 @@ int insp_simulate_batch(insp_batch *b, const int32_t *ia, const int32_t *ie, int
  * on `stream`.  Errors: as the two calls. */
 int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
                         int64_t *start, int64_t *end, int64_t *makespan, void *stream);
+/* As insp_evaluate_batch, but host output arrays must be pinned (page-locked,
+ * e.g. cudaHostAlloc) and are filled asynchronously: the call returns once the
+ * step and its device-to-host copies are enqueued on `stream`.  The outputs and
+ * the per-DAG status (insp_batch_status) are valid after `stream` is
+ * synchronised; until then the batch's staging memory is in use, so the batch
+ * must not be evaluated again on another stream, and insp_batch_destroy waits
+ * for it.  A serving loop overlaps one batch's copies with the next batch's
+ * kernels this way.  Errors: INSP_EINVAL for a pageable host output, else as
+ * insp_evaluate_batch (device-side errors show in the status). */
+int insp_evaluate_batch_async(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
+                              int32_t *worker, int64_t *start, int64_t *end, int64_t *makespan, void *stream);
 
 /* Automatic unit time per DAG (Sec. 4.3 tunes T by hand, iteratively; this
  * search replaces the hand tuning): candidates T_k = med * 2^k for

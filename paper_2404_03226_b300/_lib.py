@@ -60,6 +60,7 @@ _PROTOS = {
     "insp_simulate": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_evaluate_batch": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_evaluate_batch_async": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_simulate_trace": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(insp_trace), _vp]),
     "insp_bottom_level_batch": (ctypes.c_int, [_vp, _vp, _vp]),
     "insp_unit_time_search": (ctypes.c_int, [_vp, ctypes.c_int32, _vp, _vp]),
@@ -202,6 +203,11 @@ def insp_simulate_batch(b, ia, ie, worker, start, end, makespan, stream=None) ->
 def insp_evaluate_batch(b, unit_time_ns, ia, ie, worker, start, end, makespan, stream=None) -> None:
     check(lib().insp_evaluate_batch(b, ptr(unit_time_ns), ptr(ia), ptr(ie), ptr(worker), ptr(start), ptr(end),
                                     ptr(makespan), stream_ptr(stream)))
+
+
+def insp_evaluate_batch_async(b, unit_time_ns, ia, ie, worker, start, end, makespan, stream=None) -> None:
+    check(lib().insp_evaluate_batch_async(b, ptr(unit_time_ns), ptr(ia), ptr(ie), ptr(worker), ptr(start),
+                                          ptr(end), ptr(makespan), stream_ptr(stream)))
 
 
 def insp_simulate_per_dag(b, ia, ie, worker, start, end, makespan, stream=None) -> None:

@@ -1128,8 +1128,39 @@ INSP_API int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream) {
     return INSP_OK;
 }
 
+namespace {
+bool is_pinned_host(const void *p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+int evaluate_impl(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
+                  int64_t *start, int64_t *end, int64_t *makespan, void *stream, bool async);
+}  // namespace
+
 INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
                                  int32_t *worker, int64_t *start, int64_t *end, int64_t *makespan, void *stream) {
+    return evaluate_impl(b, unit_time_ns, ia, ie, worker, start, end, makespan, stream, false);
+}
+
+INSP_API int insp_evaluate_batch_async(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie,
+                                       int32_t *worker, int64_t *start, int64_t *end, int64_t *makespan,
+                                       void *stream) {
+    if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
+    const void *outs[6] = {ia, ie, worker, start, end, makespan};
+    for (const void *o : outs)
+        if (!is_device_ptr(o) && !is_pinned_host(o))
+            return fail(INSP_EINVAL, "insp_evaluate_batch_async needs device or pinned host outputs");
+    return evaluate_impl(b, unit_time_ns, ia, ie, worker, start, end, makespan, stream, true);
+}
+
+namespace {
+int evaluate_impl(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32_t *ie, int32_t *worker,
+                  int64_t *start, int64_t *end, int64_t *makespan, void *stream, bool async) {
     if (!b || !ia || !ie || !worker || !start || !end || !makespan) return fail(INSP_EINVAL, "NULL argument");
     if (b->mach.pol.policy == INSP_POLICY_LEARNED && !(b->owner && b->owner->has_scorer))
         return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
@@ -1210,12 +1241,14 @@ INSP_API int insp_evaluate_batch(insp_batch *b, const int64_t *unit_time_ns, int
         if (h[3]) CU(cudaMemcpyAsync(start, d_start, N * 8, cudaMemcpyDeviceToHost, s));
         if (h[4]) CU(cudaMemcpyAsync(end, d_end, N * 8, cudaMemcpyDeviceToHost, s));
         if (h[5]) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+        if (async) return INSP_OK;
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
         return first_status(b, st, s);
     }
     return INSP_OK;
 }
+}  // namespace
 
 INSP_API int insp_simulate(insp_dag *d, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
                            int64_t *end, int64_t *makespan, void *stream) {
