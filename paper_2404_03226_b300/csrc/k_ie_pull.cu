@@ -186,7 +186,9 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                 continue;
             }
         }
-        constexpr int U = IE_PULL_INFLIGHT;  // predecessor rows in flight per round
+        // predecessor rows in flight per round; the last round's loads are predicated (12 or 16
+        // narrow rows in flight were measured slower)
+        constexpr int U = IE_PULL_INFLIGHT;
         const int32_t c = I.c_cost[k];
         int32_t vv[NV];
         bool any_in = false, any_cone = false;
@@ -203,7 +205,18 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                     mb = max_u16x2(mb, pv[r + 1]);
                 }
             }
-            for (; e < chi; ++e) ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[I.c_off[e] + lane]);
+            // the rest as one more round, loads predicated (0 = outside: the max's identity)
+            if (e < chi) {
+                uint32_t pv[U];
+#pragma unroll
+                for (int r = 0; r < U; ++r)
+                    pv[r] = e + r < chi ? reinterpret_cast<const uint32_t *>(val)[I.c_off[e + r] + lane] : 0u;
+#pragma unroll
+                for (int r = 0; r < U; r += 2) {
+                    ma = max_u16x2(ma, pv[r]);
+                    mb = max_u16x2(mb, pv[r + 1]);
+                }
+            }
             for (int32_t f = max(lo, ne); f < hi_p; ++f) {
                 const int32_t qd = I.pc[e0 + f];
                 const int32_t rq = qd & I.wmask;
@@ -246,10 +259,18 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                         mb[q] = max(mb[q], cget(pv[r + 1], q));
                     }
             }
-            for (; e < chi; ++e) {
-                const Codes x = reinterpret_cast<const Codes *>(val)[I.c_off[e] + lane];
+            if (e < chi) {
+                Codes pv[U];
 #pragma unroll
-                for (int q = 0; q < NV; ++q) ma[q] = max(ma[q], cget(x, q));
+                for (int r = 0; r < U; ++r)
+                    pv[r] = e + r < chi ? reinterpret_cast<const Codes *>(val)[I.c_off[e + r] + lane] : cmake({-1, -1});
+#pragma unroll
+                for (int r = 0; r < U; r += 2)
+#pragma unroll
+                    for (int q = 0; q < NV; ++q) {
+                        ma[q] = max(ma[q], cget(pv[r], q));
+                        mb[q] = max(mb[q], cget(pv[r + 1], q));
+                    }
             }
             for (int32_t f = max(lo, ne); f < hi_p; ++f) {
                 const int32_t qd = I.pc[e0 + f];
