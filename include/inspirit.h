@@ -102,7 +102,9 @@ void insp_machine_destroy(insp_machine *m);
  * counterpart in the paper).  `bf16_weights` holds, in this order, W1[16][64],
  * b1[64], W2[64][64], b2[64], W3[64], b3[1] as raw BF16 bit patterns
  * (nbytes = 5313 * 2); every value must be k / 64 with integer |k| <= 128.
- * Host pointer.  Errors: INSP_EINVAL (size or off-grid value). */
+ * Host pointer.  Call it before loading batches on the machine, not while its
+ * batches load or evaluate on other threads.  Errors: INSP_EINVAL (size or
+ * off-grid value). */
 int insp_set_scorer(insp_machine *m, const uint16_t *bf16_weights, size_t nbytes);
 
 /* Load one DAG of n tasks (CSR, Sec. 2.1 task graph).

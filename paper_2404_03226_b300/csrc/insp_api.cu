@@ -184,7 +184,7 @@ struct insp_machine {
     insp_policy pol{};
     bool has_scorer = false;
     DBuf scorer;  // insp::ScorerPacked in device memory
-    std::mutex mu;  // guards the spare lists: batches of one machine may load and die on several threads
+    std::mutex mu;  // guards the spare lists and the tuning: batches of one machine may load and die on several threads
     std::vector<std::unique_ptr<Scratch>> spare;
     std::vector<std::unique_ptr<BatchBufs>> spare_bufs;
     insp_tuning tun = kDefaultTuning;  // the tuning batches loaded on this machine start with
@@ -572,7 +572,10 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
     b->owner = m;
-    b->tun = m->tun;
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        b->tun = m->tun;
+    }
     b->mach_params.n_cpu = m->n_cpu;
     b->mach_params.n_gpu = m->n_gpu;
     b->mach_params.xfer = m->xfer;
@@ -1370,6 +1373,7 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
 INSP_API int insp_machine_set_tuning(insp_machine *m, const insp_tuning *t) {
     if (!m || !t) return fail(INSP_EINVAL, "NULL argument");
     if (!tuning_ok(*t)) return fail(INSP_EINVAL, "tuning field out of range");
+    std::lock_guard<std::mutex> lk(m->mu);
     m->tun = *t;
     return INSP_OK;
 }
