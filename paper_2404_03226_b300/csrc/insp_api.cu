@@ -94,7 +94,10 @@ int device_info(DeviceInfo &di) {
 }
 
 constexpr int MAX_GROUPS = 16;
-const insp_tuning kDefaultTuning = {1, 1, 16, 16, 512, 4, 64, 0};
+// The tuning a batch starts with: what the autotuner picks on the 4096-DAG layered workload
+// (one group, overlapped attribute sweeps, 4-warp efficiency CTAs with a 1 GB ring budget,
+// 2-warp simulation CTAs with 32-entry pools).
+const insp_tuning kDefaultTuning = {1, 1, 16, 4, 1024, 2, 32, 0};
 
 bool tuning_ok(const insp_tuning &t) {
     return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
