@@ -262,3 +262,13 @@ def test_tiled_32_long_spans_take_the_pull_sweep():
     assert (g["status"] == 0).all()
     for d in range(b.ndag):
         compare_dag(b, d, g, m)
+
+
+def test_tiled_64_cholesky_window_4096():
+    """Cholesky at 64 tiles (45,760 tasks, edges spanning up to 2,078 ids: a 4096-row window and
+    the sparse efficiency sweep; bitset rows of 715 words; hundreds of ready tasks)."""
+    b = inputs.tiled(inputs.KIND_CHOLESKY, 64, 1)
+    m = inputs.MACHINE_TILED
+    g = gpu_run(b, m)
+    assert (g["status"] == 0).all()
+    compare_dag(b, 0, g, m)
