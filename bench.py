@@ -572,7 +572,7 @@ def run_ours(args, rank, world, local_rank):
             if rc != 0:
                 raise RuntimeError("device-side status not OK in the e2e loop: " + _lib.last_error())
 
-        th = threading.Thread(target=loader)
+        th = threading.Thread(target=loader, daemon=True)  # never blocks the exit after an error
         th.start()
         pending = None
         for k in range(warm + k_e2e):
