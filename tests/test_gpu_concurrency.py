@@ -30,7 +30,7 @@ def test_load_on_one_thread_while_another_evaluates():
         except Exception as exc:
             q.put(exc)
 
-    th = threading.Thread(target=loader)
+    th = threading.Thread(target=loader, daemon=True)
     th.start()
     stream = torch.cuda.Stream()
     results = []
