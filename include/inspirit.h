@@ -65,10 +65,16 @@ extern "C" {
                                   the library computes it, the ia / ie inputs are not read */
 
 /* Controller parameters of Sec. 4.4 (the paper gives no values).  A zero
- * field takes its default for P = n_cpu + n_gpu workers and the DAG's default
- * unit time T (4 x the lower median of its GPU costs):
+ * field takes its default for P = n_cpu + n_gpu workers and the unit time T
+ * of the DAG's inspiring efficiency (Sec. 4.2-4.3: the ascending slope is a
+ * task count per that same unit time window):
  *   task_window = s_inc = s_dec = dec_step = P, c = max(1, P / 2),
- *   k_inc = k_inc_tasks / k_inc_ns = P tasks per T ns. */
+ *   k_inc = k_inc_tasks / k_inc_ns = P tasks per T ns.
+ * T is the DAG's unit time in the batch's last insp_attributes* or
+ * insp_evaluate_batch* call (before any: the DAG's default unit time, 4 x the
+ * lower median of its GPU costs); insp_simulate_noalloc takes the default
+ * unit time.  Simulating with attributes computed elsewhere at another T needs
+ * k_inc set explicitly. */
 typedef struct {
     int32_t policy;      /* INSP_POLICY_* */
     int32_t task_window; /* re-judge the state when Nready moved by at least this much */
@@ -382,12 +388,21 @@ int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_
  * policy may be NULL; INSP_POLICY_LEARNED and INSP_POLICY_DMDAP_BL are not
  * accepted.
  *
+ * Every array must be device memory of the current device (or managed
+ * memory) at least as long as stated above, counted from the pointer to the
+ * end of its allocation (checked with the driver's cuMemGetAddressRange):
+ * host memory, another device's memory or a shorter array gives INSP_EINVAL
+ * before any kernel runs.  A short array inside a larger allocation (e.g. a
+ * caching allocator's block) passes this check; its extra elements are read.
+ * The k_inc default takes the DAG's default unit time (see insp_policy).
+ *
  * The first call on a device looks up the array's device address on that
  * device; make that first call before any stream capture.  Every call reuses
  * the same array (it keeps the previous call's contents and clears what must
  * start at zero), so calls whose work overlaps on the GPU -- two streams or
- * two host threads -- race and must be serialised by the caller.  The call is
- * synchronous: it waits for `stream` before returning the final status. */
+ * two host threads -- race and must be serialised by the caller.  Every call
+ * waits for `stream` (the validation status and the final status are read
+ * back) before it returns the final status. */
 #define INSP_NOALLOC_MAX_TASKS 65536
 #define INSP_NOALLOC_SCRATCH_BYTES 4194560
 int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, const uint8_t *type,

@@ -185,7 +185,9 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
              mlp_weights=None, force=None, trace: bool = False, feat_pop: int = -1, feat_cap: int = 0):
     """Run the event simulation; returns a dict with worker/start/end/makespan
     (and the per-pop trace when requested).  ia_/ie_ default to the oracle's
-    own attributes for unit_time."""
+    own attributes for unit_time (default: the DAG's default unit time), and
+    unit_time also sets the default ascending slope k_inc = P tasks per
+    unit_time ns."""
     pol = policy or Policy()
     T = int(unit_time) if unit_time else default_unit_time(dag)
     a = _i32(ia(dag) if ia_ is None else ia_)
@@ -215,10 +217,11 @@ def simulate(dag, machine, policy: Policy | None = None, unit_time: int | None =
                     _p(bufs["feat_task"], _i32p), _p(bufs["feat"], _i32p),
                     _p(bufs["push_t"], _i64p) if trace else None, _p(bufs["push_task"], _i32p),
                     _p(bufs["push_worker"], _i32p), _p(bufs["push_nready"], _i32p), 0)
-    # k_inc's default is P tasks per the DAG's *default* unit time, whatever T the
-    # attributes used (0 lets orc_simulate take the default).
+    # k_inc's default is P tasks per T, the unit time the attributes use (Sec. 4.2-4.4 share one
+    # unit time window: inspiring efficiency counts releases within it, and the ascending slope
+    # is a task count per such window).
     rc = _L().orc_simulate(n, _p(rp, _i32p), _p(ci, _i32p), _p(cc, _i64p), _p(cg, _i64p), machine.n_cpu,
-                           machine.n_gpu, machine.xfer_ns, ctypes.byref(pol), 0, _p(a, _i32p), _p(e, _i32p),
+                           machine.n_gpu, machine.xfer_ns, ctypes.byref(pol), T, _p(a, _i32p), _p(e, _i32p),
                            None if w is None else _p(w, _i16p), None if fobj is None else ctypes.byref(fobj),
                            _p(worker, _i32p), _p(start, _i64p), _p(end, _i64p), _p(mk, _i64p),
                            None if tr is None else ctypes.byref(tr))

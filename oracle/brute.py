@@ -95,3 +95,48 @@ def layers(dag):
         for p in all_paths_from(dag, v):
             best[p[-1]] = max(best[p[-1]], len(p) - 1)
     return best
+
+
+def optimum(dag, machine):
+    """Minimum makespan by listing every assignment of tasks to workers and
+    every topological order: tasks are placed one by one in that order, each
+    at the earliest time its worker is free and its data (with the transfer
+    cost between memory nodes: CPUs share node 0, GPU g is node 1+g) has
+    arrived.  Every schedule can be shifted left into one of these without a
+    later end, so the minimum over them is the optimum.  Tiny DAGs only."""
+    import itertools
+    n, P = dag.n, machine.n_cpu + machine.n_gpu
+    succ = _succ(dag)
+    preds = [[u for u in range(n) if v in succ[u]] for v in range(n)]
+    node = [0 if w < machine.n_cpu else 1 + w - machine.n_cpu for w in range(P)]
+
+    def orders():
+        def rec(done, seq):
+            if len(seq) == n:
+                yield list(seq)
+                return
+            for t in range(n):
+                if t not in done and all(p in done for p in preds[t]):
+                    done.add(t)
+                    seq.append(t)
+                    yield from rec(done, seq)
+                    seq.pop()
+                    done.remove(t)
+        yield from rec(set(), [])
+
+    topo = list(orders())
+    best = None
+    for assign in itertools.product(range(P), repeat=n):
+        for order in topo:
+            free = [0] * P
+            end = [0] * n
+            for t in order:
+                w = assign[t]
+                ready = max([end[p] + (machine.xfer_ns if node[assign[p]] != node[w] else 0) for p in preds[t]],
+                            default=0)
+                s = max(free[w], ready)
+                end[t] = s + int(dag.c_cpu[t] if w < machine.n_cpu else dag.c_gpu[t])
+                free[w] = end[t]
+            mk = max(end) if n else 0
+            best = mk if best is None else min(best, mk)
+    return best or 0

@@ -512,8 +512,9 @@ EXPORT int orc_simulate(int32_t n, const int32_t *row_ptr, const int32_t *col_id
     if (rc) return rc;
     if (pol_in->policy < POL_INSPIRIT || pol_in->policy > POL_DMDAP_BL) return ORC_EINVAL;
     if (pol_in->policy == POL_LEARNED && !mlp_w) return ORC_EINVAL;
-    /* unit_time only sets k_inc's default (P tasks per unit_time ns); <= 0
-     * selects the DAG's default unit time. */
+    /* unit_time is the unit time T the attributes were computed with; it sets
+     * k_inc's default, P tasks per T ns (<= 0 selects the DAG's default unit
+     * time). */
     if (unit_time <= 0) unit_time = orc_default_unit_time(n, c_gpu);
     orc_policy pol;
     orc_resolve_policy(pol_in, P, unit_time, &pol);

@@ -239,13 +239,36 @@ def insp_batch_timing(b, reset: bool = False):
     return ms, n
 
 
-INSP_NOALLOC_MAX_TASKS = 65536
+INSP_NOALLOC_MAX_TASKS = 65536  # include/inspirit.h; a CPU test keeps the two equal
+
+_NOALLOC_DTYPES = dict(row_ptr="int32", col_idx="int32", type="uint8", type_cost="int64", task_cost="int64",
+                       ia="int32", ie="int32", worker="int32", start="int64", end="int64", makespan="int64")
+
+
+def _check_noalloc_tensor(name, x):
+    """A raw pointer is taken from each array, so its dtype, layout and device are checked here."""
+    if x is None:
+        return
+    if not hasattr(x, "data_ptr"):
+        return  # host arrays are rejected by the library itself (INSP_EINVAL)
+    import torch
+    want = getattr(torch, _NOALLOC_DTYPES[name])
+    if x.dtype != want:
+        raise TypeError(f"{name} must be {want}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if x.is_cuda and x.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {x.device}, not on the current device cuda:{torch.cuda.current_device()}")
 
 
 def insp_simulate_noalloc(n, row_ptr, col_idx, type, n_types, type_cost, task_cost, n_cpu, n_gpu, xfer_ns,
                           policy, ia, ie, worker, start, end, makespan, stream=None) -> None:
     """The single-DAG simulation that allocates no device memory (all arrays
     must be device tensors the caller owns); see include/inspirit.h."""
+    for name, x in (("row_ptr", row_ptr), ("col_idx", col_idx), ("type", type), ("type_cost", type_cost),
+                    ("task_cost", task_cost), ("ia", ia), ("ie", ie), ("worker", worker), ("start", start),
+                    ("end", end), ("makespan", makespan)):
+        _check_noalloc_tensor(name, x)
     check(lib().insp_simulate_noalloc(n, ptr(row_ptr), ptr(col_idx), ptr(type), n_types, ptr(type_cost),
                                       ptr(task_cost), n_cpu, n_gpu, xfer_ns,
                                       None if policy is None else ctypes.byref(policy), ptr(ia), ptr(ie),

@@ -219,6 +219,9 @@ struct insp_batch {
     bool has_task_cost = false;
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;  // 32-source items (global efficiency sweep)
+    // per-DAG unit times of the last attributes call (device; the defaults before any): the
+    // simulation's default ascending slope k_inc is P tasks per this T
+    const int64_t *ut_attr = nullptr;
     int64_t n_items_pull = 0;                 // IE_PULL_SOURCES-source items (pull sweep)
     std::unique_ptr<Scratch> sc;
     int64_t ie_rec_stride = 0;
@@ -754,6 +757,7 @@ namespace {
 // caller's array (entries <= 0 take the default).  *wide: some T >= 2^31.
 int prep_unit_time(insp_batch *b, const int64_t *unit_time_ns, cudaStream_t s, const int64_t *&ut, bool &wide) {
     ut = b->unit_time_def.as<int64_t>();
+    b->ut_attr = ut;
     wide = b->max_unit_def >= 0x7fffffffLL;
     if (!unit_time_ns) return INSP_OK;
     if (is_device_ptr(unit_time_ns)) {
@@ -779,6 +783,7 @@ int prep_unit_time(insp_batch *b, const int64_t *unit_time_ns, cudaStream_t s, c
         if (b->ndag) CU(cudaStreamSynchronize(s));  // h is a local vector
     }
     ut = b->unit_time_user.as<int64_t>();
+    b->ut_attr = ut;
     return INSP_OK;
 }
 
@@ -914,7 +919,7 @@ void fill_sim_args(insp_batch *b, insp::SimArgs &A, const int32_t *d_ia, const i
     A.c = b->mach.pol.c;
     A.k_inc_tasks = b->mach.pol.k_inc_tasks;
     A.k_inc_ns = b->mach.pol.k_inc_ns;
-    A.unit_time_def = b->unit_time_def.as<int64_t>();
+    A.unit_time = b->ut_attr ? b->ut_attr : b->unit_time_def.as<int64_t>();
     A.indeg0 = b->indeg0.as<int32_t>();
     A.ia = d_ia;
     A.ie = d_ie;

@@ -83,14 +83,54 @@ int scratch_address(unsigned char **out) {
     return INSP_OK;
 }
 
-bool on_device(const void *p) {
-    if (!p) return false;
+// The driver's cuMemGetAddressRange (looked up through the runtime, so the library does not
+// link libcuda itself): base and size of the allocation that holds a device address.
+typedef int (*AddressRangeFn)(unsigned long long *base, size_t *size, unsigned long long ptr);
+AddressRangeFn address_range_fn() {
+    static AddressRangeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<AddressRangeFn>(f);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// A caller array must be device memory of the current device (or managed memory) whose
+// allocation holds at least `bytes` bytes from p on.  Without a staging copy, an array on
+// another GPU or a short one would otherwise reach the kernels, which would read or write
+// outside it.  Returns an empty string when the array is fine, else what is wrong.
+std::string check_array(const char *name, const void *p, size_t bytes) {
+    if (!p) return std::string(name) + " is NULL";
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return std::string(name) + " is not a device pointer";
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return std::string(name) + " is not a device pointer (every array must be a device pointer)";
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "cudaGetDevice failed";
+    }
+    if (a.type == cudaMemoryTypeDevice && a.device != dev)
+        return std::string(name) + " lives on device " + std::to_string(a.device) + ", not on the current device " +
+               std::to_string(dev);
+    AddressRangeFn fn = address_range_fn();
+    unsigned long long base = 0;
+    size_t size = 0;
+    const unsigned long long addr = reinterpret_cast<unsigned long long>(p);
+    if (!fn || fn(&base, &size, addr) != 0)
+        return std::string("cannot determine the extent of ") + name + " (cuMemGetAddressRange failed)";
+    if (addr < base || addr - base > size || size - (addr - base) < bytes)
+        return std::string(name) + " is shorter than the " + std::to_string(bytes) + " bytes it must hold";
+    return std::string();
 }
 
 #define NA_CU(call)                                                                              \
@@ -120,13 +160,24 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
         p.k_inc_ns < 0)
         return na_fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");
-    // every array must already live on the device: staging a host array would need an allocation
-    const void *need[] = {row_ptr, type, ia, ie, worker, start, end, makespan};
-    for (const void *q : need)
-        if (!on_device(q)) return na_fail(INSP_EINVAL, "every array must be a device pointer");
+    // every array must already live on the current device and be long enough: staging a host
+    // array would need an allocation, and nothing else stands between a short array and the kernels
     if (!type_cost && !task_cost) return na_fail(INSP_EINVAL, "need type_cost or task_cost");
-    if ((type_cost && !on_device(type_cost)) || (task_cost && !on_device(task_cost)))
-        return na_fail(INSP_EINVAL, "every array must be a device pointer");
+    const size_t N = size_t(n);
+    struct Need { const char *name; const void *p; size_t bytes; };
+    const Need need[] = {{"row_ptr", row_ptr, 4 * (N + 1)}, {"type", type, N},
+                         {"ia", ia, 4 * N}, {"ie", ie, 4 * N}, {"worker", worker, 4 * N},
+                         {"start", start, 8 * N}, {"end", end, 8 * N}, {"makespan", makespan, 8}};
+    for (const Need &q : need) {
+        if (q.bytes == 0 && q.p == nullptr) continue;
+        const std::string why = check_array(q.name, q.p, q.bytes);
+        if (!why.empty()) return na_fail(INSP_EINVAL, why);
+    }
+    {
+        const std::string why = task_cost ? check_array("task_cost", task_cost, 16 * N)
+                                          : check_array("type_cost", type_cost, 16 * size_t(n_types));
+        if (!why.empty()) return na_fail(INSP_EINVAL, why);
+    }
 
     unsigned char *S = nullptr;
     int rc = scratch_address(&S);
@@ -137,7 +188,10 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     NA_CU(cudaMemcpyAsync(&m, row_ptr + n, 4, cudaMemcpyDeviceToHost, s));
     NA_CU(cudaStreamSynchronize(s));
     if (m < 0) return na_fail(INSP_EINVAL, "row_ptr[n] < 0");
-    if (m > 0 && !on_device(col_idx)) return na_fail(INSP_EINVAL, "every array must be a device pointer");
+    if (m > 0) {
+        const std::string why = check_array("col_idx", col_idx, 4 * size_t(m));
+        if (!why.empty()) return na_fail(INSP_EINVAL, why);
+    }
 
     // header: bases of the one-DAG batch; status, span and in-degrees start at zero
     const int64_t hdr[4] = {0, n, 0, m};
@@ -181,7 +235,7 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     A.c = p.c;
     A.k_inc_tasks = p.k_inc_tasks;
     A.k_inc_ns = p.k_inc_ns;
-    A.unit_time_def = unit_time;
+    A.unit_time = unit_time;  // the default unit time: the attributes are taken to use it
     A.indeg0 = indeg0;
     A.ia = ia;
     A.ie = ie;
@@ -206,6 +260,8 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     NA_CU(cudaGetLastError());
     NA_CU(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));
     NA_CU(cudaStreamSynchronize(s));
-    if (st != INSP_OK) return na_fail(st, "a bounded device-side wait gave up");
+    if (st == INSP_ETIMEOUT) return na_fail(st, "a bounded device-side wait gave up");
+    if (st == INSP_ECHECK) return na_fail(st, "an internal bounds check of the debug build failed");
+    if (st != INSP_OK) return na_fail(st, "device-side error " + std::to_string(st));
     return INSP_OK;
 }

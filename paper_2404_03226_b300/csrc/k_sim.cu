@@ -225,14 +225,14 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         Pool<POOL_C> pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
         int32_t *nl_g = A.nl + tb;
 
-        // resolved policy parameters (zero = default for P workers and the DAG's default T)
+        // resolved policy parameters (zero = default for P workers and the attributes' unit time T)
         const int32_t tw = A.task_window > 0 ? A.task_window : P;
         const int32_t s_inc = A.s_inc > 0 ? A.s_inc : P;
         const int32_t s_dec = A.s_dec > 0 ? A.s_dec : P;
         const int32_t dec_step = A.dec_step > 0 ? A.dec_step : P;
         const int32_t cslack = A.c > 0 ? A.c : (P / 2 > 1 ? P / 2 : 1);
         const int64_t kt = A.k_inc_tasks > 0 ? A.k_inc_tasks : P;
-        const int64_t kns = A.k_inc_ns > 0 ? A.k_inc_ns : A.unit_time_def[d];
+        const int64_t kns = A.k_inc_ns > 0 ? A.k_inc_ns : A.unit_time[d];
         // static pick modes: DMDA (FIFO) and the DMDAP baselines; -1: the Nready controller decides
         const int32_t static_mode = A.policy == INSP_POLICY_FIFO       ? MODE_FIFO
                                     : A.policy == INSP_POLICY_DMDAP_IA ? MODE_ABILITY

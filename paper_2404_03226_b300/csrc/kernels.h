@@ -14,7 +14,7 @@ struct SimArgs {
     int64_t xfer;
     int32_t policy, task_window, s_inc, s_dec, dec_step, c;
     int64_t k_inc_tasks, k_inc_ns;
-    const int64_t *unit_time_def;  // per DAG default unit time (k_inc default)
+    const int64_t *unit_time;      // per DAG unit time T of the attributes (k_inc default: P tasks per T)
     const int32_t *indeg0;
     const int32_t *ia, *ie;
     int32_t *worker;

@@ -71,3 +71,32 @@ def edge_case_dags():
     eq = [(u, v) for u in range(60) for v in range(u + 1, min(60, u + 9)) if (u * 7 + v) % 3 == 0]
     D.append(inputs.make_dag(60, eq, [10] * 60, [10] * 60))  # equal costs: many simultaneous events
     return D
+
+
+def oracle_many(batch, idx, machine, policy="inspirit", unit_time=None, mlp_weights=None, threads=None):
+    """Oracle results of the listed DAGs on a thread pool over the host cores
+    (the oracle's C calls release the interpreter lock); unit_time is None, an
+    int, or a per-DAG array."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    pol = oracle.Policy({"inspirit": oracle.POLICY_INSPIRIT, "fifo": oracle.POLICY_FIFO,
+                         "learned": oracle.POLICY_LEARNED, "dmdap_ia": oracle.POLICY_DMDAP_IA,
+                         "dmdap_bl": oracle.POLICY_DMDAP_BL}[policy])
+
+    def one(d):
+        T = None if unit_time is None else int(np.asarray(unit_time).reshape(-1)[d] if np.ndim(unit_time) else unit_time)
+        return oracle.simulate(batch.dag(int(d)), machine, pol, unit_time=T, mlp_weights=mlp_weights)
+
+    with ThreadPoolExecutor(threads or os.cpu_count() or 1) as ex:
+        return dict(zip([int(d) for d in idx], ex.map(one, idx)))
+
+
+def compare_many(batch, gpu, machine, results, with_attributes=True):
+    """Element-by-element equality of every DAG in `results` (from oracle_many)."""
+    for d, r in results.items():
+        tb, te = int(batch.task_base[d]), int(batch.task_base[d + 1])
+        assert r["rc"] == 0, f"oracle rc of DAG {d}"
+        keys = ("ia", "ie", "worker", "start", "end") if with_attributes else ("worker", "start", "end")
+        for k in keys:
+            np.testing.assert_array_equal(gpu[k][tb:te], r[k], err_msg=f"{k} of DAG {d}")
+        assert int(gpu["makespan"][d]) == r["makespan"], f"makespan of DAG {d}"

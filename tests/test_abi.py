@@ -50,3 +50,17 @@ def test_machine_argument_errors_without_gpu():
         _lib.insp_machine_create(1, 1, -5)
     h = _lib.insp_machine_create(8, 2, 20000)
     _lib.insp_machine_destroy(h)
+
+
+def test_binding_constants_match_the_header():
+    """Constants the binding copies from include/inspirit.h stay equal to it."""
+    from paper_2404_03226_b300 import _lib
+    hdr = open(os.path.join(ROOT, "include", "inspirit.h")).read()
+    defs = dict(re.findall(r"#define\s+(INSP_[A-Z_0-9]+)\s+(-?\d+)", hdr))
+    assert int(defs["INSP_NOALLOC_MAX_TASKS"]) == _lib.INSP_NOALLOC_MAX_TASKS
+    for name in ("INSP_OK", "INSP_EINVAL", "INSP_ENOTTOPO", "INSP_ENOMEM", "INSP_ECUDA", "INSP_ETIMEOUT",
+                 "INSP_EOVERFLOW", "INSP_POLICY_INSPIRIT", "INSP_POLICY_FIFO", "INSP_POLICY_LEARNED",
+                 "INSP_POLICY_DMDAP_IA", "INSP_POLICY_DMDAP_BL"):
+        assert int(defs[name]) == getattr(_lib, name), name
+    for code, name in _lib.ERROR_NAMES.items():
+        assert int(defs[name]) == code, name

@@ -22,6 +22,19 @@ def test_algorithmic_bytes_follow_the_stated_formula():
     assert a["k_sim"] == csr + n + 4 * n + 8 * n + 20 * n + 8 * nd
 
 
+def test_path_bytes_count_each_input_and_output_once():
+    """Per task 4 + 4 x out-degree + 1 + 8 + 20 bytes, per DAG 4 + 8 + the cost table; on the
+    headline workload's shape that is about 109 bytes per task."""
+    b = inputs.layered(6, cfg=2, n_max=300)
+    n, m, nd = b.n_total, b.m_total, b.ndag
+    assert bench.path_bytes(b) == 33 * n + 4 * m + 12 * nd + 16 * nd * b.n_types
+    t = inputs.tiled(inputs.KIND_CHOLESKY, 8, 2)
+    assert bench.path_bytes(t) == 33 * t.n_total + 4 * t.m_total + 12 * t.ndag + 16 * t.n_total
+    big = inputs.layered4096(256)
+    per_task = bench.path_bytes(big) / big.n_total
+    assert 100 < per_task < 120
+
+
 def _fake_root(tmp_path, src_text, sha):
     (tmp_path / "profiles").mkdir()
     d = tmp_path / "paper_2404_03226_b300" / "csrc"

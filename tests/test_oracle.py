@@ -134,7 +134,10 @@ def test_simulation_hand_traced():
         d = inputs.make_dag(case["n"], case["edges"], case["c_cpu"], case["c_gpu"])
         m = inputs.Machine(*case["machine"])
         for pname in case["policies"]:
-            r = oracle.simulate(d, m, _policy(pname), trace=True)
+            pol = _policy(pname)
+            for k, v in case.get("policy_params", {}).items():
+                setattr(pol, k, v)
+            r = oracle.simulate(d, m, pol, unit_time=case.get("unit_time"), trace=True)
             assert r["rc"] == 0
             assert list(r["worker"]) == case["worker"], (case["name"], pname)
             assert list(r["start"]) == case["start"], (case["name"], pname)
@@ -195,16 +198,26 @@ def test_random_schedules_valid_and_bounded(seed):
         assert r["makespan"] >= _lower_bound(d, m)
 
 
-@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("seed", range(12))
 def test_exhaustive_optimum(seed):
-    """makespan >= exact optimum >= lower bound on DAGs of at most 8 tasks."""
+    """makespan >= exact optimum >= lower bound on DAGs of 2 to 10 tasks (seeds 8-11: 9 or 10 tasks)."""
     rng = np.random.default_rng(2000 + seed)
-    d = _rand_dag(rng, int(rng.integers(2, 9)), 0.3, cmax=30)
+    n = int(rng.integers(2, 9)) if seed < 8 else int(rng.integers(9, 11))
+    d = _rand_dag(rng, n, 0.3, cmax=30)
     m = inputs.Machine(int(rng.integers(1, 3)), 1, int(rng.integers(0, 10)))
     best = oracle.optimum(d, m)
     assert best >= _lower_bound(d, m)
-    for pol in ("inspirit", "fifo"):
+    for pol in ("inspirit", "fifo", "dmdap_ia", "dmdap_bl"):
         assert oracle.simulate(d, m, _policy(pol))["makespan"] >= best
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_optimum_matches_listing_every_schedule(seed):
+    """The branch and bound equals a plain listing of every assignment and topological order (<= 6 tasks)."""
+    rng = np.random.default_rng(2100 + seed)
+    d = _rand_dag(rng, int(rng.integers(2, 7)), 0.35, cmax=20)
+    m = inputs.Machine(int(rng.integers(1, 3)), int(rng.integers(0, 2)), int(rng.integers(0, 12)))
+    assert oracle.optimum(d, m) == brute.optimum(d, m)
 
 
 def test_optimum_known_cases():

@@ -4,6 +4,7 @@ quantisation is the identity, and a closed form of AdamW."""
 import numpy as np
 import pytest
 
+import inputs
 import oracle
 
 
@@ -79,3 +80,21 @@ def test_adamw_constant_gradient_closed_form():
     for t in range(1, 4):
         oracle.adamw(w2, m2, v2, np.zeros(1), t, 0.1, wd=0.5)
     assert w2[0] == pytest.approx(2.0 * 0.95 ** 3)
+
+
+def test_features_hand_computed():
+    """The 16 scorer features of the candidates at two pops, each value computed by hand."""
+    import json
+    import os
+    gold = os.path.join(os.path.dirname(__file__), "golden")
+    g = json.load(open(os.path.join(gold, "features_hand_computed.json")))
+    case = [c for c in json.load(open(os.path.join(gold, "sim_hand_traced.json")))["cases"] if c["name"] == g["dag"]][0]
+    d = inputs.make_dag(case["n"], case["edges"], case["c_cpu"], case["c_gpu"])
+    m = inputs.Machine(*case["machine"])
+    for pop in g["pops"]:
+        pol = oracle.Policy(oracle.POLICY_INSPIRIT)
+        for k, v in case["policy_params"].items():
+            setattr(pol, k, v)
+        r = oracle.simulate(d, m, pol, unit_time=pop["unit_time"] or None, feat_pop=pop["pop"], feat_cap=8)
+        assert list(r["feat_task"]) == pop["tasks"], pop["_why"]
+        np.testing.assert_array_equal(r["feat"], np.array(pop["features"]), err_msg=pop["_why"])
