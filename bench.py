@@ -53,6 +53,14 @@ def make_workload(args, rank):
         desc = (f"tiled Cholesky / LU / QR DAGs at {args.tiles} tiles x {args.instances} instances each, "
                 f"per-task costs perturbed +-20 % from seed, 16 CPU + 4 GPU workers, 20 us transfer, INSPIRIT policy")
         return b, inputs.MACHINE_TILED, desc, "16 CPU + 4 GPU workers, xfer 20000 ns"
+    if args.workload == "mixed":
+        b = inputs.mixed_workload(args.mixed_ndag, with_large=not args.no_large)
+        desc = (f"mixed-size stress: {args.mixed_ndag} DAGs with task counts log-uniform in [100, 200000], random "
+                f"layered (the layered workload's shape) and tiled Cholesky / LU / QR (largest tile count within the "
+                f"drawn size) alternating 1:1" + ("" if args.no_large else ", plus one 1,000,000-task layered DAG "
+                f"(layers of 256, edge probability 0.05, span U{{1,2,3}})") +
+                ", per-task costs, 32 CPU + 8 GPU workers, 20 us transfer, INSPIRIT policy")
+        return b, inputs.MACHINE_MIXED, desc, "32 CPU + 8 GPU workers, xfer 20000 ns"
     raise ValueError(args.workload)
 
 
@@ -211,12 +219,16 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def first_dags(batch, budget_tasks: int):
-    """The first DAGs of the workload holding about budget_tasks tasks."""
+def first_dags(batch, budget_tasks: int, max_n: int | None = None):
+    """The first DAGs of the workload (of at most max_n tasks each, if given) holding about
+    budget_tasks tasks."""
     idx, tasks = [], 0
     for d in range(batch.ndag):
+        n = int(batch.task_base[d + 1] - batch.task_base[d])
+        if max_n is not None and n > max_n:
+            continue
         idx.append(d)
-        tasks += int(batch.task_base[d + 1] - batch.task_base[d])
+        tasks += n
         if tasks >= budget_tasks:
             break
     return idx, tasks
@@ -235,24 +247,26 @@ def run_oracle(dags, machine, threads: int) -> None:
         assert all(rc == 0 for rc in ex.map(lambda g: oracle.simulate(g, machine)["rc"], dags))
 
 
-def cpu_baseline(batch, machine, per_core_tasks=100000):
-    """The oracle, as it stands, on the first DAGs of the workload: once on one core, and on
-    every host core (DAGs spread over threads)."""
+def cpu_baseline(batch, machine, per_core_tasks=100000, max_n=None):
+    """The oracle, as it stands, on the first DAGs of the workload (of at most max_n tasks each:
+    its exact inspiring ability grows with n^2): once on one core, and on every host core (DAGs
+    spread over threads)."""
     import oracle
-    oracle.simulate(batch.dag(0), machine)  # load the library before the threads start
-    idx1, t1 = first_dags(batch, per_core_tasks)
+    idx1, t1 = first_dags(batch, per_core_tasks, max_n)
+    oracle.simulate(batch.dag(idx1[0]), machine)  # load the library before the threads start
     dags1 = [batch.dag(d) for d in idx1]
     s0 = time.perf_counter()
     run_oracle(dags1, machine, 1)
     dt1 = time.perf_counter() - s0
     cores = host_cores()
-    idx, tasks = first_dags(batch, per_core_tasks * cores)
+    idx, tasks = first_dags(batch, per_core_tasks * cores, max_n)
     dags = [batch.dag(d) for d in idx]
     s0 = time.perf_counter()
     run_oracle(dags, machine, cores)
     dt = time.perf_counter() - s0
+    which = "DAGs" if max_n is None else f"DAGs of at most {max_n} tasks"
     return {"value": tasks / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {len(idx)} DAGs of the workload ({tasks} tasks), attributes + simulation, "
+            "sample": f"first {len(idx)} {which} of the workload ({tasks} tasks), attributes + simulation, "
                       f"{dt:.1f} s on {cores} threads (one DAG per oracle call)",
             "single_core": {"value": t1 / dt1, "unit": UNIT, "cores": 1,
                             "sample": f"first {len(idx1)} DAGs ({t1} tasks), {dt1:.1f} s"}}
@@ -342,6 +356,47 @@ def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5)
     return out
 
 
+# DAGs of at most this many tasks make up the CPU-baseline and per-DAG-launch samples (the
+# oracle's exact inspiring ability grows with n^2; the mixed-size workload reaches 1,000,000)
+SAMPLE_MAX_N = 20000
+
+
+def learned_leg(batch, mach, t_struct, mk_plain, dev, steps=3):
+    """The learned proposal scorer (shipped weights) beside the plain INSPIRIT priority on the
+    same batch, same tuning: evaluation-step throughput and mean makespans."""
+    import torch
+
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib, scorer
+    bits, shipped = scorer.load_trained()
+    pol = P.insp_policy()
+    pol.policy = P.INSP_POLICY_LEARNED
+    m = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns, pol)
+    _lib.insp_set_scorer(m.handle, bits)
+    bb = P.DagBatch(m, batch)
+    _lib.insp_batch_set_tuning(bb.handle, t_struct)
+    n, nd = batch.n_total, batch.ndag
+    bufs = [torch.empty(n, dtype=t, device=dev) for t in (torch.int32, torch.int32, torch.int32, torch.int64,
+                                                           torch.int64)] + [torch.empty(nd, dtype=torch.int64,
+                                                                                        device=dev)]
+    stream = torch.cuda.current_stream(dev)
+    _lib.insp_evaluate_batch(bb.handle, None, *bufs, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        _lib.insp_evaluate_batch(bb.handle, None, *bufs, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if _lib.insp_batch_status(bb.handle) != 0:
+        raise RuntimeError("learned policy: device-side status not OK: " + _lib.last_error())
+    t = e0.elapsed_time(e1) / 1e3 / steps
+    plain = float(mk_plain.double().mean())
+    lm = float(bufs[5].double().mean())
+    return {"value": n / t, "unit": UNIT, "ms_per_step": t * 1e3, "mean_makespan_ns": lm,
+            "mean_makespan_ns_plain": plain, "gain_pct_vs_plain": (plain - lm) / plain * 100.0,
+            "policy_shipped": shipped}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -379,7 +434,7 @@ def run_ours(args, rank, world, local_rank):
     if args.tuning:  # explicit launch shapes (profiling captures)
         _lib.insp_batch_set_tuning(b.handle, _lib.insp_tuning(**json.loads(args.tuning)))
         t_struct = _lib.insp_batch_get_tuning(b.handle)
-    elif args.autotune:
+    elif args.autotune and args.workload != "mixed":  # (the mixed batch's steps take seconds each)
         t_struct = _lib.insp_batch_autotune(b.handle, stream)
     else:
         t_struct = _lib.insp_batch_get_tuning(b.handle)
@@ -485,7 +540,9 @@ def run_ours(args, rank, world, local_rank):
     per_dag = None
     if rank == 0 and not args.profile:
         k_sample = 64
-        sub = batch.subset(range(k_sample))
+        small = [d for d in range(batch.ndag) if batch.task_base[d + 1] - batch.task_base[d] <= SAMPLE_MAX_N]
+        sub = batch.subset(small[:k_sample])
+        k_sample = sub.ndag
         dags, outs = [], []
         for d in range(k_sample):
             g = sub.dag(d)
@@ -622,7 +679,11 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.profile and not args.no_policies:
         policies = compare_policies(args, batch, mach, t_struct, b, mk, dev)
 
-    cb = cpu_baseline(batch, mach) if (rank == 0 and world == 1 and not args.profile) else None
+    learned = None
+    if rank == 0 and not args.profile and not args.no_learned:
+        learned = learned_leg(batch, mach, t_struct, mk, dev)
+
+    cb = cpu_baseline(batch, mach, max_n=SAMPLE_MAX_N) if (rank == 0 and world == 1 and not args.profile) else None
 
     if rank == 0:
         res = {
@@ -631,11 +692,13 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": wdesc, "ndag": ndag, "tasks": n, "edges": int(batch.m_total),
                        "machine": mdesc, "policy": "INSPIRIT (defaults)",
-                       "tuning": dict(tuning, autotuned=bool(args.autotune and not args.tuning)),
+                       "tuning": dict(tuning, autotuned=bool(args.autotune and not args.tuning
+                                                             and args.workload != "mixed")),
                        "l2": f"inputs larger than L2 ({(4 * (n + ndag) + 4 * batch.m_total + n) / 1e6:.0f} MB of CSR "
                              f"resident, 126 MB L2)", "parallelism": f"dp{world}" if world > 1 else "single GPU"},
             "per_dag_form": per_dag,
             "policies": policies,
+            "learned": learned,
             "cuda_graph": graph,
             "e2e": e2e,
             "roofline": roofline,
@@ -662,17 +725,25 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ndag", type=int, default=4096, help="first K DAGs of the workload (profiling captures)")
-    ap.add_argument("--workload", choices=["layered", "layered_degree", "tiled"], default="layered",
-                    help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches")
+    ap.add_argument("--workload", choices=["layered", "layered_degree", "tiled", "mixed"], default="layered",
+                    help="layered: the 4096-DAG headline workload; tiled: Cholesky/LU/QR batches; mixed: the "
+                         "mixed-size stress batch")
+    ap.add_argument("--mixed-ndag", dest="mixed_ndag", type=int, default=10000,
+                    help="DAGs of the mixed-size workload (before the 1M-task DAG)")
+    ap.add_argument("--no-large", dest="no_large", action="store_true",
+                    help="mixed workload without the 1,000,000-task DAG")
     ap.add_argument("--tiles", default="16,32", help="tile counts of the tiled workload")
     ap.add_argument("--instances", type=int, default=256, help="instances per (kind, tiles) of the tiled workload")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the library's default launch shapes instead of autotuning them on the batch")
     ap.add_argument("--tuning", default=None,
                     help='explicit tuning as JSON, e.g. \'{"groups": 1, "attr_overlap": 0, "ia_warps": 32, '
-                         '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64, "group_split": 0}\'')
+                         '"ie_warps": 16, "ie_ring_mb": 512, "sim_warps": 4, "sim_queue": 64, "group_split": 0, '
+                         '"ia_block": 0}\'')
     ap.add_argument("--no-policies", dest="no_policies", action="store_true",
                     help="skip the DMDA / DMDAP baselines and the unit-time search leg")
+    ap.add_argument("--no-learned", dest="no_learned", action="store_true",
+                    help="skip the learned-scorer leg beside the plain policy")
     ap.add_argument("--profile", action="store_true",
                     help="only the timed steps: no per-DAG form, e2e or CPU baseline (for ncu captures)")
     args = ap.parse_args()

@@ -331,6 +331,10 @@ typedef struct {
                               learned scorer): a simulation whose CTA does not fit fails with INSP_EINVAL */
     int32_t group_split;   /* 0: groups of equal DAG counts; 1: geometric, each group 4x the DAGs of the
                               one before (the largest DAGs, whose simulations take longest, start first) */
+    int32_t ia_block;      /* ability sweep: 0: DAGs of up to 16384 tasks keep one bitset row of n bits per task
+                              in one CTA (n x n bits), larger ones are cut into target blocks; 1: every DAG
+                              is cut into blocks of 2048 target ids, one CTA per (DAG, block), rows in a ring
+                              of (longest edge span + warps) slots per CTA, so memory does not grow with n */
 } insp_tuning;
 
 /* Time a fixed candidate set of tunings on this batch (the fastest of three

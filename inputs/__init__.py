@@ -96,6 +96,11 @@ def _load():
         lib.insg_free.argtypes = [ctypes.POINTER(_CBatch)]
         lib.insg_tiled_count.restype = ctypes.c_int64
         lib.insg_tiled_count.argtypes = [ctypes.c_int32, ctypes.c_int32]
+        lib.insg_mixed.restype = ctypes.POINTER(_CBatch)
+        lib.insg_mixed.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.POINTER(_LayeredParams), ctypes.POINTER(ctypes.c_int64)]
+        lib.insg_mixed_sizes.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
         lib.insg_dag_seed.restype = ctypes.c_uint64
         lib.insg_dag_seed.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64]
         _lib = lib
@@ -219,6 +224,36 @@ def tiled(kind: int, N: int, ndag: int = 1, cfg: int = 3, first: int = 0, *, per
     return _from_c(ptr)
 
 
+def mixed(ndag: int, cfg: int = 5, first: int = 0, *, n_lo: int = 100, n_hi: int = 200000,
+          base_seed=BASE_SEED) -> Batch:
+    """The mixed-size stress workload: task counts log-uniform in [n_lo, n_hi]; even DAG indices
+    random layered DAGs (the 4096-DAG workload's shape, 8 types), odd ones tiled Cholesky / LU /
+    QR DAGs of the largest tile count within the drawn size, per-task costs (+-20 % on the
+    tiled ones)."""
+    p = _LayeredParams(0, 0, 4, 64, 0.1, 0.5, 1, 3, 8, float(100 * US), 1.0, 0.5, 20.0, 0)
+    bc = np.zeros((3, 4, 2), np.int64)
+    for k, tab in TILED_COST.items():
+        bc[k, :tab.shape[0]] = tab
+    bc = np.ascontiguousarray(bc)
+    return _from_c(_load().insg_mixed(base_seed, cfg, first, ndag, n_lo, n_hi, ctypes.byref(p),
+                                      bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+
+
+def mixed_sizes(ndag: int, cfg: int = 5, first: int = 0, *, n_lo: int = 100, n_hi: int = 200000,
+                base_seed=BASE_SEED) -> np.ndarray:
+    """The task counts mixed() draws (tiled DAGs round them down to a whole tile count)."""
+    out = np.zeros(max(ndag, 1), np.int64)
+    _load().insg_mixed_sizes(base_seed, cfg, first, ndag, n_lo, n_hi, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    return out[:ndag]
+
+
+def layered_1m(n: int = 1_000_000, cfg: int = 6, base_seed=BASE_SEED) -> Batch:
+    """The one large layered DAG of the mixed-size stress workload: n tasks in layers of 256,
+    edge probability 0.05 to the next U{1,2,3} layers, 8 types, log-normal costs."""
+    return layered(1, cfg=cfg, n_min=n, n_max=n, w_min=256, w_max=256, p_min=0.05, p_max=0.05,
+                   base_seed=base_seed)
+
+
 def tiled_count(kind: int, N: int) -> int:
     return int(_load().insg_tiled_count(kind, N))
 
@@ -246,6 +281,33 @@ def concat(batches: list[Batch]) -> Batch:
     return concat_dags(dags)
 
 
+def concat_batches(batches: list[Batch]) -> Batch:
+    """Concatenate whole batches (per-DAG local row offsets and successor ids stay as they are);
+    costs become per task."""
+    nt = max(b.n_types for b in batches)
+    tb = [np.zeros(1, np.int64)]
+    eb = [np.zeros(1, np.int64)]
+    n0 = m0 = 0
+    costs = []
+    tcs = []
+    for b in batches:
+        tb.append(b.task_base[1:] + n0)
+        eb.append(b.edge_base[1:] + m0)
+        n0 += b.n_total
+        m0 += b.m_total
+        if b.task_cost is not None:
+            costs.append(np.asarray(b.task_cost, np.int64))
+        else:
+            d_of = np.repeat(np.arange(b.ndag), np.diff(b.task_base))
+            costs.append(b.type_cost[d_of, b.type.astype(np.int64)])
+        tc = np.ones((b.ndag, nt, 2), np.int64)
+        tc[:, :b.n_types] = b.type_cost
+        tcs.append(tc)
+    return Batch(sum(b.ndag for b in batches), nt, np.concatenate(tb), np.concatenate(eb),
+                 np.concatenate([b.row_ptr for b in batches]), np.concatenate([b.col_idx for b in batches]),
+                 np.concatenate([b.type for b in batches]), np.concatenate(tcs), np.concatenate(costs))
+
+
 def make_dag(n: int, edges, c_cpu, c_gpu, type=None) -> Dag:
     """A small DAG from an edge list (u, v) with u < v (tests and examples)."""
     rows = [[] for _ in range(n)]
@@ -267,6 +329,15 @@ MACHINE_CHOLESKY8 = Machine(4, 1, 20 * US)
 MACHINE_LAYERED = Machine(8, 2, 20 * US)
 MACHINE_TILED = Machine(16, 4, 20 * US)
 MACHINE_MIXED = Machine(32, 8, 20 * US)
+
+
+def mixed_workload(ndag: int = 10000, with_large: bool = True) -> Batch:
+    """The mixed-size stress batch: `ndag` DAGs of mixed() and, with_large, the 1M-task layered
+    DAG after them (all with per-task costs)."""
+    parts = [mixed(ndag)]
+    if with_large:
+        parts.append(layered_1m())
+    return concat_batches(parts) if len(parts) > 1 else parts[0]
 
 
 def cholesky8() -> Batch:

@@ -501,3 +501,72 @@ EXPORT insg_batch *insg_concat(insg_batch *const *parts, int32_t nparts) {
     free(D);
     return R;
 }
+
+/* The mixed-size stress workload: DAG i (i = first .. first+ndag-1) draws from its own stream a
+ * task count n* = round(exp(U[ln n_lo, ln n_hi))) (log-uniform); even i give a random layered
+ * DAG of exactly n* tasks (shape parameters P, its n range ignored), odd i a tiled Cholesky, LU
+ * or QR DAG (kind uniform) of the largest tile count whose task count is at most n* (at least
+ * one tile).  Costs are per task: a layered task's from its DAG's type table, a tiled task's
+ * from base_cost[kind][type] scaled by (800000 + r mod 400001) / 1e6 as in insg_tiled.  Draw
+ * order per DAG: n*, then (tiled) kind, then the generator's own draws from a second stream
+ * seeded by the DAG's seed plus one. */
+EXPORT insg_batch *insg_mixed(uint64_t base, uint32_t cfg, uint64_t first, int32_t ndag, int64_t n_lo, int64_t n_hi,
+                              const insg_layered_params *P, const int64_t *base_cost /* [3][4][2] */) {
+    if (ndag < 0 || n_lo < 1 || n_hi < n_lo || n_hi > (1 << 24) - 1 || P->n_types < 1 || P->n_types > 16 ||
+        P->typing != 0)
+        return NULL;
+    one_dag *D = (one_dag *)calloc((size_t)ndag + 1, sizeof(one_dag));
+    if (!D) return NULL;
+    int fail = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : fail)
+    for (int32_t i = 0; i < ndag; ++i) {
+        uint64_t seed = insg_dag_seed(base, cfg, first + (uint64_t)i);
+        uint64_t s = seed;
+        double ln = log((double)n_lo) + (log((double)n_hi) - log((double)n_lo)) * u01(&s);
+        int64_t want = (int64_t)llround(exp(ln));
+        if (want < n_lo) want = n_lo;
+        if (want > n_hi) want = n_hi;
+        one_dag *d = &D[i];
+        if (((first + (uint64_t)i) & 1u) == 0) {
+            insg_layered_params Q = *P;
+            Q.n_min = Q.n_max = (int32_t)want;
+            if (gen_layered_one(seed + 1, &Q, d)) { fail = 1; continue; }
+            d->task_cost = (int64_t *)malloc(sizeof(int64_t) * (size_t)d->n * 2 + 8);
+            if (!d->task_cost) { fail = 1; continue; }
+            for (int32_t t = 0; t < d->n; ++t)
+                for (int c = 0; c < 2; ++c) d->task_cost[2 * t + c] = d->type_cost[2 * d->type[t] + c];
+        } else {
+            int32_t kind = (int32_t)urange(&s, 0, 2);
+            int32_t N = 1;
+            while (insg_tiled_count(kind, N + 1) <= want) ++N;
+            if (gen_tiled_one(kind, N, d, NULL)) { fail = 1; continue; }
+            uint64_t r = seed + 1;
+            d->task_cost = (int64_t *)malloc(sizeof(int64_t) * (size_t)d->n * 2 + 8);
+            if (!d->task_cost) { fail = 1; continue; }
+            const int64_t *bc = base_cost + (size_t)kind * 8;
+            for (int32_t t = 0; t < d->n; ++t) {
+                int64_t f = 800000 + (int64_t)(sm64_next(&r) % 400001u);
+                for (int c = 0; c < 2; ++c) {
+                    int64_t v = bc[2 * d->type[t] + c] * f / 1000000;
+                    d->task_cost[2 * t + c] = v < 1 ? 1 : v;
+                }
+            }
+            for (int32_t k = 0; k < 16; ++k) { d->type_cost[2 * k] = 1; d->type_cost[2 * k + 1] = 1; }
+        }
+    }
+    insg_batch *B = fail ? NULL : concat(D, ndag, P->n_types, 1, 1);
+    for (int32_t i = 0; i < ndag; ++i) one_free(&D[i]);
+    free(D);
+    return B;
+}
+
+/* The task count insg_mixed draws for DAG i (before tiling rounds it down): n*[i - first]. */
+EXPORT void insg_mixed_sizes(uint64_t base, uint32_t cfg, uint64_t first, int32_t ndag, int64_t n_lo, int64_t n_hi,
+                             int64_t *out) {
+    for (int32_t i = 0; i < ndag; ++i) {
+        uint64_t s = insg_dag_seed(base, cfg, first + (uint64_t)i);
+        double ln = log((double)n_lo) + (log((double)n_hi) - log((double)n_lo)) * u01(&s);
+        int64_t want = (int64_t)llround(exp(ln));
+        out[i] = want < n_lo ? n_lo : (want > n_hi ? n_hi : want);
+    }
+}

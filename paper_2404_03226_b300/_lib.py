@@ -25,7 +25,8 @@ class insp_policy(ctypes.Structure):
 
 class insp_tuning(ctypes.Structure):
     _fields_ = [("groups", _i32), ("attr_overlap", _i32), ("ia_warps", _i32), ("ie_warps", _i32),
-                ("ie_ring_mb", _i32), ("sim_warps", _i32), ("sim_queue", _i32), ("group_split", _i32)]
+                ("ie_ring_mb", _i32), ("sim_warps", _i32), ("sim_queue", _i32), ("group_split", _i32),
+                ("ia_block", _i32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

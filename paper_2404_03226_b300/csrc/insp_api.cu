@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "kernels.h"
@@ -96,8 +97,11 @@ int device_info(DeviceInfo &di) {
 constexpr int MAX_GROUPS = 16;
 // The tuning a batch starts with: what the autotuner picks on the 4096-DAG layered workload
 // (one group, overlapped attribute sweeps, 4-warp efficiency CTAs with a 1 GB ring budget,
-// 2-warp simulation CTAs with 32-entry pools).
-const insp_tuning kDefaultTuning = {1, 1, 16, 4, 1024, 2, 32, 0};
+// 2-warp simulation CTAs with 32-entry pools, whole-DAG bitsets for the ability sweep).
+const insp_tuning kDefaultTuning = {1, 1, 16, 4, 1024, 2, 32, 0, 0};
+// Largest DAG whose inspiring ability takes whole-DAG bitset rows (n x n bits in one CTA slot)
+// when the tuning's ia_block is 0; larger DAGs always take the target-block sweep.
+constexpr int32_t IA_FULL_MAX = 16384;
 
 bool tuning_ok(const insp_tuning &t) {
     return t.groups >= 1 && t.groups <= MAX_GROUPS && (t.attr_overlap == 0 || t.attr_overlap == 1) &&
@@ -106,7 +110,7 @@ bool tuning_ok(const insp_tuning &t) {
            t.sim_warps >= 1 && t.sim_warps <= insp::sim_max_warps() &&
            (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128 || t.sim_queue == 256 ||
             t.sim_queue == 512 || t.sim_queue == 1024) &&
-           (t.group_split == 0 || t.group_split == 1);
+           (t.group_split == 0 || t.group_split == 1) && (t.ia_block == 0 || t.ia_block == 1);
 }
 
 // First DAG rank of size group g of G (g = G: ndag), equal DAG counts or geometric (group g
@@ -127,7 +131,8 @@ int group_begin(int g, int G, int ndag, int split) {
 // API reuses device memory instead of allocating it again.
 struct Scratch {
     DBuf st_a, st_b, p_idw, p_seq, p_ia, p_ie, p_dr, p_cost, nl;  // simulation
-    DBuf ia_bits, ia_done;                                         // inspiring ability
+    DBuf ia_bits, ia_done;                                         // inspiring ability, whole-DAG rows
+    DBuf ia_ring, ia_flags, ia_seq;                                // inspiring ability, target blocks
     DBuf ie_rec, ie_acc;                                           // inspiring efficiency
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
     DBuf ie_ring;  // per-warp window rings of the pull efficiency sweep (global, meant to stay in L2)
@@ -170,6 +175,9 @@ struct BatchBufs {
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters, dag_span;
     DBuf pr_ptr, pcol, cursor;
     DBuf item_dag, item_dag_lpt, item_base_lpt;
+    // inspiring-ability plan: DAGs of the whole-row sweep, work items and zeroed DAGs of the
+    // target-block sweep, {dag, representative} pairs of repeated structures; fingerprints
+    DBuf ia_small_order, ia_items, ia_blk_dags, ia_pairs, dag_hash;
     // The load's own non-blocking stream: a load orders its copies and kernels on it and waits
     // for it alone, so it can run while other batches evaluate on other streams.
     cudaStream_t ls = nullptr;
@@ -229,6 +237,17 @@ struct insp_batch {
     insp_tuning tun = kDefaultTuning;
     int64_t ia_slot = 1;  // 64-bit bitset words per CTA slot of the ability sweep
     int grid_ia = 0;
+    // The inspiring-ability plan (build_ia_plan).  IA depends only on a DAG's structure, so DAGs
+    // whose tasks and successor lists equal an earlier DAG's (found at load by fingerprint, then
+    // compared exactly) take their representative's IA.  Representatives of up to IA_FULL_MAX
+    // tasks take the whole-row sweep unless the tuning asks for target blocks; the rest are cut
+    // into target blocks.  Per size rank r, prefix counts of the entries of each list.
+    std::vector<int32_t> h_ia_rep, h_dag_span;
+    bool ia_dups = false;
+    std::vector<int32_t> h_rank_small, h_rank_blk, h_rank_blkdag;
+    int32_t ia_n_pairs = 0, ia_small_max_n = 0, ia_blk_max_span = 0;
+    int32_t ia_ring_rows = 0;  // ring slots per CTA of the target-block sweep
+    int grid_ia_blk = 0;
     bool ie_global_ready = false;
     int grid_ie = 1;
     cudaStream_t last_stream = nullptr;
@@ -281,20 +300,136 @@ int copy_in(DBuf &dst, const void *src, size_t bytes, cudaStream_t s) {
 
 int alloc_ie_global(insp_batch *b);
 
-// Inspiring-ability scratch for the current tuning: one bitset slot per CTA,
-// sized by the largest DAG (rows of n tasks x ceil(n/32) words).
+// Longest edge span of every DAG (host copy) and the representative of every DAG's structure:
+// DAGs with equal fingerprints, task counts and edge counts are compared exactly on the device,
+// and a DAG equal to an earlier one takes that one as its representative.
+int find_repeated_structures(insp_batch *b, cudaStream_t s) {
+    const int32_t nd = b->ndag;
+    b->h_ia_rep.resize(nd);
+    b->h_dag_span.assign(nd, 0);
+    for (int d = 0; d < nd; ++d) b->h_ia_rep[d] = d;
+    if (nd == 0) return INSP_OK;
+    DeviceInfo di;
+    int rc = device_info(di);
+    if (rc) return rc;
+    DBuf &hash = b->bufs->dag_hash;
+    if ((rc = hash.alloc(size_t(nd) * 8))) return rc;
+    insp::launch_dag_hash(b->dev(), hash.as<unsigned long long>(), std::min(nd, di.sms * 8), s);
+    std::vector<unsigned long long> h(nd);
+    CU(cudaMemcpyAsync(h.data(), hash.p, size_t(nd) * 8, cudaMemcpyDeviceToHost, s));
+    CU(cudaMemcpyAsync(b->h_dag_span.data(), b->dag_span.p, size_t(nd) * 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    std::vector<int32_t> idx(nd);
+    for (int d = 0; d < nd; ++d) idx[d] = d;
+    auto key = [&](int d) {
+        return std::make_tuple(h[d], b->h_task_base[d + 1] - b->h_task_base[d], b->h_edge_base[d + 1] - b->h_edge_base[d]);
+    };
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) { return key(x) < key(y) || (key(x) == key(y) && x < y); });
+    std::vector<int2> cand;
+    for (int k = 1; k < nd; ++k) {
+        int first = k;
+        while (first > 0 && key(idx[first - 1]) == key(idx[k])) --first;
+        if (first < k && b->h_task_base[idx[k] + 1] > b->h_task_base[idx[k]]) cand.push_back(make_int2(idx[k], idx[first]));
+    }
+    if (cand.empty()) return INSP_OK;
+    DBuf pairs, same;
+    if ((rc = copy_in(pairs, cand.data(), cand.size() * 8, s)) || (rc = same.alloc(cand.size() * 4))) return rc;
+    insp::launch_dag_equal(b->dev(), pairs.as<int2>(), int32_t(cand.size()), same.as<int32_t>(), s);
+    std::vector<int32_t> eq(cand.size());
+    CU(cudaMemcpyAsync(eq.data(), same.p, cand.size() * 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (size_t k = 0; k < cand.size(); ++k)
+        if (eq[k]) b->h_ia_rep[cand[k].x] = cand[k].y;
+    return INSP_OK;
+}
+
+// The inspiring-ability plan for the current tuning's ia_block (see insp_batch): which
+// representatives take the whole-row sweep and which the target-block sweep, the block work
+// items along the size order (largest DAGs first, a DAG's last block -- the longest sweep --
+// first), and the pairs whose IA is copied from their representative.  Uploaded on stream s.
+int build_ia_plan(insp_batch *b, cudaStream_t s) {
+    const int32_t nd = b->ndag;
+    const int32_t full_max = b->tun.ia_block ? 0 : IA_FULL_MAX;
+    std::vector<int32_t> small, blkdags;
+    std::vector<int2> items, pairs;
+    b->h_rank_small.assign(nd + 1, 0);
+    b->h_rank_blk.assign(nd + 1, 0);
+    b->h_rank_blkdag.assign(nd + 1, 0);
+    b->ia_small_max_n = 0;
+    b->ia_blk_max_span = 0;
+    for (int r = 0; r < nd; ++r) {
+        const int d = b->h_order[r];
+        const int32_t n = int32_t(b->h_task_base[d + 1] - b->h_task_base[d]);
+        if (b->h_ia_rep[d] == d && n > 0) {
+            if (n <= full_max) {
+                small.push_back(d);
+                b->ia_small_max_n = std::max(b->ia_small_max_n, n);
+            } else {
+                blkdags.push_back(d);
+                b->ia_blk_max_span = std::max(b->ia_blk_max_span, b->h_dag_span[d]);
+                for (int32_t j = (n + insp::IA_BLK_BITS - 1) / insp::IA_BLK_BITS - 1; j >= 0; --j)
+                    items.push_back(make_int2(d, j));
+            }
+        }
+        b->h_rank_small[r + 1] = int32_t(small.size());
+        b->h_rank_blk[r + 1] = int32_t(items.size());
+        b->h_rank_blkdag[r + 1] = int32_t(blkdags.size());
+    }
+    for (int d = 0; d < nd; ++d)
+        if (b->h_ia_rep[d] != d) pairs.push_back(make_int2(d, b->h_ia_rep[d]));
+    b->ia_dups = !pairs.empty();
+    b->ia_n_pairs = int32_t(pairs.size());
+    int rc;
+    if ((rc = copy_in(b->bufs->ia_small_order, small.data(), std::max<size_t>(small.size(), 1) * 4, s)) ||
+        (rc = copy_in(b->bufs->ia_items, items.data(), std::max<size_t>(items.size(), 1) * 8, s)) ||
+        (rc = copy_in(b->bufs->ia_blk_dags, blkdags.data(), std::max<size_t>(blkdags.size(), 1) * 4, s)) ||
+        (rc = copy_in(b->bufs->ia_pairs, pairs.data(), std::max<size_t>(pairs.size(), 1) * 8, s)))
+        return rc;
+    return INSP_OK;
+}
+
+// Inspiring-ability scratch for the current tuning and plan: for the whole-row sweep one bitset
+// slot per CTA sized by its largest DAG (n x ceil(n/64) words); for the target-block sweep one
+// ring per CTA of ring_rows x (IA_BLK_BITS / 8 + 8) bytes, ring_rows a power of two above the
+// longest edge span of its DAGs plus the warps of a CTA (each wave of warps takes one task per
+// warp), with its publish flags and item tags zeroed.
 int alloc_ia(insp_batch *b) {
     DeviceInfo di;
     int rc = device_info(di);
     if (rc) return rc;
-    const int64_t n = b->max_n;
+    const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
+    const int64_t n = b->ia_small_max_n;
     b->ia_slot = std::max<int64_t>(n * ((n + 63) / 64), 1);  // 64-bit words
     const int occ = std::max(1, insp::ia_occupancy(b->tun.ia_warps));
-    const int64_t budget = int64_t(24) << 30;  // bytes of bitset scratch at most
-    int64_t g = std::min<int64_t>(int64_t(di.sms) * occ, b->ndag);
+    const int64_t n_small = b->h_rank_small.empty() ? 0 : b->h_rank_small.back();
+    int64_t g = std::min<int64_t>(int64_t(di.sms) * occ, std::max<int64_t>(n_small, 1));
     g = std::max<int64_t>(1, std::min(g, budget / (b->ia_slot * 8)));
     b->grid_ia = int(g);
-    return b->sc->ia_bits.alloc(size_t(g * b->ia_slot) * 8 + 16);
+    if ((rc = b->sc->ia_bits.alloc(size_t(g * b->ia_slot) * 8 + 16))) return rc;
+    const int64_t n_items = b->h_rank_blk.empty() ? 0 : b->h_rank_blk.back();
+    if (n_items == 0) {
+        b->grid_ia_blk = 0;
+        return INSP_OK;
+    }
+    int32_t rows = 1;
+    while (rows < b->ia_blk_max_span + b->tun.ia_warps + 1) rows <<= 1;
+    b->ia_ring_rows = rows;
+    const int64_t per_cta = int64_t(rows) * (insp::IA_BLK_WORDS * 8 + 8);
+    const int occ_b = std::max(1, insp::ia_blk_occupancy(b->tun.ia_warps));
+    int64_t gb = std::min<int64_t>(int64_t(di.sms) * occ_b, n_items);
+    gb = std::max<int64_t>(1, std::min(gb, budget / per_cta));
+    b->grid_ia_blk = int(gb);
+    Scratch &S = *b->sc;
+    if ((rc = S.ia_ring.alloc(size_t(gb) * rows * insp::IA_BLK_WORDS * 8)) ||
+        (rc = S.ia_flags.alloc(size_t(gb) * rows * 8)) || (rc = S.ia_seq.alloc(size_t(gb) * 4)))
+        return rc;
+    // flags of 0 never match a key (item tags start at 1); the tags restart with the flags.  No
+    // sweep of this batch may run meanwhile, and the zeroing completes before the next one starts.
+    if (b->last_stream) CU(cudaStreamSynchronize(b->last_stream));
+    CU(cudaMemset(S.ia_flags.p, 0, size_t(gb) * rows * 8));
+    CU(cudaMemset(S.ia_seq.p, 0, size_t(gb) * 4));
+    CU(cudaStreamSynchronize(nullptr));
+    return INSP_OK;
 }
 
 // Window rings of the pull efficiency sweep for the current tuning (L2 budget).
@@ -671,6 +806,8 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
         return (b->h_task_base[a + 1] - b->h_task_base[a]) > (b->h_task_base[c + 1] - b->h_task_base[c]);
     });
     b->h_order = order;
+    if ((rc = find_repeated_structures(b, ls))) return bail(rc);
+    if ((rc = build_ia_plan(b, ls))) return bail(rc);
     std::vector<int64_t> items(ndag + 1, 0);
     for (int d = 0; d < ndag; ++d) items[d + 1] = items[d] + (b->h_task_base[d + 1] - b->h_task_base[d] + 31) / 32;
     b->n_items = items[ndag];
@@ -787,6 +924,35 @@ int prep_unit_time(insp_batch *b, const int64_t *unit_time_ns, cudaStream_t s, c
     return INSP_OK;
 }
 
+// The inspiring ability of the DAGs at ranks [r0, r1) of the size order on stream s (counters
+// c_small and c_blk zeroed): the whole-row sweep over its representatives, the zeroing and the
+// target-block sweep of the others, then the copies for repeated structures.  With repeated
+// structures, all of it runs with the first range (r0 == 0), for every rank.
+void launch_ia_ranks(insp_batch *b, int r0, int r1, int32_t *c_small, int32_t *c_blk, int32_t *d_ia,
+                     cudaStream_t s) {
+    if (b->ia_dups) {
+        if (r0 != 0) return;
+        r1 = b->ndag;
+    }
+    Scratch &S = *b->sc;
+    insp::StepCounters *sc = S.step.as<insp::StepCounters>();
+    const insp::DevBatch B = b->dev();
+    const int32_t s0 = b->h_rank_small[r0], s1 = b->h_rank_small[r1];
+    if (s1 > s0)
+        insp::launch_ia(B, b->bufs->ia_small_order.as<int32_t>() + s0, s1 - s0, c_small, S.ia_bits.as<uint64_t>(),
+                        b->ia_slot, S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(),
+                        std::min(b->grid_ia, s1 - s0), b->tun.ia_warps, s);
+    const int32_t i0 = b->h_rank_blk[r0], i1 = b->h_rank_blk[r1];
+    if (i1 > i0) {
+        const int32_t z0 = b->h_rank_blkdag[r0], z1 = b->h_rank_blkdag[r1];
+        insp::launch_ia_zero(B, b->bufs->ia_blk_dags.as<int32_t>() + z0, z1 - z0, d_ia, s);
+        insp::launch_ia_blk(B, b->bufs->ia_items.as<int2>() + i0, i1 - i0, c_blk, S.ia_ring.as<uint64_t>(),
+                            S.ia_flags.as<unsigned long long>(), b->ia_ring_rows, S.ia_seq.as<uint32_t>(), d_ia,
+                            b->status.as<int32_t>(), std::min(b->grid_ia_blk, i1 - i0), b->tun.ia_warps, s);
+    }
+    if (b->ia_dups) insp::launch_ia_copy(B, b->bufs->ia_pairs.as<int2>(), b->ia_n_pairs, d_ia, s);
+}
+
 // The attribute sweeps of the DAGs at ranks [r0, r1) of the size order: the
 // ability sweep on s_ia, the efficiency sweep on s_ie (the two are
 // independent).  ctr: this launch pair's two work counters (zeroed).  The
@@ -801,9 +967,7 @@ int launch_attr(insp_batch *b, int r0, int r1, int32_t *ctr, const int64_t *ut, 
     if (nd <= 0) return INSP_OK;
     {
         TimedLaunch tl(b, TK_IA, s_ia);
-        insp::launch_ia(B, b->order.as<int32_t>() + r0, nd, ctr + 0, S.ia_bits.as<uint64_t>(), b->ia_slot,
-                        S.ia_done.as<int32_t>(), &sc->epoch, d_ia, b->status.as<int32_t>(),
-                        std::min(b->grid_ia, nd), b->tun.ia_warps, s_ia);
+        launch_ia_ranks(b, r0, r1, ctr + 0, ctr + 3, d_ia, s_ia);
     }
     {
         TimedLaunch tl(b, TK_IE, s_ie);
@@ -1080,12 +1244,11 @@ INSP_API int insp_unit_time_search(insp_batch *b, int32_t k_max, int64_t *unit_t
     CU(cudaMemsetAsync(b->status.p, 0, size_t(nd) * 4, s));
     const insp::DevBatch B = b->dev();
     insp::StepCounters *sc = S.step.as<insp::StepCounters>();
-    int32_t *c = ctr.as<int32_t>();  // 0: ability, 1: targets, 8 + 4k..: per candidate, 63: decided DAGs
+    int32_t *c = ctr.as<int32_t>();  // 0, 2: ability, 1: targets, 8 + 4k..: per candidate, 63: decided DAGs
     const int32_t *order = b->order.as<int32_t>();
     const int grid = std::max(1, std::min(di.sms * 8, (nd + 7) / 8));
     insp::launch_step_begin(sc, b->n_items, s);
-    insp::launch_ia(B, order, nd, c + 0, S.ia_bits.as<uint64_t>(), b->ia_slot, S.ia_done.as<int32_t>(), &sc->epoch,
-                    ia.as<int32_t>(), b->status.as<int32_t>(), std::min(b->grid_ia, nd), b->tun.ia_warps, s);
+    launch_ia_ranks(b, 0, nd, c + 0, c + 2, ia.as<int32_t>(), s);
     insp::launch_search_target(B, order, c + 1, ia.as<int32_t>(), layer.as<int32_t>(), bm.as<uint32_t>(),
                                bmb.as<int64_t>(), target.as<int64_t>(), grid, s);
     const int64_t max_med = std::max<int64_t>(1, b->max_unit_def / 4), cap = int64_t(1) << 62;
@@ -1358,7 +1521,8 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
     const insp_tuning old = b->tun;
     b->tun = *t;
     int rc = INSP_OK;
-    if (old.ia_warps != t->ia_warps) rc = alloc_ia(b);
+    if (old.ia_block != t->ia_block) rc = build_ia_plan(b, nullptr);
+    if (rc == INSP_OK && (old.ia_warps != t->ia_warps || old.ia_block != t->ia_block)) rc = alloc_ia(b);
     if (rc == INSP_OK && b->pull && (old.ie_warps != t->ie_warps || old.ie_ring_mb != t->ie_ring_mb))
         rc = alloc_pull_ring(b);
     if (rc != INSP_OK) {
@@ -1366,7 +1530,8 @@ INSP_API int insp_batch_set_tuning(insp_batch *b, const insp_tuning *t) {
         // old sizes fitted before); the batch stays usable with its previous tuning
         const std::string err = g_err;
         b->tun = old;
-        const int r2 = alloc_ia(b);
+        const int r1 = build_ia_plan(b, nullptr);
+        const int r2 = r1 ? r1 : alloc_ia(b);
         const int r3 = b->pull ? alloc_pull_ring(b) : INSP_OK;
         if (r2 || r3) return fail(rc, err + "; restoring the previous tuning failed too");
         g_err = err;
@@ -1469,14 +1634,16 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
             }
         rc = search(c);
     }
-    // 3. ability sweep: CTA size
+    // 3. ability sweep: CTA size, whole-DAG rows or target blocks
     if (rc == INSP_OK) {
         c.clear();
-        for (int w : {8, 16, 32}) {
-            insp_tuning t = best;
-            t.ia_warps = w;
-            c.push_back(t);
-        }
+        for (int blk : {0, 1})
+            for (int w : {8, 16, 32}) {
+                insp_tuning t = best;
+                t.ia_warps = w;
+                t.ia_block = blk;
+                c.push_back(t);
+            }
         rc = search(c);
     }
     // 4. pipelining: size groups and concurrent attribute sweeps

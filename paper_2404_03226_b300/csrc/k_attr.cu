@@ -17,6 +17,8 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <algorithm>
+
 namespace insp {
 
 // --------------------------------------------------------- inspiring ability
@@ -105,6 +107,195 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
         }
         timed_out = __syncthreads_or(timed_out);
         if (timed_out && threadIdx.x == 0) status[d] = INSP_ETIMEOUT;
+    }
+}
+
+// Inspiring ability at any DAG size: the target ids are cut into blocks of IA_BLK_BITS, and one
+// CTA sweeps one (DAG, block) work item.  Within block j = [b0, b1) the row of task v is
+// row_j(v) = ({v} if v is in the block) | OR over successors s of row_j(s); a successor at or
+// above b1 adds nothing (its descendants come after it), so the sweep runs from b1 - 1 down to
+// task 0, and IA(v) = sum over blocks of popcount(row_j(v)) - 1.  A row is read only by
+// predecessors at most `span` ids below it (the DAG's longest edge), so rows live in a ring of
+// R >= span + warps slots: the CTA's warps take the tasks in waves of one task per warp, the
+// waves separated by a barrier, so when a slot is overwritten every reader of its previous row
+// has finished.  Within a wave a task waits (bounded) for its successors' publish flags, which
+// carry the item's tag and the task id.  Memory per CTA: R x (IA_BLK_BITS / 8 + 8) bytes,
+// independent of the DAG's size.  Partial counts are added to ia (zeroed first) atomically.
+__device__ __forceinline__ bool wait_key(const unsigned long long *flag, unsigned long long key, int32_t *abort,
+                                         int limit) {
+    int it = 0;
+    while (*(const volatile unsigned long long *)flag != key) {
+        if (++it > limit || ld_volatile(abort)) {
+            st_volatile(abort, 1);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia_blk(DevBatch B, const int2 *items, int32_t n_items,
+                                                              int32_t *counter, uint64_t *ring,
+                                                              unsigned long long *flags, int32_t ring_rows,
+                                                              uint32_t *slot_seq, int32_t *ia_out, int32_t *status) {
+    __shared__ int32_t s_item;
+    __shared__ uint32_t s_tag;
+    __shared__ int32_t s_abort;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    uint64_t *R = ring + int64_t(blockIdx.x) * ring_rows * IA_BLK_WORDS;
+    unsigned long long *F = flags + int64_t(blockIdx.x) * ring_rows;
+    const int32_t rmask = ring_rows - 1;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int k = atomicAdd(counter, 1);
+            s_item = k < n_items ? k : -1;
+            if (k < n_items) {
+                s_tag = slot_seq[blockIdx.x] + 1;  // unique per item of this CTA (flags start at 0)
+                slot_seq[blockIdx.x] = s_tag;
+            }
+            s_abort = 0;
+        }
+        __syncthreads();
+        if (s_item < 0) return;
+        const int2 it = items[s_item];
+        const int d = it.x;
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int32_t n = int32_t(B.task_base[d + 1] - tb);
+        const int32_t b0 = it.y * IA_BLK_BITS, b1 = min(n, b0 + IA_BLK_BITS);
+        const int32_t NWb = (b1 - b0 + 63) >> 6;
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        const unsigned long long tag = (unsigned long long)s_tag << 32;
+        bool timed_out = false;
+        for (int32_t top = b1 - 1; top >= 0; top -= nwarps) {
+            const int32_t v = top - wib;
+            if (v >= 0) {
+                const int32_t lo = rp[v], hi = rp[v + 1];
+                // successors below b1 (the list is ascending), each waited for (bounded)
+                int32_t deg = 0;
+                for (int32_t base = lo; base < hi; base += 32) {
+                    const int32_t i = base + lane;
+                    const int32_t s = i < hi ? col[i] : b1;
+                    const bool in = s < b1;
+                    if (in && insp_check(s > v && s - v < ring_rows, status + d) &&
+                        !wait_key(F + (s & rmask), tag | uint32_t(s), &s_abort, SPIN_LIMIT))
+                        timed_out = true;
+                    const uint32_t m = __ballot_sync(FULL, in);
+                    deg += __popc(m);
+                    if (m != FULL) break;
+                }
+                __syncwarp();
+                __threadfence_block();
+                const bool own = v >= b0;
+                const int32_t wlo = own ? (v - b0) >> 6 : 0;
+                const int32_t span_w = NWb - wlo;
+                const int32_t lg = span_w >= 32 ? 5 : (span_w <= 1 ? 0 : 32 - __clz(span_w - 1));
+                const int32_t g = 1 << lg;
+                const int32_t G = 32 >> lg, grp = lane >> lg, wl = lane & (g - 1);
+                uint64_t *row_v = R + int64_t(v & rmask) * IA_BLK_WORDS;
+                int32_t count = 0;
+                for (int32_t cw = wlo; cw < NWb; cw += g) {
+                    const int32_t w = cw + wl;
+                    uint64_t acc = (own && grp == 0 && w == wlo) ? (1ull << ((v - b0) & 63)) : 0ull;
+#pragma unroll 4
+                    for (int32_t i = grp; i < deg; i += G) {
+                        const int32_t s = col[lo + i];
+                        // words of row(s) below its own first word were not written for it
+                        const int32_t ws = s >= b0 ? (s - b0) >> 6 : 0;
+                        if (w >= ws && w < NWb) acc |= R[int64_t(s & rmask) * IA_BLK_WORDS + w];
+                    }
+                    for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
+                    if (grp == 0 && w < NWb) {
+                        row_v[w] = acc;
+                        count += __popcll(acc);
+                    }
+                }
+                count = __reduce_add_sync(FULL, count) - (own ? 1 : 0);
+                __threadfence_block();
+                __syncwarp();
+                if (lane == 0) {
+                    *(volatile unsigned long long *)(F + (v & rmask)) = tag | uint32_t(v);
+                    if (count > 0) atomicAdd(ia_out + tb + v, count);
+                }
+            }
+            __syncthreads();
+        }
+        timed_out = __syncthreads_or(timed_out);
+        if (timed_out && threadIdx.x == 0) status[d] = INSP_ETIMEOUT;
+    }
+}
+
+// Zero the inspiring ability of the listed DAGs (before k_ia_blk adds its partial counts).
+__global__ void k_ia_zero(DevBatch B, const int32_t *dags, int32_t n_dags, int32_t *ia) {
+    for (int k = blockIdx.x; k < n_dags; k += gridDim.x) {
+        const int d = dags[k];
+        const int64_t tb = B.task_base[d], te = B.task_base[d + 1];
+        for (int64_t t = tb + threadIdx.x; t < te; t += blockDim.x) ia[t] = 0;
+    }
+}
+
+// A DAG whose structure (tasks, successor lists) equals an earlier one's takes its inspiring
+// ability, which depends on nothing else: pairs[k] = {dag, representative}.
+__global__ void k_ia_copy(DevBatch B, const int2 *pairs, int32_t n_pairs, int32_t *ia) {
+    for (int k = blockIdx.x; k < n_pairs; k += gridDim.x) {
+        const int2 p = pairs[k];
+        const int64_t td = B.task_base[p.x], tr = B.task_base[p.y];
+        const int64_t n = B.task_base[p.x + 1] - td;
+        for (int64_t t = threadIdx.x; t < n; t += blockDim.x) ia[td + t] = ia[tr + t];
+    }
+}
+
+// Structure fingerprint of every DAG: a sum (order-free, so deterministic) of 64-bit mixes of
+// (position, value) over the task count, row offsets and successor ids.  Equal structures give
+// equal fingerprints; the host confirms candidates with k_dag_equal before sharing anything.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+__global__ void __launch_bounds__(256) k_dag_hash(DevBatch B, unsigned long long *hash) {
+    __shared__ unsigned long long s_h;
+    for (int d = blockIdx.x; d < B.ndag; d += gridDim.x) {
+        if (threadIdx.x == 0) s_h = 0;
+        __syncthreads();
+        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
+        const int64_t n = B.task_base[d + 1] - tb, m = B.edge_base[d + 1] - eb;
+        const int32_t *rp = B.row_ptr + tb + d;
+        const int32_t *col = B.col_idx + eb;
+        unsigned long long h = threadIdx.x == 0 ? mix64(uint64_t(n) * 0x100000001ull + uint64_t(m)) : 0ull;
+        for (int64_t i = threadIdx.x; i <= n; i += blockDim.x) h += mix64((uint64_t(i) << 32) ^ uint32_t(rp[i]));
+        for (int64_t e = threadIdx.x; e < m; e += blockDim.x)
+            h += mix64(((uint64_t(e) + 0x80000000ull) << 32) ^ uint32_t(col[e]) ^ 0x5bd1e995ull);
+        atomicAdd(&s_h, h);
+        __syncthreads();
+        if (threadIdx.x == 0) hash[d] = s_h;
+        __syncthreads();
+    }
+}
+
+// Exact comparison of candidate pairs {dag, representative} of equal fingerprints, task counts
+// and edge counts: same[k] = 1 when their row offsets and successor ids are equal.
+__global__ void __launch_bounds__(256) k_dag_equal(DevBatch B, const int2 *pairs, int32_t n_pairs, int32_t *same) {
+    __shared__ int32_t s_diff;
+    for (int k = blockIdx.x; k < n_pairs; k += gridDim.x) {
+        if (threadIdx.x == 0) s_diff = 0;
+        __syncthreads();
+        const int2 p = pairs[k];
+        const int64_t ta = B.task_base[p.x], tr = B.task_base[p.y];
+        const int64_t n = B.task_base[p.x + 1] - ta, m = B.edge_base[p.x + 1] - B.edge_base[p.x];
+        const int32_t *ra = B.row_ptr + ta + p.x, *rr = B.row_ptr + tr + p.y;
+        const int32_t *ca = B.col_idx + B.edge_base[p.x], *cr = B.col_idx + B.edge_base[p.y];
+        bool diff = n != B.task_base[p.y + 1] - tr || m != B.edge_base[p.y + 1] - B.edge_base[p.y];
+        if (!diff) {
+            for (int64_t i = threadIdx.x; i <= n && !diff; i += blockDim.x) diff = ra[i] != rr[i];
+            for (int64_t e = threadIdx.x; e < m && !diff; e += blockDim.x) diff = ca[e] != cr[e];
+        }
+        if (diff) s_diff = 1;
+        __syncthreads();
+        if (threadIdx.x == 0) same[k] = s_diff ? 0 : 1;
+        __syncthreads();
     }
 }
 
@@ -239,6 +430,29 @@ void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int
     else
         k_ie<int32_t><<<grid, 256, 0, s>>>(B, item_base, n_items, counter, unit_time, rec, rec_stride,
                                            (int32_t *)acc, W, tag_base, ie);
+}
+
+void launch_ia_blk(const DevBatch &B, const int2 *items, int32_t n_items, int32_t *counter, uint64_t *ring,
+                   unsigned long long *flags, int32_t ring_rows, uint32_t *slot_seq, int32_t *ia, int32_t *status,
+                   int grid, int warps, cudaStream_t s) {
+    k_ia_blk<<<grid, 32 * warps, 0, s>>>(B, items, n_items, counter, ring, flags, ring_rows, slot_seq, ia, status);
+}
+void launch_ia_zero(const DevBatch &B, const int32_t *dags, int32_t n_dags, int32_t *ia, cudaStream_t s) {
+    if (n_dags > 0) k_ia_zero<<<std::min(n_dags, 4096), 256, 0, s>>>(B, dags, n_dags, ia);
+}
+void launch_ia_copy(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *ia, cudaStream_t s) {
+    if (n_pairs > 0) k_ia_copy<<<std::min(n_pairs, 4096), 256, 0, s>>>(B, pairs, n_pairs, ia);
+}
+void launch_dag_hash(const DevBatch &B, unsigned long long *hash, int grid, cudaStream_t s) {
+    k_dag_hash<<<grid, 256, 0, s>>>(B, hash);
+}
+void launch_dag_equal(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *same, cudaStream_t s) {
+    if (n_pairs > 0) k_dag_equal<<<std::min(n_pairs, 4096), 256, 0, s>>>(B, pairs, n_pairs, same);
+}
+int ia_blk_occupancy(int warps) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ia_blk, 32 * warps, 0) != cudaSuccess) return 0;
+    return nb;
 }
 
 int ia_max_warps() { return IA_MAX_WARPS; }

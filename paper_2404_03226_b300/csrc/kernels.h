@@ -66,6 +66,19 @@ void launch_ia(const DevBatch &B, const int32_t *order, int32_t n_order, int32_t
 void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int32_t *counter,
                const int64_t *unit_time, uint4 *rec, int64_t rec_stride, void *acc, int32_t W, bool wide,
                const uint64_t *tag_base, int32_t *ie, int grid, cudaStream_t s);
+// Inspiring ability by target blocks (any DAG size): work items {dag, block} of IA_BLK_BITS
+// target ids, per CTA a ring of ring_rows rows (a power of two >= the DAG's longest edge span
+// + warps per CTA) and publish flags; slot_seq[grid] per-CTA item tags (start at 0).
+constexpr int32_t IA_BLK_BITS = 2048;
+constexpr int32_t IA_BLK_WORDS = IA_BLK_BITS / 64;
+void launch_ia_blk(const DevBatch &B, const int2 *items, int32_t n_items, int32_t *counter, uint64_t *ring,
+                   unsigned long long *flags, int32_t ring_rows, uint32_t *slot_seq, int32_t *ia, int32_t *status,
+                   int grid, int warps, cudaStream_t s);
+void launch_ia_zero(const DevBatch &B, const int32_t *dags, int32_t n_dags, int32_t *ia, cudaStream_t s);
+void launch_ia_copy(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *ia, cudaStream_t s);
+void launch_dag_hash(const DevBatch &B, unsigned long long *hash, int grid, cudaStream_t s);
+void launch_dag_equal(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *same, cudaStream_t s);
+int ia_blk_occupancy(int warps);
 // inspiring efficiency, pull form (k_ie_pull.cu)
 // Longest window (ring rows, a power of two above the batch's longest edge span) of the
 // pull form: its per-warp ring is W x 128 bytes, so long spans only cost ring memory (the

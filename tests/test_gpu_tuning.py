@@ -11,16 +11,24 @@ from helpers import compare_dag, edge_case_dags
 pytestmark = pytest.mark.gpu
 
 TUNINGS = [
-    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64, group_split=0),
-    dict(groups=3, attr_overlap=1, ia_warps=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32, group_split=0),
+    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=64, sim_warps=8, sim_queue=64, group_split=0,
+         ia_block=0),
+    dict(groups=3, attr_overlap=1, ia_warps=32, ie_warps=1, ie_ring_mb=1, sim_warps=1, sim_queue=32, group_split=0,
+         ia_block=1),
     dict(groups=16, attr_overlap=0, ia_warps=32, ie_warps=16, ie_ring_mb=2048, sim_warps=8, sim_queue=128,
-         group_split=0),
-    dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128, group_split=1),
-    dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32, group_split=0),
-    dict(groups=3, attr_overlap=0, ia_warps=16, ie_warps=16, ie_ring_mb=512, sim_warps=4, sim_queue=64, group_split=1),
-    dict(groups=2, attr_overlap=1, ia_warps=16, ie_warps=8, ie_ring_mb=256, sim_warps=8, sim_queue=512, group_split=0),
-    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=3, sim_queue=256, group_split=0),
-    dict(groups=2, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=5, sim_queue=1024, group_split=0),
+         group_split=0, ia_block=0),
+    dict(groups=4, attr_overlap=1, ia_warps=3, ie_warps=8, ie_ring_mb=256, sim_warps=3, sim_queue=128, group_split=1,
+         ia_block=1),
+    dict(groups=1, attr_overlap=1, ia_warps=1, ie_warps=2, ie_ring_mb=8, sim_warps=5, sim_queue=32, group_split=0,
+         ia_block=1),
+    dict(groups=3, attr_overlap=0, ia_warps=16, ie_warps=16, ie_ring_mb=512, sim_warps=4, sim_queue=64, group_split=1,
+         ia_block=0),
+    dict(groups=2, attr_overlap=1, ia_warps=16, ie_warps=8, ie_ring_mb=256, sim_warps=8, sim_queue=512, group_split=0,
+         ia_block=1),
+    dict(groups=1, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=3, sim_queue=256, group_split=0,
+         ia_block=0),
+    dict(groups=2, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=5, sim_queue=1024, group_split=0,
+         ia_block=1),
 ]
 
 
@@ -106,7 +114,8 @@ def test_tuning_rejects_out_of_range():
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
     good = B.tuning
     for field, bad in (("groups", 0), ("groups", 17), ("attr_overlap", 2), ("ia_warps", 0), ("ia_warps", 33),
-                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48), ("group_split", 2)):
+                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48), ("group_split", 2),
+                       ("ia_block", 2)):
         t = dict(good, **{field: bad})
         with pytest.raises(P.InspError):
             B.tuning = t
@@ -154,4 +163,37 @@ def test_simulation_cta_that_does_not_fit_is_an_error():
     B.tuning = TUNINGS[0]
     out = _run(B, True)
     for d in range(0, b.ndag, 7):
+        compare_dag(b, d, out, m)
+
+
+@pytest.mark.parametrize("ia_block", [0, 1])
+@pytest.mark.parametrize("groups", [1, 3])
+def test_repeated_structures_share_ability(ia_block, groups):
+    """Instances of one tiled structure with different per-task costs (inspiring ability depends
+    on the structure alone, so it is computed once per structure and copied), mixed with unique
+    DAGs, in both ability sweeps, one group or pipelined groups, two-call and fused steps."""
+    import paper_2404_03226_b300 as P
+    b = inputs.concat([inputs.tiled(inputs.KIND_CHOLESKY, 16, 5, cfg=42), inputs.layered(7, cfg=43, n_max=700),
+                       inputs.tiled(inputs.KIND_LU, 8, 3, cfg=44), inputs.tiled(inputs.KIND_QR, 8, 1, cfg=45)])
+    m = inputs.MACHINE_TILED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = dict(TUNINGS[0], groups=groups, ia_block=ia_block)
+    for fused in (False, True):
+        out = _run(B, fused)
+        for d in range(b.ndag):
+            compare_dag(b, d, out, m)
+
+
+@pytest.mark.parametrize("ia_block", [0, 1])
+def test_ability_by_target_blocks_on_larger_dags(ia_block):
+    """DAGs of several 2048-id target blocks (layered up to 7,000 tasks; Cholesky at 48 tiles,
+    19,600 tasks, above the whole-row limit, so it takes the blocks in both modes)."""
+    import paper_2404_03226_b300 as P
+    b = inputs.concat([inputs.layered(6, cfg=46, n_min=2040, n_max=7000),
+                       inputs.tiled(inputs.KIND_CHOLESKY, 48, 1, cfg=47)])
+    m = inputs.MACHINE_TILED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    B.tuning = dict(TUNINGS[0], ia_block=ia_block, ia_warps=32)
+    out = _run(B)
+    for d in range(b.ndag):
         compare_dag(b, d, out, m)

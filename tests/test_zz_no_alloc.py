@@ -25,11 +25,13 @@ POLICIES = {"inspirit": (0, oracle.POLICY_INSPIRIT), "fifo": (1, oracle.POLICY_F
 
 
 def _costs(dag, type_table):
-    """(n_types, type_cost, task_cost) in the layout the C ABI takes."""
+    """(n_types, type_cost, task_cost, type) in the layout the C ABI takes; with per-task costs
+    there is one type and every task has type 0."""
     if type_table is None:
-        return 1, None, np.ascontiguousarray(np.stack([dag.c_cpu, dag.c_gpu], 1), np.int64)
+        return (1, None, np.ascontiguousarray(np.stack([dag.c_cpu, dag.c_gpu], 1), np.int64),
+                np.zeros(max(dag.n, 1), np.uint8))
     tt = np.ascontiguousarray(type_table, np.int64)
-    return tt.shape[0], tt, None
+    return tt.shape[0], tt, None, np.ascontiguousarray(dag.type if dag.n else np.zeros(1), np.uint8)
 
 
 def _dev(x, dtype):
@@ -47,7 +49,7 @@ def _policy(name):
 def _regular(dag, machine, type_table, policy):
     """Schedule from the existing single-DAG entry points (host arrays)."""
     from paper_2404_03226_b300 import _lib
-    nt, tc, kc = _costs(dag, type_table)
+    nt, tc, kc, ty = _costs(dag, type_table)
     M = _lib.insp_machine_create(machine.n_cpu, machine.n_gpu, machine.xfer_ns, _policy(policy))
     n = dag.n
     out = dict(ia=np.zeros(max(n, 1), np.int32), ie=np.zeros(max(n, 1), np.int32),
@@ -56,9 +58,7 @@ def _regular(dag, machine, type_table, policy):
     try:
         h = _lib.insp_dag_load_csr(M, n, np.ascontiguousarray(dag.row_ptr, np.int32),
                                    np.ascontiguousarray(dag.col_idx, np.int32) if dag.col_idx.size
-                                   else np.zeros(1, np.int32),
-                                   np.ascontiguousarray(dag.type, np.uint8) if n else np.zeros(1, np.uint8),
-                                   nt, tc, kc)
+                                   else np.zeros(1, np.int32), ty, nt, tc, kc)
         try:
             _lib.insp_attributes(h, 0, out["ia"], out["ie"])
             _lib.insp_simulate(h, out["ia"], out["ie"], out["worker"], out["start"], out["end"], out["makespan"])
@@ -73,10 +73,10 @@ def _noalloc(dag, machine, ia, ie, type_table=None, policy="inspirit"):
     import torch
     from paper_2404_03226_b300 import _lib
     n = dag.n
-    nt, tc, kc = _costs(dag, type_table)
+    nt, tc, kc, ty = _costs(dag, type_table)
     row_ptr = _dev(dag.row_ptr, np.int32)
     col_idx = _dev(dag.col_idx if dag.col_idx.size else np.zeros(1), np.int32)
-    typ = _dev(dag.type if n else np.zeros(1), np.uint8)
+    typ = _dev(ty, np.uint8)
     d_tc = None if tc is None else _dev(tc, np.int64)
     d_kc = None if kc is None else _dev(kc if n else np.ones((1, 2)), np.int64)
     d_ia = _dev(ia if n else np.zeros(1), np.int32)
