@@ -379,11 +379,15 @@ int build_ia_plan(insp_batch *b, cudaStream_t s) {
         if (b->h_ia_rep[d] != d) pairs.push_back(make_int2(d, b->h_ia_rep[d]));
     b->ia_dups = !pairs.empty();
     b->ia_n_pairs = int32_t(pairs.size());
+    // (an empty list still gets a small buffer; nothing is copied from it)
+    auto put = [&](DBuf &dst, const void *src, size_t bytes) {
+        return bytes ? copy_in(dst, src, bytes, s) : dst.alloc(16);
+    };
     int rc;
-    if ((rc = copy_in(b->bufs->ia_small_order, small.data(), std::max<size_t>(small.size(), 1) * 4, s)) ||
-        (rc = copy_in(b->bufs->ia_items, items.data(), std::max<size_t>(items.size(), 1) * 8, s)) ||
-        (rc = copy_in(b->bufs->ia_blk_dags, blkdags.data(), std::max<size_t>(blkdags.size(), 1) * 4, s)) ||
-        (rc = copy_in(b->bufs->ia_pairs, pairs.data(), std::max<size_t>(pairs.size(), 1) * 8, s)))
+    if ((rc = put(b->bufs->ia_small_order, small.data(), small.size() * 4)) ||
+        (rc = put(b->bufs->ia_items, items.data(), items.size() * 8)) ||
+        (rc = put(b->bufs->ia_blk_dags, blkdags.data(), blkdags.size() * 4)) ||
+        (rc = put(b->bufs->ia_pairs, pairs.data(), pairs.size() * 8)))
         return rc;
     return INSP_OK;
 }
