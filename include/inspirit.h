@@ -285,6 +285,16 @@ int insp_batch_status(insp_batch *b, int32_t *status);
  *   work: caller scratch of n * (2*h1 + 2*h2 + 2) floats; grad[nw], loss[1].
  *   Gradients are reduced over samples in a fixed order (deterministic).
  *
+ * insp_scorer_train_grad_tc: the same loss and gradient with every matrix
+ *   product on the tensor cores (BF16 mma.sync, FP32 accumulation, FP32 master
+ *   weights w): each FP32 operand enters as two BF16 numbers hi + lo and each
+ *   product as hi*hi + hi*lo + lo*hi, about 16 significant bits; in mode 1 the
+ *   weights on the k/64 grid, integer features and floored activations are exact
+ *   in BF16, so the forward pass and the loss are exact.  part: caller scratch of
+ *   ceil(n / 16) * (nw + 1) floats, nw = in*h1 + h1 + h1*h2 + h2 + h2 + 1 (one
+ *   partial gradient per tile of 16 samples, summed in tile order:
+ *   deterministic).  Same dimension limits and errors.
+ *
  * insp_adamw: one AdamW step (decoupled weight decay), step t >= 1, in place
  *   on w, m, v with gradient g.
  *
@@ -297,6 +307,9 @@ int insp_simulate_rollout(insp_batch *b, const int32_t *ia, const int32_t *ie, i
                           int32_t *feat_n, void *stream);
 int insp_scorer_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
                            const float *x, const float *target, float *work, float *grad, float *loss, void *stream);
+int insp_scorer_train_grad_tc(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                              const float *x, const float *target, float *part, float *grad, float *loss,
+                              void *stream);
 int insp_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t t, float lr, float b1, float b2,
                float eps, float wd, void *stream);
 int insp_scorer_quantize(int64_t nw, const float *w, uint16_t *bf16_out, void *stream);

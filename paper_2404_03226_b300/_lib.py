@@ -75,6 +75,7 @@ _PROTOS = {
     "insp_simulate_rollout": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp,
                                              _vp, _vp]),
     "insp_scorer_train_grad": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "insp_scorer_train_grad_tc": (ctypes.c_int, [_i32, _i32, _i32, _vp, _i32, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_adamw": (ctypes.c_int, [_i64, _vp, _vp, _vp, _vp, _i32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                   ctypes.c_float, ctypes.c_float, _vp]),
     "insp_scorer_quantize": (ctypes.c_int, [_i64, _vp, _vp, _vp]),
@@ -290,6 +291,11 @@ def insp_simulate_rollout(b, ia, ie, worker, start, end, makespan, force_pop=Non
 def insp_scorer_train_grad(inp, h1, h2, w, mode, n, x, target, work, grad, loss, stream=None) -> None:
     check(lib().insp_scorer_train_grad(inp, h1, h2, ptr(w), mode, n, ptr(x), ptr(target), ptr(work), ptr(grad),
                                        ptr(loss), stream_ptr(stream)))
+
+
+def insp_scorer_train_grad_tc(inp, h1, h2, w, mode, n, x, target, part, grad, loss, stream=None) -> None:
+    check(lib().insp_scorer_train_grad_tc(inp, h1, h2, ptr(w), mode, n, ptr(x), ptr(target), ptr(part), ptr(grad),
+                                          ptr(loss), stream_ptr(stream)))
 
 
 def insp_adamw(nw, w, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8, wd=0.0, stream=None) -> None:

@@ -666,6 +666,20 @@ INSP_API int insp_scorer_train_grad(int32_t in, int32_t h1, int32_t h2, const fl
     return INSP_OK;
 }
 
+INSP_API int insp_scorer_train_grad_tc(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                                       const float *x, const float *target, float *part, float *grad, float *loss,
+                                       void *stream) {
+    if (in < 1 || in > 32 || h1 < 1 || h1 > 64 || h2 < 1 || h2 > 64 || n < 1 || (mode != 0 && mode != 1))
+        return fail(INSP_EINVAL, "need 1 <= in <= 32, 1 <= h1, h2 <= 64, n >= 1, mode 0 or 1");
+    const void *ptrs[] = {w, x, target, part, grad, loss};
+    for (const void *q : ptrs)
+        if (!is_device_ptr(q)) return fail(INSP_EINVAL, "device pointers required");
+    insp::launch_mlp_train_grad_tc(in, h1, h2, w, mode, n, x, target, part, grad, loss,
+                                   static_cast<cudaStream_t>(stream));
+    CU(cudaGetLastError());
+    return INSP_OK;
+}
+
 INSP_API int insp_adamw(int64_t nw, float *w, float *m_, float *v, const float *g, int32_t t, float lr, float b1,
                         float b2, float eps, float wd, void *stream) {
     if (nw < 1 || t < 1) return fail(INSP_EINVAL, "need nw >= 1 and step t >= 1");

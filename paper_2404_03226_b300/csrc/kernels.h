@@ -103,6 +103,10 @@ void launch_scorer_eval(const ScorerPacked *P, const int32_t *feat, int64_t n, i
 void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
                            const float *x, const float *target, float *work, float *grad, float *loss,
                            cudaStream_t s);
+// the tensor-core form: part = caller scratch of ceil(n / 16) x (nweights + 1) floats
+void launch_mlp_train_grad_tc(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
+                              const float *x, const float *target, float *part, float *grad, float *loss,
+                              cudaStream_t s);
 void launch_adamw(int64_t nw, float *w, float *m, float *v, const float *g, int32_t t, float lr, float b1, float b2,
                   float eps, float wd, cudaStream_t s);
 void launch_quantize(int64_t nw, const float *w, uint16_t *out, cudaStream_t s);

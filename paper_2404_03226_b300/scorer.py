@@ -108,8 +108,10 @@ def init_weights(seed: int) -> np.ndarray:
 
 def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3, seed: int = 0,
           w0: np.ndarray | None = None, log=None, checkpoint: str | None = None):
-    """Quantisation-aware training on the GPU; returns (fp32 master weights,
-    BF16 grid weights as uint16, per-epoch mean loss).
+    """Quantisation-aware training on the GPU, the loss and gradient of each
+    minibatch on the tensor cores (insp_scorer_train_grad_tc: BF16 mma.sync,
+    FP32 accumulation, FP32 master weights), then AdamW; returns (fp32 master
+    weights, BF16 grid weights as uint16, per-epoch mean loss).
 
     checkpoint: a .npz path written after every epoch (fp32 weights, AdamW
     moments, step, epoch, seed, loss history); if it exists when training
@@ -127,7 +129,7 @@ def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3,
     g = torch.zeros_like(w)
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     bs = min(batch, n)
-    work = torch.empty(bs * (2 * H + 2 * H + 2), dtype=torch.float32, device=dev)
+    part = torch.empty(((bs + 15) // 16) * (NW + 1), dtype=torch.float32, device=dev)  # per-tile partials
     rng = np.random.default_rng(seed + 1)
     t = 0
     hist = []
@@ -149,7 +151,7 @@ def train(roll: Rollouts, epochs: int = 30, batch: int = 4096, lr: float = 2e-3,
             idx = perm[s0:s0 + bs]
             xb = x[idx].contiguous()
             yb = y[idx].contiguous()
-            _lib.insp_scorer_train_grad(IN, H, H, w, 1, bs, xb, yb, work, g, loss)
+            _lib.insp_scorer_train_grad_tc(IN, H, H, w, 1, bs, xb, yb, part, g, loss)
             t += 1
             _lib.insp_adamw(NW, w, m, v, g, t, lr)
             losses.append(loss)

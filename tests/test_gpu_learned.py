@@ -232,3 +232,79 @@ def test_training_checkpoint_resume_is_exact(tmp_path):
     np.testing.assert_array_equal(w_res, w_full)
     np.testing.assert_array_equal(q_res, q_full)
     assert h_res == h_full
+
+
+@pytest.mark.parametrize("dims,mode", [((16, 4, 4), 0), ((16, 4, 4), 1), ((16, 64, 64), 0), ((16, 64, 64), 1),
+                                       ((32, 64, 64), 1), ((7, 13, 5), 0), ((7, 13, 5), 1)])
+def test_training_gradient_on_tensor_cores_matches_oracle(dims, mode):
+    """The tensor-core form (BF16 mma.sync, FP32 accumulation) against the oracle's fp64
+    gradient, at the tolerance of the FP32 path: each FP32 operand enters as hi + lo BF16 parts
+    and each product drops only lo*lo, below 2^-16 of the product, so the relative error of a
+    product stays under 2^-16 (1.5e-5) and the FP32 sums over up to a few hundred terms keep
+    the gradient within rtol 1e-4 (atol 1e-5 of the largest gradient for cancelling sums).  In
+    the quantisation-aware mode (1) the forward pass is exact, so the loss matches to 1e-6;
+    the smooth mode (0) carries the split error into the loss (1e-4).  300 samples: a ragged
+    last tile.  Deterministic, and close to the FP32 form."""
+    import torch
+    from paper_2404_03226_b300 import _lib
+    rng = np.random.default_rng(sum(dims) * 7 + mode)
+    nw = oracle.mlp_nweights_dims(*dims)
+    w = rng.normal(0, 0.1, nw).astype(np.float32)
+    w[dims[0] * dims[1]:dims[0] * dims[1] + dims[1]] = 1.5  # live first-layer units
+    n = 300
+    x = rng.integers(0, 20, (n, dims[0])).astype(np.float32)
+    t = rng.normal(0, 2, n).astype(np.float32)
+    dev = torch.device("cuda")
+    dw, dx, dt = (torch.from_numpy(a).to(dev) for a in (w, x, t))
+    g = torch.zeros(nw, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    part = torch.empty(((n + 15) // 16) * (nw + 1), dtype=torch.float32, device=dev)
+    _lib.insp_scorer_train_grad_tc(dims[0], dims[1], dims[2], dw, mode, n, dx, dt, part, g, loss)
+    torch.cuda.synchronize()
+    l_ref, g_ref = oracle.mlp_loss_grad(w.astype(np.float64), x, t, dims, mode)
+    assert float(loss.cpu()[0]) == pytest.approx(l_ref, rel=1e-6 if mode else 1e-4)
+    scale = np.abs(g_ref).max()
+    np.testing.assert_allclose(g.cpu().numpy(), g_ref, rtol=1e-4, atol=1e-5 * scale)
+    g2 = torch.zeros_like(g)
+    _lib.insp_scorer_train_grad_tc(dims[0], dims[1], dims[2], dw, mode, n, dx, dt, part, g2, loss)
+    assert torch.equal(g, g2)
+    work = torch.empty(n * (2 * dims[1] + 2 * dims[2] + 2), dtype=torch.float32, device=dev)
+    g3 = torch.zeros_like(g)
+    _lib.insp_scorer_train_grad(dims[0], dims[1], dims[2], dw, mode, n, dx, dt, work, g3, loss)
+    np.testing.assert_allclose(g.cpu().numpy(), g3.cpu().numpy(), rtol=1e-4, atol=1e-5 * scale)
+
+
+def test_training_time_tensor_cores_vs_fp32():
+    """Both forms on one minibatch of the trainer's shape (4096 samples, 16 -> 64 -> 64 -> 1,
+    quantisation-aware): the tensor-core form is timed beside the FP32 one (printed) and gives
+    the same gradient within the tolerance above."""
+    import torch
+    from paper_2404_03226_b300 import _lib, scorer
+    rng = np.random.default_rng(11)
+    nw = oracle.mlp_nweights_dims(16, 64, 64)
+    n = 4096
+    dev = torch.device("cuda")
+    w = torch.from_numpy(scorer.init_weights(3)).to(dev)
+    x = torch.from_numpy(rng.integers(0, 256, (n, 16)).astype(np.float32)).to(dev)
+    t = torch.from_numpy(rng.normal(0, 2, n).astype(np.float32)).to(dev)
+    g1, g2 = torch.zeros(nw, device=dev), torch.zeros(nw, device=dev)
+    loss = torch.zeros(1, device=dev)
+    part = torch.empty(((n + 15) // 16) * (nw + 1), device=dev)
+    work = torch.empty(n * (2 * 64 + 2 * 64 + 2), device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(3):
+        _lib.insp_scorer_train_grad_tc(16, 64, 64, w, 1, n, x, t, part, g1, loss)
+        _lib.insp_scorer_train_grad(16, 64, 64, w, 1, n, x, t, work, g2, loss)
+    ev[0].record()
+    for _ in range(20):
+        _lib.insp_scorer_train_grad_tc(16, 64, 64, w, 1, n, x, t, part, g1, loss)
+    ev[1].record()
+    ev[2].record()
+    for _ in range(20):
+        _lib.insp_scorer_train_grad(16, 64, 64, w, 1, n, x, t, work, g2, loss)
+    ev[3].record()
+    torch.cuda.synchronize()
+    tc, fp = ev[0].elapsed_time(ev[1]) / 20, ev[2].elapsed_time(ev[3]) / 20
+    print(f"gradient of a 4096-sample minibatch: tensor cores {tc:.3f} ms, FP32 CUDA cores {fp:.3f} ms")
+    scale = float(g2.abs().max())
+    np.testing.assert_allclose(g1.cpu().numpy(), g2.cpu().numpy(), rtol=1e-4, atol=1e-5 * scale)
