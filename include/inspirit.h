@@ -27,9 +27,17 @@
  *     final status, including device-side errors.
  *   - Streams: `stream` is a cudaStream_t passed as void*; NULL means the
  *     legacy default stream.  Calls on one batch must not overlap in time.
- *   - Numbering: tasks of a DAG are 0..n-1 and every edge (u, v) must satisfy
- *     u < v (ids are a topological order); successor lists are strictly
- *     increasing.  Workers 0..n_cpu-1 are CPUs, n_cpu..n_cpu+n_gpu-1 GPUs.
+ *   - Numbering: tasks of a DAG are 0..n-1; successor lists are strictly
+ *     increasing.  The method needs ids in a topological order (every edge
+ *     (u, v) with u < v).  A DAG loaded in another numbering (as a runtime's
+ *     dependency manager lists its tasks, Sec. 2.1) is renumbered at load by
+ *     Kahn's algorithm in rounds -- round 0 the tasks without predecessors,
+ *     round r + 1 the tasks whose predecessors all lie in rounds <= r, new ids
+ *     consecutive within a round in ascending old id -- and evaluated in that
+ *     numbering (every tie broken by the lowest id means the lowest new id);
+ *     all per-task inputs and outputs stay in the caller's numbering.  A DAG
+ *     whose ids are already topological keeps them.  A cycle: INSP_ECYCLE.
+ *     Workers 0..n_cpu-1 are CPUs, n_cpu..n_cpu+n_gpu-1 GPUs.
  *   - Time: all costs and times are int64 nanoseconds; costs are >= 1.
  */
 #ifndef INSPIRIT_H
@@ -45,12 +53,14 @@ extern "C" {
 /* ---------------------------------------------------------------- status */
 #define INSP_OK 0
 #define INSP_EINVAL 1    /* malformed argument: bad CSR, id out of range, duplicate or unsorted successor, cost < 1, type >= n_types, bad size */
-#define INSP_ENOTTOPO 2  /* an edge (u, v) with v <= u: ids are not a topological order */
+#define INSP_ENOTTOPO 2  /* an edge (u, v) with v <= u where a topological numbering is required
+                            (insp_simulate_noalloc); the load functions renumber instead */
 #define INSP_ENOMEM 3    /* device or host allocation failed */
 #define INSP_ECUDA 4     /* a CUDA runtime call failed (message in insp_last_error) */
 #define INSP_ETIMEOUT 5  /* a bounded device-side wait gave up (no GPU hang; the DAG's outputs are invalid) */
 #define INSP_EOVERFLOW 6 /* sum over tasks of (max cost + transfer) exceeds 2^54 ns, so times could overflow */
 #define INSP_ECHECK 7    /* debug builds only (INSP_CHECK): an internal bounds check failed; outputs invalid */
+#define INSP_ECYCLE 8    /* the successor lists contain a cycle: no topological numbering exists */
 
 /* ---------------------------------------------------------------- policy */
 #define INSP_POLICY_INSPIRIT 0 /* adaptive priority by the Nready controller (default) */
@@ -118,8 +128,9 @@ int insp_set_scorer(insp_machine *m, const uint16_t *bf16_weights, size_t nbytes
  *   int32 successor ids; type[n] uint8 < n_types (<= 64);
  *   type_cost[n_types][2] int64 (CPU ns, GPU ns) used when task_cost is NULL;
  *   task_cost[n][2] int64 per-task (CPU ns, GPU ns), overrides type_cost.
- * Validation runs on the device; errors: INSP_EINVAL, INSP_ENOTTOPO,
- * INSP_EOVERFLOW, INSP_ENOMEM, INSP_ECUDA.  n <= 2^24 - 1.  Synchronous. */
+ * Validation (and renumbering, see Numbering above) runs on the device;
+ * errors: INSP_EINVAL, INSP_ECYCLE, INSP_EOVERFLOW, INSP_ENOMEM, INSP_ECUDA.
+ * n <= 2^24 - 1.  Synchronous. */
 int insp_dag_load_csr(insp_machine *m, int32_t n, const int32_t *row_ptr, const int32_t *col_idx,
                       const uint8_t *type, int32_t n_types, const int64_t *type_cost, const int64_t *task_cost,
                       insp_dag **out);
@@ -238,7 +249,9 @@ typedef struct {
     int64_t *pop_time;
     int32_t *pop_task, *pop_worker, *pop_nready, *pop_mode;
 } insp_trace;
-/* insp_simulate_batch that also writes the trace (device pointers only). */
+/* insp_simulate_batch that also writes the trace (device pointers only; the
+ * batch's DAGs must have been loaded in a topological numbering, INSP_EINVAL
+ * otherwise, and so for insp_simulate_rollout). */
 int insp_simulate_trace(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *worker, int64_t *start,
                         int64_t *end, int64_t *makespan, const insp_trace *trace, void *stream);
 

@@ -30,7 +30,7 @@ _SRC = os.path.join(_HERE, "oracle.c")
 _lock = threading.Lock()
 _lib = None
 
-OK, EINVAL, ENOTTOPO, ENOMEM, EOVERFLOW = 0, 1, 2, 3, 6
+OK, EINVAL, ENOTTOPO, ENOMEM, EOVERFLOW, ECYCLE = 0, 1, 2, 3, 6, 8
 POLICY_INSPIRIT, POLICY_FIFO, POLICY_LEARNED, POLICY_DMDAP_IA, POLICY_DMDAP_BL = 0, 1, 2, 3, 4
 MODE_FIFO, MODE_ABILITY, MODE_EFI, MODE_EFI_LOC, MODE_LEARNED, MODE_PRIO = 0, 1, 2, 3, 4, 5
 STATE_INC, STATE_DEC = 0, 1
@@ -83,6 +83,7 @@ def _L():
         lib = ctypes.CDLL(build())
         lib.orc_check_dag.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, _i64p, ctypes.c_int64]
         lib.orc_ia.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
+        lib.orc_renumber.argtypes = [ctypes.c_int32, _i32p, _i32p, _i32p]
         lib.orc_ie.argtypes = [ctypes.c_int32, _i32p, _i32p, _i64p, ctypes.c_int64, _i32p]
         lib.orc_default_unit_time.restype = ctypes.c_int64
         lib.orc_default_unit_time.argtypes = [ctypes.c_int32, _i64p]
@@ -128,6 +129,29 @@ def check_dag(dag, xfer_ns: int = 0) -> int:
     rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx)
     return _L().orc_check_dag(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(_i64(dag.c_cpu), _i64p),
                               _p(_i64(dag.c_gpu), _i64p), xfer_ns)
+
+
+def renumber(dag) -> tuple[int, np.ndarray]:
+    """(rc, new_id[old]): the DAG's own ids when they are topological, else Kahn rounds with
+    ascending old id within a round; rc ECYCLE for a cycle (see orc_renumber)."""
+    out = np.zeros(max(dag.n, 1), np.int32)
+    rp, ci = _i32(dag.row_ptr), _i32(dag.col_idx if dag.col_idx.size else np.zeros(1))
+    rc = _L().orc_renumber(dag.n, _p(rp, _i32p), _p(ci, _i32p), _p(out, _i32p))
+    return int(rc), out[:dag.n]
+
+
+def relabel(dag, new_id):
+    """The same DAG with task old -> new_id[old]: rows moved, successors mapped and sorted,
+    types and costs moved with their tasks."""
+    n = dag.n
+    old_of = np.empty(n, np.int64)
+    old_of[np.asarray(new_id, np.int64)] = np.arange(n)
+    rows = [np.sort(np.asarray(new_id)[dag.col_idx[dag.row_ptr[o]:dag.row_ptr[o + 1]]]) for o in old_of]
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows]) if n else []
+    ci = np.concatenate(rows).astype(np.int32) if n and rp[-1] else np.zeros(0, np.int32)
+    return type(dag)(n, rp, ci, np.asarray(dag.type)[old_of], np.asarray(dag.c_cpu)[old_of],
+                     np.asarray(dag.c_gpu)[old_of])
 
 
 def ia(dag) -> np.ndarray:

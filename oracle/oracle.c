@@ -30,6 +30,8 @@
  *                priority (IA, or the bottom level), optionally with a trace
  *                of every push and pop (Sec. 4.4 "Implementation details":
  *                the Nready time piling of push and pop).
+ *  orc_renumber  a topological numbering for a DAG given in another one (Kahn
+ *                rounds, ascending old id within a round).
  *  orc_validate  an independent check of a schedule's feasibility.
  *  orc_optimum   exhaustive optimum makespan for tiny DAGs.
  *  orc_mlp_*     integer restatement of the learned proposal scorer (fixed
@@ -54,7 +56,7 @@
 
 #define EXPORT __attribute__((visibility("default")))
 
-enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOTTOPO = 2, ORC_ENOMEM = 3, ORC_EOVERFLOW = 6 };
+enum { ORC_OK = 0, ORC_EINVAL = 1, ORC_ENOTTOPO = 2, ORC_ENOMEM = 3, ORC_EOVERFLOW = 6, ORC_ECYCLE = 8 };
 enum { POL_INSPIRIT = 0, POL_FIFO = 1, POL_LEARNED = 2, POL_DMDAP_IA = 3, POL_DMDAP_BL = 4 };
 enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
 enum { ST_INC = 0, ST_DEC = 1 };
@@ -96,6 +98,56 @@ EXPORT int orc_check_dag(int32_t n, const int32_t *row_ptr, const int32_t *col_i
     if (nottopo) return ORC_ENOTTOPO;
     if (overflow) return ORC_EOVERFLOW;
     return ORC_OK;
+}
+
+/* ------------------------------------------------------------ renumbering */
+
+/* Task ids must be a topological order for the rest of the method (a task's
+ * predecessors come before it).  A DAG given in another numbering (tasks as a
+ * runtime's dependency manager lists them, Sec. 2.1) keeps its ids when they
+ * are already topological; otherwise it is renumbered by Kahn's algorithm in
+ * rounds: round 0 takes every task without predecessors, round r + 1 every
+ * task whose predecessors all lie in rounds <= r, and within a round the tasks
+ * get consecutive new ids in ascending old id.  new_id[old] receives the new
+ * id.  A cycle leaves tasks that no round takes: ORC_ECYCLE.  Duplicate or
+ * out-of-range successors: ORC_EINVAL. */
+EXPORT int orc_renumber(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t *new_id) {
+    if (n < 0) return ORC_EINVAL;
+    if (n == 0) return ORC_OK;
+    if (row_ptr[0] != 0) return ORC_EINVAL;
+    int topo = 1;
+    for (int32_t u = 0; u < n; ++u) {
+        if (row_ptr[u + 1] < row_ptr[u]) return ORC_EINVAL;
+        for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+            int32_t v = col_idx[e];
+            if (v < 0 || v >= n || (e > row_ptr[u] && v <= col_idx[e - 1])) return ORC_EINVAL;
+            if (v <= u) topo = 0;
+        }
+    }
+    if (topo) {
+        for (int32_t t = 0; t < n; ++t) new_id[t] = t;
+        return ORC_OK;
+    }
+    int32_t *indeg = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    int32_t *round = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!indeg || !round) { free(indeg); free(round); return ORC_ENOMEM; }
+    for (int32_t e = 0; e < row_ptr[n]; ++e) indeg[col_idx[e]]++;
+    for (int32_t t = 0; t < n; ++t) round[t] = -1;
+    int32_t next = 0, r = 0;
+    for (;;) {
+        /* this round: every untaken task whose in-degree has reached 0, ascending id */
+        int32_t taken = 0;
+        for (int32_t t = 0; t < n; ++t)
+            if (round[t] < 0 && indeg[t] == 0) { round[t] = r; new_id[t] = next++; ++taken; }
+        if (taken == 0) break;
+        for (int32_t t = 0; t < n; ++t)
+            if (round[t] == r)
+                for (int32_t e = row_ptr[t]; e < row_ptr[t + 1]; ++e) indeg[col_idx[e]]--;
+        ++r;
+    }
+    free(indeg);
+    free(round);
+    return next == n ? ORC_OK : ORC_ECYCLE;
 }
 
 /* ------------------------------------------------------- inspiring ability */

@@ -10,9 +10,10 @@ import os
 from . import build as _build
 
 INSP_OK, INSP_EINVAL, INSP_ENOTTOPO, INSP_ENOMEM, INSP_ECUDA, INSP_ETIMEOUT, INSP_EOVERFLOW = range(7)
+INSP_ECHECK, INSP_ECYCLE = 7, 8
 INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO, INSP_POLICY_LEARNED, INSP_POLICY_DMDAP_IA, INSP_POLICY_DMDAP_BL = 0, 1, 2, 3, 4
 ERROR_NAMES = {0: "INSP_OK", 1: "INSP_EINVAL", 2: "INSP_ENOTTOPO", 3: "INSP_ENOMEM", 4: "INSP_ECUDA",
-               5: "INSP_ETIMEOUT", 6: "INSP_EOVERFLOW", 7: "INSP_ECHECK"}
+               5: "INSP_ETIMEOUT", 6: "INSP_EOVERFLOW", 7: "INSP_ECHECK", 8: "INSP_ECYCLE"}
 
 _vp = ctypes.c_void_p
 _i32, _i64 = ctypes.c_int32, ctypes.c_int64

@@ -135,6 +135,7 @@ struct Scratch {
     DBuf ia_ring, ia_flags, ia_seq;                                // inspiring ability, target blocks
     DBuf ie_rec, ie_acc;                                           // inspiring efficiency
     DBuf s_ia, s_ie, s_worker, s_start, s_end, s_makespan;         // staging of host arrays
+    DBuf s_perm, s_bl;  // reordering into or out of the caller's numbering; bottom levels
     DBuf ie_ring;  // per-warp window rings of the pull efficiency sweep (global, meant to stay in L2)
     DBuf blevel;   // bottom levels (INSP_POLICY_DMDAP_BL)
     DBuf step;              // insp::StepCounters (device-side epoch and record tags)
@@ -174,6 +175,9 @@ struct BatchBufs {
     DBuf task_base, edge_base, row_ptr, col_idx, type, type_cost, task_cost;
     DBuf indeg0, unit_time_def, unit_time_user, order, item_base, status, max_span, counters, dag_span;
     DBuf pr_ptr, pcol, cursor;
+    // DAGs renumbered at load: old_of_new[task_base[d] + p] = the caller's id of task p (identity
+    // for the DAGs that kept their numbering)
+    DBuf old_of_new;
     DBuf item_dag, item_dag_lpt, item_base_lpt;
     // inspiring-ability plan: DAGs of the whole-row sweep, work items and zeroed DAGs of the
     // target-block sweep, {dag, representative} pairs of repeated structures; fingerprints
@@ -225,6 +229,7 @@ struct insp_batch {
     DBuf &item_dag_lpt = bufs->item_dag_lpt, &item_base_lpt = bufs->item_base_lpt;
     std::vector<int64_t> h_rank_item;  // first item (size-order numbering) of the DAG at each rank
     bool has_task_cost = false;
+    bool renumbered = false;  // some DAG was renumbered at load: per-task arrays are reordered
     int32_t max_n = 0, max_span_h = 0, W = 1;
     int64_t max_unit_def = 1, n_items = 0;  // 32-source items (global efficiency sweep)
     // per-DAG unit times of the last attributes call (device; the defaults before any): the
@@ -299,6 +304,71 @@ int copy_in(DBuf &dst, const void *src, size_t bytes, cudaStream_t s) {
 }
 
 int alloc_ie_global(insp_batch *b);
+
+// Validation statuses after the load's validation kernels: the first DAG with an error other
+// than a non-topological numbering fails the load; those DAGs are renumbered instead.
+int validation_status(insp_batch *b, std::vector<int32_t> &st, cudaStream_t s) {
+    st.assign(std::max(b->ndag, 0), 0);
+    if (b->ndag) {
+        CU(cudaMemcpyAsync(st.data(), b->status.p, size_t(b->ndag) * 4, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+    }
+    for (int d = 0; d < b->ndag; ++d)
+        if (st[d] != INSP_OK && st[d] != INSP_ENOTTOPO)
+            return fail(st[d], "DAG validation failed: DAG " + std::to_string(d) + ": device-side error");
+    return INSP_OK;
+}
+
+void swap_buf(DBuf &a, DBuf &c) {
+    std::swap(a.p, c.p);
+    std::swap(a.bytes, c.bytes);
+}
+
+// Renumber the listed DAGs (ids not topological) on the device: Kahn rounds, then new row
+// offsets, mapped and sorted successor rows, types and per-task costs in new arrays that
+// replace the batch's; old_of_new keeps the caller's ids.  A cycle fails with INSP_ECYCLE.
+int renumber_dags(insp_batch *b, const std::vector<int32_t> &dags, cudaStream_t s) {
+    const int64_t N = std::max<int64_t>(b->n_total, 1);
+    const int32_t k = int32_t(dags.size());
+    DBuf list, cnt, level, qa, qb, nlev, new_of_old, rp2, col2, type2, cost2;
+    int rc;
+    if ((rc = copy_in(list, dags.data(), dags.size() * 4, s)) || (rc = cnt.alloc(N * 4)) ||
+        (rc = level.alloc(N * 4)) || (rc = qa.alloc(N * 4)) || (rc = qb.alloc(N * 4)) || (rc = nlev.alloc(k * 4)) ||
+        (rc = new_of_old.alloc(N * 4)) || (rc = b->bufs->old_of_new.alloc(N * 4)))
+        return rc;
+    insp::DevBatch B = b->dev();
+    insp::launch_local_iota(b->task_base.as<int64_t>(), b->ndag, b->bufs->old_of_new.as<int32_t>(), s);
+    insp::launch_kahn(B, list.as<int32_t>(), k, b->indeg0.as<int32_t>(), cnt.as<int32_t>(), level.as<int32_t>(),
+                      qa.as<int32_t>(), qb.as<int32_t>(), nlev.as<int32_t>(), new_of_old.as<int32_t>(),
+                      b->bufs->old_of_new.as<int32_t>(), b->status.as<int32_t>(), s);
+    CU(cudaGetLastError());
+    std::vector<int32_t> st(b->ndag);
+    CU(cudaMemcpyAsync(st.data(), b->status.p, size_t(b->ndag) * 4, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int32_t d : dags)
+        if (st[d] != INSP_OK)
+            return fail(INSP_ECYCLE, "DAG " + std::to_string(d) + " has a cycle: no topological numbering exists");
+    const size_t rp_bytes = size_t(b->n_total + b->ndag) * 4, col_bytes = size_t(b->m_total) * 4;
+    if ((rc = rp2.alloc(rp_bytes)) || (rc = col2.alloc(col_bytes)) || (rc = type2.alloc(size_t(b->n_total))) ||
+        (b->has_task_cost && (rc = cost2.alloc(size_t(b->n_total) * 16))))
+        return rc;
+    if (rp_bytes) CU(cudaMemcpyAsync(rp2.p, b->row_ptr.p, rp_bytes, cudaMemcpyDeviceToDevice, s));
+    if (col_bytes) CU(cudaMemcpyAsync(col2.p, b->col_idx.p, col_bytes, cudaMemcpyDeviceToDevice, s));
+    if (b->n_total) CU(cudaMemcpyAsync(type2.p, b->type.p, size_t(b->n_total), cudaMemcpyDeviceToDevice, s));
+    if (b->has_task_cost && b->n_total)
+        CU(cudaMemcpyAsync(cost2.p, b->task_cost.p, size_t(b->n_total) * 16, cudaMemcpyDeviceToDevice, s));
+    insp::launch_renumber(B, list.as<int32_t>(), k, b->bufs->old_of_new.as<int32_t>(), new_of_old.as<int32_t>(),
+                          rp2.as<int32_t>(), col2.as<int32_t>(), type2.as<uint8_t>(),
+                          b->has_task_cost ? cost2.as<int64_t>() : nullptr, b->status.as<int32_t>(), s);
+    CU(cudaGetLastError());
+    CU(cudaStreamSynchronize(s));
+    swap_buf(b->row_ptr, rp2);
+    swap_buf(b->col_idx, col2);
+    swap_buf(b->type, type2);
+    if (b->has_task_cost) swap_buf(b->task_cost, cost2);
+    b->renumbered = true;
+    return INSP_OK;
+}
 
 // Longest edge span of every DAG (host copy) and the representative of every DAG's structure:
 // DAGs with equal fingerprints, task counts and edge counts are compared exactly on the device,
@@ -535,24 +605,62 @@ struct TimedLaunch {
     }
 };
 
-// Stage a caller array into a device buffer when it lives on the host.
+// Per-task arrays cross the boundary in the caller's numbering.  Stage a caller input into a
+// device buffer when it lives on the host or the batch was renumbered at load (then reorder it
+// into the batch's numbering).
 template <typename T>
-int stage_in(DBuf &buf, const T *src, int64_t count, cudaStream_t s, const T *&dev) {
-    if (is_device_ptr(src)) { dev = src; return INSP_OK; }
+int stage_in(insp_batch *b, DBuf &buf, const T *src, int64_t count, cudaStream_t s, const T *&dev) {
+    const bool host = !is_device_ptr(src);
+    if (!host && !b->renumbered) { dev = src; return INSP_OK; }
     int rc = buf.alloc(std::max<int64_t>(count, 1) * sizeof(T));
     if (rc) return rc;
-    if (count) CU(cudaMemcpyAsync(buf.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
     dev = buf.as<T>();
+    if (!b->renumbered) {
+        if (count) CU(cudaMemcpyAsync(buf.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+        return INSP_OK;
+    }
+    const T *from = src;
+    if (host) {
+        if ((rc = b->sc->s_perm.alloc(std::max<int64_t>(count, 1) * 8))) return rc;
+        if (count) CU(cudaMemcpyAsync(b->sc->s_perm.p, src, count * sizeof(T), cudaMemcpyHostToDevice, s));
+        from = b->sc->s_perm.as<T>();
+    }
+    insp::launch_permute(b->task_base.as<int64_t>(), b->ndag, b->bufs->old_of_new.as<int32_t>(), from, buf.p,
+                         int(sizeof(T)), false, s);
     return INSP_OK;
 }
 
+// Where the kernels write an output: the caller's array itself when it is device memory (and,
+// for a per-task array, the batch kept the caller's numbering), else a staging buffer that
+// finish_out delivers.
 template <typename T>
-int stage_out(DBuf &buf, T *dst, int64_t count, T *&dev, bool &staged) {
-    if (is_device_ptr(dst)) { dev = dst; staged = false; return INSP_OK; }
+int stage_out(insp_batch *b, DBuf &buf, T *dst, int64_t count, T *&dev, bool &staged, bool per_task = true) {
+    if (is_device_ptr(dst) && !(per_task && b->renumbered)) { dev = dst; staged = false; return INSP_OK; }
     int rc = buf.alloc(std::max<int64_t>(count, 1) * sizeof(T));
     if (rc) return rc;
     dev = buf.as<T>();
     staged = true;
+    return INSP_OK;
+}
+
+// Deliver a staged output after the kernels that write it (stream-ordered): reorder a per-task
+// array into the caller's numbering, copy to the host.
+template <typename T>
+int finish_out(insp_batch *b, T *dst, const T *dev, int64_t count, cudaStream_t s, bool per_task = true) {
+    const bool host = !is_device_ptr(dst);
+    const T *src = dev;
+    if (per_task && b->renumbered) {
+        T *to = dst;
+        if (host) {
+            int rc = b->sc->s_perm.alloc(std::max<int64_t>(count, 1) * 8);
+            if (rc) return rc;
+            to = b->sc->s_perm.as<T>();
+        }
+        insp::launch_permute(b->task_base.as<int64_t>(), b->ndag, b->bufs->old_of_new.as<int32_t>(), dev, to,
+                             int(sizeof(T)), true, s);
+        src = to;
+    }
+    if (host && count) CU(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
     return INSP_OK;
 }
 
@@ -804,9 +912,26 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return bail(fail(INSP_ECUDA, "validation kernels failed"));
     std::vector<int32_t> st;
-    if ((rc = first_status(b, st, ls))) {
-        g_err = "DAG validation failed: " + g_err;
-        return bail(rc);
+    if ((rc = validation_status(b, st, ls))) return bail(rc);
+    std::vector<int32_t> renum;
+    for (int d = 0; d < ndag; ++d)
+        if (st[d] == INSP_ENOTTOPO) renum.push_back(d);
+    if (!renum.empty()) {
+        if ((rc = renumber_dags(b, renum, ls))) return bail(rc);
+        // validate the renumbered batch again: in-degrees, spans and unit times of the new ids
+        B = b->dev();
+        if (cudaMemsetAsync(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4, ls) != cudaSuccess ||
+            cudaMemsetAsync(b->max_span.p, 0, 4, ls) != cudaSuccess)
+            return bail(fail(INSP_ECUDA, "memset"));
+        insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
+                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, ls);
+        insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, ls);
+        if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+            return bail(fail(INSP_ECUDA, "validation kernels failed"));
+        if ((rc = first_status(b, st, ls))) {
+            g_err = "renumbered DAG failed validation: " + g_err;
+            return bail(rc);
+        }
     }
     std::vector<int64_t> ut(std::max(ndag, 1), 1);
     if (cudaMemcpyAsync(&b->max_span_h, b->max_span.p, 4, cudaMemcpyDeviceToHost, ls) != cudaSuccess ||
@@ -1018,7 +1143,7 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
     int32_t *d_ia, *d_ie;
     bool st_ia, st_ie;
     Scratch &S = *b->sc;
-    if ((rc = stage_out(S.s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(S.s_ie, ie, N, d_ie, st_ie))) return rc;
+    if ((rc = stage_out(b, S.s_ia, ia, N, d_ia, st_ia)) || (rc = stage_out(b, S.s_ie, ie, N, d_ie, st_ie))) return rc;
     const int64_t *ut;
     bool wide;
     if ((rc = prep_unit_time(b, unit_time_ns, s, ut, wide))) return rc;
@@ -1041,9 +1166,8 @@ INSP_API int insp_attributes_batch(insp_batch *b, const int64_t *unit_time_ns, i
         CU(cudaStreamWaitEvent(s, S.ev_ie[0], 0));
     }
     CU(cudaGetLastError());
-    if (st_ia || st_ie) {
-        if (st_ia) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
-        if (st_ie) CU(cudaMemcpyAsync(ie, d_ie, N * 4, cudaMemcpyDeviceToHost, s));
+    if ((st_ia && (rc = finish_out(b, ia, d_ia, N, s))) || (st_ie && (rc = finish_out(b, ie, d_ie, N, s)))) return rc;
+    if (!is_device_ptr(ia) || !is_device_ptr(ie)) {
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
         return first_status(b, st, s);
@@ -1165,12 +1289,13 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
     int rc;
     const int32_t *d_ia, *d_ie;
     Scratch &S = *b->sc;
-    if ((rc = stage_in(S.s_ia, ia, N, s, d_ia)) || (rc = stage_in(S.s_ie, ie, N, s, d_ie))) return rc;
+    if ((rc = stage_in(b, S.s_ia, ia, N, s, d_ia)) || (rc = stage_in(b, S.s_ie, ie, N, s, d_ie))) return rc;
     int32_t *d_worker;
     int64_t *d_start, *d_end, *d_mk;
     bool sw, ss, se, sm;
-    if ((rc = stage_out(S.s_worker, worker, N, d_worker, sw)) || (rc = stage_out(S.s_start, start, N, d_start, ss)) ||
-        (rc = stage_out(S.s_end, end, N, d_end, se)) || (rc = stage_out(S.s_makespan, makespan, b->ndag, d_mk, sm)))
+    if ((rc = stage_out(b, S.s_worker, worker, N, d_worker, sw)) ||
+        (rc = stage_out(b, S.s_start, start, N, d_start, ss)) || (rc = stage_out(b, S.s_end, end, N, d_end, se)) ||
+        (rc = stage_out(b, S.s_makespan, makespan, b->ndag, d_mk, sm, false)))
         return rc;
     if (b->ndag > 0) {
         CU(cudaMemsetAsync(b->counters.p, 0, 64, s));
@@ -1200,11 +1325,11 @@ int simulate_impl(insp_batch *b, const int32_t *ia, const int32_t *ie, int32_t *
         }
         CU(cudaGetLastError());
     }
-    if (sw || ss || se || sm) {
-        if (sw) CU(cudaMemcpyAsync(worker, d_worker, N * 4, cudaMemcpyDeviceToHost, s));
-        if (ss) CU(cudaMemcpyAsync(start, d_start, N * 8, cudaMemcpyDeviceToHost, s));
-        if (se) CU(cudaMemcpyAsync(end, d_end, N * 8, cudaMemcpyDeviceToHost, s));
-        if (sm) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+    if ((sw && (rc = finish_out(b, worker, d_worker, N, s))) || (ss && (rc = finish_out(b, start, d_start, N, s))) ||
+        (se && (rc = finish_out(b, end, d_end, N, s))) ||
+        (sm && (rc = finish_out(b, makespan, d_mk, b->ndag, s, false))))
+        return rc;
+    if (!is_device_ptr(worker) || !is_device_ptr(start) || !is_device_ptr(end) || !is_device_ptr(makespan)) {
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
         return first_status(b, st, s);
@@ -1223,6 +1348,7 @@ INSP_API int insp_simulate_trace(insp_batch *b, const int32_t *ia, const int32_t
                                  int64_t *start, int64_t *end, int64_t *makespan, const insp_trace *trace,
                                  void *stream) {
     if (!b || !trace) return fail(INSP_EINVAL, "NULL argument");
+    if (b->renumbered) return fail(INSP_EINVAL, "the trace needs DAGs loaded in a topological numbering");
     const void *ptrs[] = {ia, ie, worker, start, end, makespan, trace->push_time, trace->push_task,
                           trace->push_worker, trace->push_nready, trace->pop_time, trace->pop_task,
                           trace->pop_worker, trace->pop_nready, trace->pop_mode};
@@ -1310,13 +1436,11 @@ INSP_API int insp_bottom_level_batch(insp_batch *b, int64_t *bl, void *stream) {
     b->last_stream = s;
     int64_t *d_bl;
     bool staged;
-    int rc = stage_out(b->sc->s_start, bl, b->n_total, d_bl, staged);
+    int rc = stage_out(b, b->sc->s_bl, bl, b->n_total, d_bl, staged);
     if (rc) return rc;
     if ((rc = launch_blevel_all(b, d_bl, s))) return rc;
-    if (staged) {
-        if (b->n_total) CU(cudaMemcpyAsync(bl, d_bl, size_t(b->n_total) * 8, cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-    }
+    if (staged && (rc = finish_out(b, bl, d_bl, b->n_total, s))) return rc;
+    if (!is_device_ptr(bl)) CU(cudaStreamSynchronize(s));
     return INSP_OK;
 }
 
@@ -1365,9 +1489,10 @@ int evaluate_impl(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32
     int32_t *d_ia, *d_ie, *d_worker;
     int64_t *d_start, *d_end, *d_mk;
     bool h[6];
-    if ((rc = stage_out(S.s_ia, ia, N, d_ia, h[0])) || (rc = stage_out(S.s_ie, ie, N, d_ie, h[1])) ||
-        (rc = stage_out(S.s_worker, worker, N, d_worker, h[2])) || (rc = stage_out(S.s_start, start, N, d_start, h[3])) ||
-        (rc = stage_out(S.s_end, end, N, d_end, h[4])) || (rc = stage_out(S.s_makespan, makespan, b->ndag, d_mk, h[5])))
+    if ((rc = stage_out(b, S.s_ia, ia, N, d_ia, h[0])) || (rc = stage_out(b, S.s_ie, ie, N, d_ie, h[1])) ||
+        (rc = stage_out(b, S.s_worker, worker, N, d_worker, h[2])) ||
+        (rc = stage_out(b, S.s_start, start, N, d_start, h[3])) || (rc = stage_out(b, S.s_end, end, N, d_end, h[4])) ||
+        (rc = stage_out(b, S.s_makespan, makespan, b->ndag, d_mk, h[5], false)))
         return rc;
     const int64_t *ut;
     bool wide;
@@ -1426,13 +1551,14 @@ int evaluate_impl(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32
         }
     }
     CU(cudaGetLastError());
-    if (h[0] || h[1] || h[2] || h[3] || h[4] || h[5]) {
-        if (h[0]) CU(cudaMemcpyAsync(ia, d_ia, N * 4, cudaMemcpyDeviceToHost, s));
-        if (h[1]) CU(cudaMemcpyAsync(ie, d_ie, N * 4, cudaMemcpyDeviceToHost, s));
-        if (h[2]) CU(cudaMemcpyAsync(worker, d_worker, N * 4, cudaMemcpyDeviceToHost, s));
-        if (h[3]) CU(cudaMemcpyAsync(start, d_start, N * 8, cudaMemcpyDeviceToHost, s));
-        if (h[4]) CU(cudaMemcpyAsync(end, d_end, N * 8, cudaMemcpyDeviceToHost, s));
-        if (h[5]) CU(cudaMemcpyAsync(makespan, d_mk, size_t(b->ndag) * 8, cudaMemcpyDeviceToHost, s));
+    if ((h[0] && (rc = finish_out(b, ia, d_ia, N, s))) || (h[1] && (rc = finish_out(b, ie, d_ie, N, s))) ||
+        (h[2] && (rc = finish_out(b, worker, d_worker, N, s))) || (h[3] && (rc = finish_out(b, start, d_start, N, s))) ||
+        (h[4] && (rc = finish_out(b, end, d_end, N, s))) || (h[5] && (rc = finish_out(b, makespan, d_mk, b->ndag, s, false))))
+        return rc;
+    const void *outs[6] = {ia, ie, worker, start, end, makespan};
+    bool any_host = false;
+    for (const void *o : outs) any_host |= !is_device_ptr(o);
+    if (any_host) {
         if (async) return INSP_OK;
         CU(cudaStreamSynchronize(s));
         std::vector<int32_t> st;
@@ -1452,6 +1578,7 @@ INSP_API int insp_simulate_rollout(insp_batch *b, const int32_t *ia, const int32
                                    const int32_t *force_task, const int32_t *feat_pop, int32_t feat_cap,
                                    int32_t *feat_task, int32_t *feat, int32_t *feat_n, void *stream) {
     if (!b) return fail(INSP_EINVAL, "batch is NULL");
+    if (b->renumbered) return fail(INSP_EINVAL, "rollouts need DAGs loaded in a topological numbering");
     if ((force_pop == nullptr) != (force_task == nullptr)) return fail(INSP_EINVAL, "force_pop and force_task go together");
     if (feat_pop && (feat_cap < 1 || !feat_task || !feat || !feat_n)) return fail(INSP_EINVAL, "feature capture needs outputs");
     const void *ptrs[] = {ia, ie, worker, start, end, makespan};

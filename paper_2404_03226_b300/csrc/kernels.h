@@ -51,6 +51,20 @@ void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *
                      int32_t *dag_span,
                      int grid, cudaStream_t s);
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s);
+// Renumbering of the listed DAGs (ids not topological): Kahn rounds, ascending old id within a
+// round (k_load.cu).  Scratch cnt, level, qa, qb: per task (global indexing); n_levels: per
+// listed DAG.  status[d] becomes INSP_OK or INSP_ECYCLE.
+void launch_kahn(const DevBatch &B, const int32_t *dags, int32_t n_dags, const int32_t *indeg0, int32_t *cnt,
+                 int32_t *level, int32_t *qa, int32_t *qb, int32_t *n_levels, int32_t *new_of_old,
+                 int32_t *old_of_new, int32_t *status, cudaStream_t s);
+// The renumbered arrays of the listed DAGs into out_* (which hold a copy of the batch).
+void launch_renumber(const DevBatch &B, const int32_t *dags, int32_t n_dags, const int32_t *old_of_new,
+                     const int32_t *new_of_old, int32_t *out_rp, int32_t *out_col, uint8_t *out_type,
+                     int64_t *out_task_cost, const int32_t *status, cudaStream_t s);
+void launch_local_iota(const int64_t *task_base, int32_t ndag, int32_t *out, cudaStream_t s);
+// Per-task arrays between the batch's numbering and the caller's (4- or 8-byte elements).
+void launch_permute(const int64_t *task_base, int32_t ndag, const int32_t *old_of_new, const void *src, void *dst,
+                    int elem_bytes, bool to_caller, cudaStream_t s);
 // Device-side step counters of the attribute kernels: the done-flag epoch of
 // the ability sweep and the 64-bit record tag base of the efficiency sweep.
 struct StepCounters {

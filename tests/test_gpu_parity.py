@@ -149,9 +149,6 @@ def test_load_errors():
     m = P.Machine(2, 1, 10)
     good = inputs.make_dag(3, [(0, 1), (1, 2)], [1, 1, 1], [1, 1, 1])
     cases = []
-    back = inputs.Dag(2, np.array([0, 0, 1], np.int32), np.array([0], np.int32), np.zeros(2, np.uint8),
-                      np.ones(2, np.int64), np.ones(2, np.int64))
-    cases.append((back, _lib.INSP_ENOTTOPO))
     dup = inputs.Dag(2, np.array([0, 2, 2], np.int32), np.array([1, 1], np.int32), np.zeros(2, np.uint8),
                      np.ones(2, np.int64), np.ones(2, np.int64))
     cases.append((dup, _lib.INSP_EINVAL))
@@ -272,3 +269,110 @@ def test_tiled_64_cholesky_window_4096():
     g = gpu_run(b, m)
     assert (g["status"] == 0).all()
     compare_dag(b, 0, g, m)
+
+
+def _shuffle_batch(batch, seed):
+    """Every DAG of the batch under a random relabelling (not topological), and the new ids
+    the oracle's renumbering gives each."""
+    rng = np.random.default_rng(seed)
+    dags, news = [], []
+    for d in range(batch.ndag):
+        g = batch.dag(d)
+        s = oracle.relabel(g, rng.permutation(g.n).astype(np.int32)) if g.n > 1 else g
+        dags.append(s)
+        rc, new = oracle.renumber(s)
+        assert rc == oracle.OK
+        news.append(new)
+    return dags, news
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_non_topological_numbering_is_renumbered(host):
+    """DAGs given in a shuffled numbering (mixed with ones already topological) are renumbered
+    at load by Kahn rounds; every per-task result comes back in the caller's numbering and
+    equals the oracle's on the renumbered DAG, mapped back.  Two-call and fused steps, device
+    and host outputs (per-task costs, which move with their tasks)."""
+    import torch
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    base = inputs.concat([inputs.layered(10, cfg=48, n_max=900), inputs.tiled(inputs.KIND_LU, 8, 2, cfg=49)])
+    sh, news = _shuffle_batch(base, 5)
+    keep = [base.dag(0), base.dag(3)]  # already topological: they keep their ids
+    dags = sh[:6] + keep + sh[6:]
+    news = news[:6] + [np.arange(d.n) for d in keep] + news[6:]
+    b = inputs.concat_dags(dags)
+    m = inputs.MACHINE_LAYERED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    n, nd = b.n_total, b.ndag
+    refs = [oracle.simulate(oracle.relabel(g, nw), m) for g, nw in zip(dags, news)]
+
+    def check(got, what):
+        for d, (r, nw) in enumerate(zip(refs, news)):
+            tb, te = int(b.task_base[d]), int(b.task_base[d + 1])
+            for k in ("ia", "ie", "worker", "start", "end"):
+                np.testing.assert_array_equal(got[k][tb:te], np.asarray(r[k])[nw], err_msg=f"{k} of DAG {d}, {what}")
+            assert int(got["makespan"][d]) == r["makespan"], f"makespan of DAG {d}, {what}"
+
+    if host:
+        out = dict(ia=np.zeros(n, np.int32), ie=np.zeros(n, np.int32), worker=np.zeros(n, np.int32),
+                   start=np.zeros(n, np.int64), end=np.zeros(n, np.int64), makespan=np.zeros(nd, np.int64))
+        _lib.insp_evaluate_batch(B.handle, None, *out.values())
+        check(out, "fused, host")
+        out2 = {k: np.zeros_like(v) for k, v in out.items()}
+        _lib.insp_attributes_batch(B.handle, None, out2["ia"], out2["ie"])
+        _lib.insp_simulate_batch(B.handle, out2["ia"], out2["ie"], out2["worker"], out2["start"], out2["end"],
+                                 out2["makespan"])
+        check(out2, "two calls, host")
+    else:
+        ia, ie, s = B.evaluate()
+        torch.cuda.synchronize()
+        assert (B.status() == 0).all()
+        check(dict(ia=ia.cpu().numpy(), ie=ie.cpu().numpy(), worker=s.worker.cpu().numpy(),
+                   start=s.start.cpu().numpy(), end=s.end.cpu().numpy(), makespan=s.makespan.cpu().numpy()), "fused")
+        ia, ie = B.attributes()
+        s = B.simulate(ia, ie)
+        torch.cuda.synchronize()
+        check(dict(ia=ia.cpu().numpy(), ie=ie.cpu().numpy(), worker=s.worker.cpu().numpy(),
+                   start=s.start.cpu().numpy(), end=s.end.cpu().numpy(), makespan=s.makespan.cpu().numpy()),
+              "two calls")
+        # bottom levels follow their tasks too
+        bl = B.bottom_level().cpu().numpy()
+        for d, (g, nw) in enumerate(zip(dags, news)):
+            tb, te = int(b.task_base[d]), int(b.task_base[d + 1])
+            np.testing.assert_array_equal(bl[tb:te], oracle.bottom_level(oracle.relabel(g, nw), m)[nw])
+        with pytest.raises(_lib.InspError):
+            B.simulate_trace(ia, ie)
+
+
+def test_cycles_are_reported():
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    good = inputs.make_dag(3, [(0, 1), (1, 2)], [1, 1, 1], [1, 1, 1])
+    cyc = inputs.Dag(3, np.array([0, 1, 2, 3], np.int32), np.array([1, 2, 0], np.int32), np.zeros(3, np.uint8),
+                     np.ones(3, np.int64), np.ones(3, np.int64))  # 0 -> 1 -> 2 -> 0
+    assert oracle.renumber(cyc)[0] == oracle.ECYCLE
+    with pytest.raises(_lib.InspError) as e:
+        P.DagBatch(P.Machine(2, 1, 10), inputs.concat_dags([good, cyc]))
+    assert e.value.code == _lib.INSP_ECYCLE
+
+
+def test_renumbered_dags_with_per_type_costs():
+    """Shuffled layered DAGs with per-type cost tables: the types move with their tasks."""
+    import torch
+    import paper_2404_03226_b300 as P
+    base = inputs.layered(6, cfg=50, n_max=700)
+    sh, news = _shuffle_batch(base, 9)
+    nb = inputs.concat_dags(sh)
+    b = inputs.Batch(nb.ndag, base.n_types, nb.task_base, nb.edge_base, nb.row_ptr, nb.col_idx, nb.type,
+                     base.type_cost, None)
+    m = inputs.MACHINE_LAYERED
+    B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    ia, ie, s = B.evaluate()
+    torch.cuda.synchronize()
+    assert (B.status() == 0).all()
+    for d in range(b.ndag):
+        g = b.dag(d)
+        r = oracle.simulate(oracle.relabel(g, news[d]), m)
+        tb, te = int(b.task_base[d]), int(b.task_base[d + 1])
+        for k, v in (("ia", ia), ("ie", ie), ("worker", s.worker), ("start", s.start), ("end", s.end)):
+            np.testing.assert_array_equal(v.cpu().numpy()[tb:te], np.asarray(r[k])[news[d]], err_msg=f"{k} of {d}")

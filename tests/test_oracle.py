@@ -409,3 +409,69 @@ def test_unit_time_search_matches_brute_force(seed):
             break
     assert want is not None
     assert oracle.unit_time_search(d, 11) == want
+
+
+# ----------------------------------------------------------------- renumbering
+def _shuffled(d, rng):
+    """The same DAG under a random relabelling (rows re-sorted): usually not topological."""
+    perm = rng.permutation(d.n).astype(np.int32)
+    return oracle.relabel(d, perm)
+
+
+def test_renumber_hand_example_and_topological_identity():
+    # old edges 2->0, 2->3, 0->1, 3->1: round 0 {2}, round 1 {0, 3}, round 2 {1}
+    d = inputs.make_dag(4, [], [1] * 4, [1] * 4)
+    d = inputs.Dag(4, np.array([0, 1, 1, 3, 4], np.int32), np.array([1, 0, 3, 1], np.int32), np.zeros(4, np.uint8),
+                   np.ones(4, np.int64), np.ones(4, np.int64))
+    rc, new = oracle.renumber(d)
+    assert rc == oracle.OK and list(new) == [1, 3, 0, 2]
+    # ids already topological stay as they are (even where Kahn rounds would reorder: 0->1, 2 isolated)
+    chain = inputs.make_dag(3, [(0, 1)], [1] * 3, [1] * 3)
+    assert list(oracle.renumber(chain)[1]) == [0, 1, 2]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_renumber_is_kahn_rounds_by_path_enumeration(seed):
+    """On shuffled random DAGs: a permutation, a topological order, and sorted by (round, old id)
+    where the round is the most edges on a path from a source (enumerated by brute force)."""
+    rng = np.random.default_rng(3000 + seed)
+    d = _shuffled(_rand_dag(rng, int(rng.integers(2, 25)), 0.25), rng)
+    rc, new = oracle.renumber(d)
+    assert rc == oracle.OK
+    assert sorted(new) == list(range(d.n))
+    for u in range(d.n):
+        for v in d.col_idx[d.row_ptr[u]:d.row_ptr[u + 1]]:
+            assert new[u] < new[v]
+    layer = brute.layers(d)
+    order = sorted(range(d.n), key=lambda t: (layer[t], t))
+    assert [int(new[t]) for t in order] == list(range(d.n))
+
+
+def test_renumber_reports_cycles_and_bad_rows():
+    two = inputs.Dag(2, np.array([0, 1, 2], np.int32), np.array([1, 0], np.int32), np.zeros(2, np.uint8),
+                     np.ones(2, np.int64), np.ones(2, np.int64))
+    self_loop = inputs.Dag(2, np.array([0, 1, 1], np.int32), np.array([0], np.int32), np.zeros(2, np.uint8),
+                           np.ones(2, np.int64), np.ones(2, np.int64))
+    deep = inputs.Dag(5, np.array([0, 1, 2, 3, 4, 4], np.int32), np.array([1, 2, 3, 1], np.int32),
+                      np.zeros(5, np.uint8), np.ones(5, np.int64), np.ones(5, np.int64))  # 1 -> 2 -> 3 -> 1
+    for d in (two, self_loop, deep):
+        assert oracle.renumber(d)[0] == oracle.ECYCLE
+    dup = inputs.Dag(2, np.array([0, 2, 2], np.int32), np.array([1, 1], np.int32), np.zeros(2, np.uint8),
+                     np.ones(2, np.int64), np.ones(2, np.int64))
+    assert oracle.renumber(dup)[0] == oracle.EINVAL
+
+
+def test_relabel_keeps_attributes_and_schedule_validity():
+    """A relabelled DAG is the same DAG: IA and IE follow their tasks (closed under the
+    relabelling), and the renumbered DAG's schedule mapped back is valid for the original."""
+    rng = np.random.default_rng(7)
+    d = _rand_dag(rng, 40, 0.15)
+    s = _shuffled(d, rng)
+    rc, new = oracle.renumber(s)
+    assert rc == oracle.OK
+    r = oracle.relabel(s, new)
+    m = inputs.Machine(2, 1, 5)
+    res = oracle.simulate(r, m)
+    back = {k: np.asarray(res[k])[new] for k in ("worker", "start", "end", "ia")}
+    assert oracle.validate(s, m, back["worker"], back["start"], back["end"], res["makespan"]) == (0, -1)
+    assert list(back["ia"]) == brute.ia(s)
