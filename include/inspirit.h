@@ -359,7 +359,7 @@ typedef struct {
                               one before (the largest DAGs, whose simulations take longest, start first) */
     int32_t ia_block;      /* ability sweep: 0: DAGs of up to 16384 tasks keep one bitset row of n bits per task
                               in one CTA (n x n bits), larger ones are cut into target blocks; 1: every DAG
-                              is cut into blocks of 2048 target ids, one CTA per (DAG, block), rows in a ring
+                              is cut into blocks of 8192 target ids, one CTA per (DAG, block), rows in a ring
                               of (longest edge span + warps) slots per CTA, so memory does not grow with n */
 } insp_tuning;
 
@@ -396,6 +396,18 @@ int insp_selftest_wait(int32_t flag_value, int32_t wait_value, int32_t limit, vo
  * Steps replayed from a recorded graph are not timed. */
 int insp_batch_set_timing(insp_batch *b, int32_t enable);
 int insp_batch_timing(insp_batch *b, double *ms, int64_t *launches, int32_t reset);
+
+/* Replace the policy a batch was loaded with (its machine's), e.g. to sweep the
+ * controller parameters of Sec. 4.4 over resident DAGs without reloading them.
+ * Same rules as insp_machine_create's policy; INSP_POLICY_LEARNED needs a
+ * scorer installed on the batch's machine.  Later simulate / evaluate calls use
+ * it (a recorded graph keeps the old one: record again).  Errors: INSP_EINVAL,
+ * INSP_ENOMEM. */
+int insp_batch_set_policy(insp_batch *b, const insp_policy *policy);
+
+/* Number of distinct DAG structures (tasks and successor lists) in the batch:
+ * repeated structures share one inspiring-ability sweep. */
+int insp_batch_structures(const insp_batch *b, int32_t *n_distinct);
 
 /* Batch facts: number of DAGs, total tasks, total edges. */
 int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges);

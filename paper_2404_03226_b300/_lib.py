@@ -70,6 +70,8 @@ _PROTOS = {
     "insp_simulate_per_dag": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "insp_batch_status": (ctypes.c_int, [_vp, _vp]),
     "insp_batch_info": (ctypes.c_int, [_vp, ctypes.POINTER(_i32), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "insp_batch_set_policy": (ctypes.c_int, [_vp, ctypes.POINTER(insp_policy)]),
+    "insp_batch_structures": (ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     "insp_batch_set_timing": (ctypes.c_int, [_vp, _i32]),
     "insp_batch_timing": (ctypes.c_int, [_vp, _vp, _vp, _i32]),
     "insp_scorer_eval": (ctypes.c_int, [_vp, _vp, _i64, _vp, _vp]),
@@ -226,6 +228,16 @@ def insp_batch_info(b) -> tuple[int, int, int]:
     nd, nt, ne = _i32(), _i64(), _i64()
     check(lib().insp_batch_info(b, ctypes.byref(nd), ctypes.byref(nt), ctypes.byref(ne)))
     return nd.value, nt.value, ne.value
+
+
+def insp_batch_structures(b) -> int:
+    k = _i32()
+    check(lib().insp_batch_structures(b, ctypes.byref(k)))
+    return k.value
+
+
+def insp_batch_set_policy(b, policy: insp_policy) -> None:
+    check(lib().insp_batch_set_policy(b, ctypes.byref(policy)))
 
 
 def insp_batch_set_timing(b, enable: bool) -> None:

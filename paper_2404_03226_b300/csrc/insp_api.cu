@@ -96,9 +96,12 @@ int device_info(DeviceInfo &di) {
 
 constexpr int MAX_GROUPS = 16;
 // The tuning a batch starts with: what the autotuner picks on the 4096-DAG layered workload
-// (one group, overlapped attribute sweeps, 4-warp efficiency CTAs with a 1 GB ring budget,
-// 2-warp simulation CTAs with 32-entry pools, whole-DAG bitsets for the ability sweep).
-const insp_tuning kDefaultTuning = {1, 1, 16, 4, 1024, 2, 32, 0, 0};
+// (one group, overlapped attribute sweeps, 4-warp efficiency CTAs, 2-warp simulation CTAs with
+// 32-entry pools, whole-DAG bitsets for the ability sweep), with a 16 GB ring budget for the
+// efficiency sweep: enough for every resident warp up to the largest window (8192 rows, 2 MB
+// per warp), where a 1 GB budget left DAGs with long edges at a tenth of the warps (tiled and
+// mixed-size workloads 2.5x and 10x slower); with short windows the grid stops at occupancy.
+const insp_tuning kDefaultTuning = {1, 1, 16, 4, 16384, 2, 32, 0, 0};
 // Largest DAG whose inspiring ability takes whole-DAG bitset rows (n x n bits in one CTA slot)
 // when the tuning's ia_block is 0; larger DAGs always take the target-block sweep.
 constexpr int32_t IA_FULL_MAX = 16384;
@@ -1023,6 +1026,30 @@ INSP_API void insp_batch_destroy(insp_batch *b) {
 }
 INSP_API void insp_dag_destroy(insp_dag *d) { insp_batch_destroy(d); }
 
+INSP_API int insp_batch_set_policy(insp_batch *b, const insp_policy *policy) {
+    if (!b || !policy) return fail(INSP_EINVAL, "NULL argument");
+    const insp_policy &p = *policy;
+    if (p.policy < INSP_POLICY_INSPIRIT || p.policy > INSP_POLICY_DMDAP_BL) return fail(INSP_EINVAL, "unknown policy");
+    if (p.task_window < 0 || p.s_inc < 0 || p.s_dec < 0 || p.dec_step < 0 || p.c < 0 || p.k_inc_tasks < 0 ||
+        p.k_inc_ns < 0)
+        return fail(INSP_EINVAL, "policy parameters must be >= 0 (0 = default)");
+    if (p.policy == INSP_POLICY_LEARNED && !(b->owner && b->owner->has_scorer))
+        return fail(INSP_EINVAL, "INSP_POLICY_LEARNED needs a scorer installed with insp_set_scorer");
+    if (p.policy == INSP_POLICY_DMDAP_BL) {
+        const int rc = b->sc->blevel.alloc(std::max<int64_t>(b->n_total, 1) * 8);
+        if (rc) return rc;
+    }
+    b->mach_params.pol = p;
+    b->mach_params.has_scorer = b->owner && b->owner->has_scorer;
+    return INSP_OK;
+}
+
+INSP_API int insp_batch_structures(const insp_batch *b, int32_t *n_distinct) {
+    if (!b || !n_distinct) return fail(INSP_EINVAL, "NULL argument");
+    *n_distinct = b->ndag - b->ia_n_pairs;
+    return INSP_OK;
+}
+
 INSP_API int insp_batch_info(const insp_batch *b, int32_t *ndag, int64_t *n_tasks, int64_t *n_edges) {
     if (!b) return fail(INSP_EINVAL, "batch is NULL");
     if (ndag) *ndag = b->ndag;
@@ -1772,7 +1799,7 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
     if (rc == INSP_OK && b->pull) {
         c.clear();
         for (int w : {4, 8, 16})
-            for (int mb : {128, 256, 512, 1024}) {
+            for (int mb : {128, 256, 512, 1024, 4096, 16384}) {
                 insp_tuning t = best;
                 t.ie_warps = w; t.ie_ring_mb = mb;
                 c.push_back(t);

@@ -83,7 +83,7 @@ void launch_ie(const DevBatch &B, const int64_t *item_base, int64_t n_items, int
 // Inspiring ability by target blocks (any DAG size): work items {dag, block} of IA_BLK_BITS
 // target ids, per CTA a ring of ring_rows rows (a power of two >= the DAG's longest edge span
 // + warps per CTA) and publish flags; slot_seq[grid] per-CTA item tags (start at 0).
-constexpr int32_t IA_BLK_BITS = 2048;
+constexpr int32_t IA_BLK_BITS = 8192;
 constexpr int32_t IA_BLK_WORDS = IA_BLK_BITS / 64;
 void launch_ia_blk(const DevBatch &B, const int2 *items, int32_t n_items, int32_t *counter, uint64_t *ring,
                    unsigned long long *flags, int32_t ring_rows, uint32_t *slot_seq, int32_t *ia, int32_t *status,

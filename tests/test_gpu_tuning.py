@@ -177,6 +177,8 @@ def test_repeated_structures_share_ability(ia_block, groups):
                        inputs.tiled(inputs.KIND_LU, 8, 3, cfg=44), inputs.tiled(inputs.KIND_QR, 8, 1, cfg=45)])
     m = inputs.MACHINE_TILED
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
+    from paper_2404_03226_b300 import _lib
+    assert _lib.insp_batch_structures(B.handle) == 1 + 7 + 1 + 1  # Cholesky-16, 7 layered, LU-8, QR-8
     B.tuning = dict(TUNINGS[0], groups=groups, ia_block=ia_block)
     for fused in (False, True):
         out = _run(B, fused)
@@ -186,11 +188,13 @@ def test_repeated_structures_share_ability(ia_block, groups):
 
 @pytest.mark.parametrize("ia_block", [0, 1])
 def test_ability_by_target_blocks_on_larger_dags(ia_block):
-    """DAGs of several 2048-id target blocks (layered up to 7,000 tasks; Cholesky at 48 tiles,
-    19,600 tasks, above the whole-row limit, so it takes the blocks in both modes)."""
+    """DAGs of one to three 8192-id target blocks (layered of 8,300 to 12,000 tasks, LU and QR at 32
+    tiles; Cholesky at 48 tiles, 19,600 tasks, above the whole-row limit, so it takes the blocks
+    in both modes)."""
     import paper_2404_03226_b300 as P
-    b = inputs.concat([inputs.layered(6, cfg=46, n_min=2040, n_max=7000),
-                       inputs.tiled(inputs.KIND_CHOLESKY, 48, 1, cfg=47)])
+    b = inputs.concat([inputs.layered(2, cfg=46, n_min=8300, n_max=12000),
+                       inputs.tiled(inputs.KIND_CHOLESKY, 48, 1, cfg=47), inputs.tiled(inputs.KIND_LU, 32, 1, cfg=47),
+                       inputs.tiled(inputs.KIND_QR, 32, 1, cfg=47)])
     m = inputs.MACHINE_TILED
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
     B.tuning = dict(TUNINGS[0], ia_block=ia_block, ia_warps=32)
