@@ -318,13 +318,12 @@ def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5)
                                                            torch.int64)] + [torch.empty(nd, dtype=torch.int64,
                                                                                         device=dev)]
     stream = torch.cuda.current_stream(dev)
+    bb = b_main  # each baseline's policy set on the resident batch in turn (then back to INSPIRIT)
     for name, pid in (("dmda_fifo", P.INSP_POLICY_FIFO), ("dmdap_ia", P.INSP_POLICY_DMDAP_IA),
                       ("dmdap_bottom_level", P.INSP_POLICY_DMDAP_BL)):
         pol = P.insp_policy()
         pol.policy = pid
-        m = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns, pol)
-        bb = P.DagBatch(m, batch)
-        _lib.insp_batch_set_tuning(bb.handle, t_struct)
+        _lib.insp_batch_set_policy(bb.handle, pol)
         for _ in range(2):
             _lib.insp_evaluate_batch(bb.handle, None, *bufs, stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -338,7 +337,7 @@ def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5)
         t = e0.elapsed_time(e1) / 1e3 / steps
         out[name] = {"value": n / t, "unit": UNIT, "ms_per_step": t * 1e3,
                      "mean_makespan_ns": float(bufs[5].double().mean())}
-        del bb, m
+    _lib.insp_batch_set_policy(bb.handle, P.insp_policy())
     # unit-time search (k = 0..16) on the main batch, then INSPIRIT with the searched T
     ut = torch.empty(nd, dtype=torch.int64, device=dev)
     torch.cuda.synchronize()
@@ -361,20 +360,19 @@ def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5)
 SAMPLE_MAX_N = 20000
 
 
-def learned_leg(batch, mach, t_struct, mk_plain, dev, steps=3):
+def learned_leg(batch, machine, bb, mk_plain, dev, steps=3):
     """The learned proposal scorer (shipped weights) beside the plain INSPIRIT priority on the
-    same batch, same tuning: evaluation-step throughput and mean makespans."""
+    same resident batch (its policy switched for the leg, then back), same tuning: evaluation-step
+    throughput and mean makespans."""
     import torch
 
     import paper_2404_03226_b300 as P
     from paper_2404_03226_b300 import _lib, scorer
     bits, shipped = scorer.load_trained()
+    _lib.insp_set_scorer(machine.handle, bits)
     pol = P.insp_policy()
     pol.policy = P.INSP_POLICY_LEARNED
-    m = P.Machine(mach.n_cpu, mach.n_gpu, mach.xfer_ns, pol)
-    _lib.insp_set_scorer(m.handle, bits)
-    bb = P.DagBatch(m, batch)
-    _lib.insp_batch_set_tuning(bb.handle, t_struct)
+    _lib.insp_batch_set_policy(bb.handle, pol)
     n, nd = batch.n_total, batch.ndag
     bufs = [torch.empty(n, dtype=t, device=dev) for t in (torch.int32, torch.int32, torch.int32, torch.int64,
                                                            torch.int64)] + [torch.empty(nd, dtype=torch.int64,
@@ -390,6 +388,7 @@ def learned_leg(batch, mach, t_struct, mk_plain, dev, steps=3):
     if _lib.insp_batch_status(bb.handle) != 0:
         raise RuntimeError("learned policy: device-side status not OK: " + _lib.last_error())
     t = e0.elapsed_time(e1) / 1e3 / steps
+    _lib.insp_batch_set_policy(bb.handle, P.insp_policy())  # back to the plain INSPIRIT defaults
     plain = float(mk_plain.double().mean())
     lm = float(bufs[5].double().mean())
     return {"value": n / t, "unit": UNIT, "ms_per_step": t * 1e3, "mean_makespan_ns": lm,
@@ -608,7 +607,11 @@ def run_ours(args, rank, world, local_rank):
         streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]  # non-blocking: loads run beside them
         k_e2e = max(1, min(args.steps, 10))
         # one step at a time: load, evaluate, read back
-        evaluate(load(), streams[0])
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        h_first = load()
+        # device bytes a loaded batch holds, plus the staging of its host outputs at evaluation
+        per_batch = max(free0 - torch.cuda.mem_get_info(dev)[0], 1) + 32 * n
+        evaluate(h_first, streams[0])
         t0 = time.perf_counter()
         for _ in range(k_e2e):
             evaluate(load(), streams[0])
@@ -619,60 +622,69 @@ def run_ours(args, rank, world, local_rank):
         # host thread and its own stream while this one evaluates, and each step's read-back
         # (asynchronous, into pinned memory) overlaps the next step's kernels; steps alternate
         # between two streams and two sets of outputs
-        import queue
-        import threading
-        outs = [(ia_e, ie_e, o_w, o_s, o_e, o_m),
-                (torch.empty_like(ia), torch.empty_like(ie), torch.empty(n, dtype=torch.int32).pin_memory(),
-                 torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
-                 torch.empty(ndag, dtype=torch.int64).pin_memory())]
-        slots = threading.Semaphore(3)  # batches alive: loading, evaluating, reading back
-        q = queue.Queue()
-        warm = 2
+        # three batches alive at once (loading, evaluating, reading back) must fit the device
+        serving = torch.cuda.mem_get_info(dev)[0] > 3.2 * per_batch
+        if serving:
+            import queue
+            import threading
+            outs = [(ia_e, ie_e, o_w, o_s, o_e, o_m),
+                    (torch.empty_like(ia), torch.empty_like(ie), torch.empty(n, dtype=torch.int32).pin_memory(),
+                     torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
+                     torch.empty(ndag, dtype=torch.int64).pin_memory())]
+            slots = threading.Semaphore(3)  # batches alive: loading, evaluating, reading back
+            q = queue.Queue()
+            warm = 2
 
-        def loader():
-            try:
-                for _ in range(warm + k_e2e):
-                    slots.acquire()
-                    q.put(load())
-            except Exception as exc:  # handed to the evaluating thread
-                q.put(exc)
+            def loader():
+                try:
+                    for _ in range(warm + k_e2e):
+                        slots.acquire()
+                        q.put(load())
+                except Exception as exc:  # handed to the evaluating thread
+                    q.put(exc)
 
-        def finish(p):  # wait for a step's read-back, check it, release its batch
-            h, j = p
-            streams[j].synchronize()
-            rc = _lib.insp_batch_status(h)
-            _lib.insp_batch_destroy(h)
-            slots.release()
-            if rc != 0:
-                raise RuntimeError("device-side status not OK in the e2e loop: " + _lib.last_error())
+            def finish(p):  # wait for a step's read-back, check it, release its batch
+                h, j = p
+                streams[j].synchronize()
+                rc = _lib.insp_batch_status(h)
+                _lib.insp_batch_destroy(h)
+                slots.release()
+                if rc != 0:
+                    raise RuntimeError("device-side status not OK in the e2e loop: " + _lib.last_error())
 
-        th = threading.Thread(target=loader, daemon=True)  # never blocks the exit after an error
-        th.start()
-        pending = None
-        for k in range(warm + k_e2e):
-            if k == warm:
+            th = threading.Thread(target=loader, daemon=True)  # never blocks the exit after an error
+            th.start()
+            pending = None
+            for k in range(warm + k_e2e):
+                if k == warm:
+                    if pending is not None:
+                        finish(pending)
+                        pending = None
+                    t0 = time.perf_counter()
+                h = q.get()
+                if isinstance(h, Exception):
+                    raise h
+                j = k % 2
+                o = outs[j]
+                _lib.insp_evaluate_batch_async(h, None, o[0], o[1], o[2], o[3], o[4], o[5], streams[j])
                 if pending is not None:
                     finish(pending)
-                    pending = None
-                t0 = time.perf_counter()
-            h = q.get()
-            if isinstance(h, Exception):
-                raise h
-            j = k % 2
-            o = outs[j]
-            _lib.insp_evaluate_batch_async(h, None, o[0], o[1], o[2], o[3], o[4], o[5], streams[j])
-            if pending is not None:
-                finish(pending)
-            pending = (h, j)
-        finish(pending)
-        t_e2e = (time.perf_counter() - t0) / k_e2e
-        th.join()
-        for o in outs:
-            assert np.array_equal(o[5].numpy(), mk.cpu().numpy())
-        e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
-               "mode": "serving loop: the next step's load and this step's read-back overlap the kernels",
-               "serial": {"value": n / t_serial, "ms_per_step": t_serial * 1e3}}
+                pending = (h, j)
+            finish(pending)
+            t_e2e = (time.perf_counter() - t0) / k_e2e
+            th.join()
+            for o in outs:
+                assert np.array_equal(o[5].numpy(), mk.cpu().numpy())
+            e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
+                   "mode": "serving loop: the next step's load and this step's read-back overlap the kernels",
+                   "serial": {"value": n / t_serial, "ms_per_step": t_serial * 1e3}}
+        else:  # one batch at a time: the serial figure is the end-to-end one
+            e2e = {"value": n / t_serial, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "ms_per_step": t_serial * 1e3, "steps": k_e2e,
+                   "mode": "one step at a time: load, evaluate, read back (three batches of this size do not "
+                           "fit the device together, so the serving loop's overlap is not run)",
+                   "serial": {"value": n / t_serial, "ms_per_step": t_serial * 1e3}}
 
     # ---- the baselines and the unit-time search on the same batch (same tuning, same step)
     policies = None
@@ -681,7 +693,7 @@ def run_ours(args, rank, world, local_rank):
 
     learned = None
     if rank == 0 and not args.profile and not args.no_learned:
-        learned = learned_leg(batch, mach, t_struct, mk, dev)
+        learned = learned_leg(batch, machine, b, mk, dev)
 
     cb = cpu_baseline(batch, mach, max_n=SAMPLE_MAX_N) if (rank == 0 and world == 1 and not args.profile) else None
 
