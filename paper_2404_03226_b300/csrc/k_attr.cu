@@ -121,16 +121,23 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia(DevBatch B, const int3
 // has finished.  Within a wave a task waits (bounded) for its successors' publish flags, which
 // carry the item's tag and the task id.  Memory per CTA: R x (IA_BLK_BITS / 8 + 8) bytes,
 // independent of the DAG's size.  Partial counts are added to ia (zeroed first) atomically.
+// Full rows: a row holding the whole block (every target id a descendant) is published with a
+// full mark and never written; a task with a full successor is full itself (its row contains
+// the successor's), so the long stretch of a sweep below a block -- where most tasks reach all
+// of it -- costs a flag read per successor instead of the successors' rows.
+constexpr unsigned long long IA_FULL = 1ull << 31;  // in the task-id half of a flag (ids < 2^24)
 __device__ __forceinline__ bool wait_key(const unsigned long long *flag, unsigned long long key, int32_t *abort,
-                                         int limit) {
+                                         int limit, bool &full) {
     int it = 0;
-    while (*(const volatile unsigned long long *)flag != key) {
+    unsigned long long f;
+    while (((f = *(const volatile unsigned long long *)flag) & ~IA_FULL) != key) {
         if (++it > limit || ld_volatile(abort)) {
             st_volatile(abort, 1);
             return false;
         }
         __nanosleep(64);
     }
+    full = (f & IA_FULL) != 0;
     return true;
 }
 
@@ -174,49 +181,61 @@ __global__ void __launch_bounds__(IA_MAX_WARPS * 32) k_ia_blk(DevBatch B, const 
                 const int32_t lo = rp[v], hi = rp[v + 1];
                 // successors below b1 (the list is ascending), each waited for (bounded)
                 int32_t deg = 0;
+                bool any_full = false;
                 for (int32_t base = lo; base < hi; base += 32) {
                     const int32_t i = base + lane;
                     const int32_t s = i < hi ? col[i] : b1;
                     const bool in = s < b1;
+                    bool full = false;
                     if (in && insp_check(s > v && s - v < ring_rows, status + d) &&
-                        !wait_key(F + (s & rmask), tag | uint32_t(s), &s_abort, SPIN_LIMIT))
+                        !wait_key(F + (s & rmask), tag | uint32_t(s), &s_abort, SPIN_LIMIT, full))
                         timed_out = true;
+                    any_full |= __ballot_sync(FULL, full) != 0;
                     const uint32_t m = __ballot_sync(FULL, in);
                     deg += __popc(m);
                     if (m != FULL) break;
                 }
                 __syncwarp();
                 __threadfence_block();
-                const bool own = v >= b0;
-                const int32_t wlo = own ? (v - b0) >> 6 : 0;
-                const int32_t span_w = NWb - wlo;
-                const int32_t lg = span_w >= 32 ? 5 : (span_w <= 1 ? 0 : 32 - __clz(span_w - 1));
-                const int32_t g = 1 << lg;
-                const int32_t G = 32 >> lg, grp = lane >> lg, wl = lane & (g - 1);
-                uint64_t *row_v = R + int64_t(v & rmask) * IA_BLK_WORDS;
-                int32_t count = 0;
-                for (int32_t cw = wlo; cw < NWb; cw += g) {
-                    const int32_t w = cw + wl;
-                    uint64_t acc = (own && grp == 0 && w == wlo) ? (1ull << ((v - b0) & 63)) : 0ull;
+                if (any_full) {  // v reaches the whole block (so v < b0: a row at or above b0 holds no id below it)
+                    if (lane == 0) {
+                        *(volatile unsigned long long *)(F + (v & rmask)) = tag | uint32_t(v) | IA_FULL;
+                        atomicAdd(ia_out + tb + v, b1 - b0 - (v >= b0 ? 1 : 0));
+                    }
+                } else {
+                    const bool own = v >= b0;
+                    const int32_t wlo = own ? (v - b0) >> 6 : 0;
+                    const int32_t span_w = NWb - wlo;
+                    const int32_t lg = span_w >= 32 ? 5 : (span_w <= 1 ? 0 : 32 - __clz(span_w - 1));
+                    const int32_t g = 1 << lg;
+                    const int32_t G = 32 >> lg, grp = lane >> lg, wl = lane & (g - 1);
+                    uint64_t *row_v = R + int64_t(v & rmask) * IA_BLK_WORDS;
+                    int32_t count = 0;
+                    for (int32_t cw = wlo; cw < NWb; cw += g) {
+                        const int32_t w = cw + wl;
+                        uint64_t acc = (own && grp == 0 && w == wlo) ? (1ull << ((v - b0) & 63)) : 0ull;
 #pragma unroll 4
-                    for (int32_t i = grp; i < deg; i += G) {
-                        const int32_t s = col[lo + i];
-                        // words of row(s) below its own first word were not written for it
-                        const int32_t ws = s >= b0 ? (s - b0) >> 6 : 0;
-                        if (w >= ws && w < NWb) acc |= R[int64_t(s & rmask) * IA_BLK_WORDS + w];
+                        for (int32_t i = grp; i < deg; i += G) {
+                            const int32_t s = col[lo + i];
+                            // words of row(s) below its own first word were not written for it
+                            const int32_t ws = s >= b0 ? (s - b0) >> 6 : 0;
+                            if (w >= ws && w < NWb) acc |= R[int64_t(s & rmask) * IA_BLK_WORDS + w];
+                        }
+                        for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
+                        if (grp == 0 && w < NWb) {
+                            row_v[w] = acc;
+                            count += __popcll(acc);
+                        }
                     }
-                    for (int32_t off = g; off < 32; off <<= 1) acc |= __shfl_xor_sync(FULL, acc, off);
-                    if (grp == 0 && w < NWb) {
-                        row_v[w] = acc;
-                        count += __popcll(acc);
+                    count = __reduce_add_sync(FULL, count);
+                    const bool full = count == b1 - b0;
+                    count -= own ? 1 : 0;
+                    __threadfence_block();
+                    __syncwarp();
+                    if (lane == 0) {
+                        *(volatile unsigned long long *)(F + (v & rmask)) = tag | uint32_t(v) | (full ? IA_FULL : 0ull);
+                        if (count > 0) atomicAdd(ia_out + tb + v, count);
                     }
-                }
-                count = __reduce_add_sync(FULL, count) - (own ? 1 : 0);
-                __threadfence_block();
-                __syncwarp();
-                if (lane == 0) {
-                    *(volatile unsigned long long *)(F + (v & rmask)) = tag | uint32_t(v);
-                    if (count > 0) atomicAdd(ia_out + tb + v, count);
                 }
             }
             __syncthreads();
