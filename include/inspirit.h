@@ -356,7 +356,9 @@ typedef struct {
                               1024 (more spill to global memory); 1024 fits CTAs of at most 6 warps (5 with the
                               learned scorer): a simulation whose CTA does not fit fails with INSP_EINVAL */
     int32_t group_split;   /* 0: groups of equal DAG counts; 1: geometric, each group 4x the DAGs of the
-                              one before (the largest DAGs, whose simulations take longest, start first) */
+                              one before (the largest DAGs, whose simulations take longest, start first);
+                              2: the first group holds one DAG per SM (the largest), the others split the
+                              rest equally, so the longest simulations run beside the others' sweeps */
     int32_t ia_block;      /* ability sweep: 0: DAGs of up to 16384 tasks keep one bitset row of n bits per task
                               in one CTA (n x n bits), larger ones are cut into target blocks; 1: every DAG
                               is cut into blocks of 8192 target ids, one CTA per (DAG, block), rows in a ring

@@ -113,15 +113,21 @@ bool tuning_ok(const insp_tuning &t) {
            t.sim_warps >= 1 && t.sim_warps <= insp::sim_max_warps() &&
            (t.sim_queue == 32 || t.sim_queue == 64 || t.sim_queue == 128 || t.sim_queue == 256 ||
             t.sim_queue == 512 || t.sim_queue == 1024) &&
-           (t.group_split == 0 || t.group_split == 1) && (t.ia_block == 0 || t.ia_block == 1);
+           (t.group_split >= 0 && t.group_split <= 2) && (t.ia_block == 0 || t.ia_block == 1);
 }
 
-// First DAG rank of size group g of G (g = G: ndag), equal DAG counts or geometric (group g
-// holds 4x the DAGs of group g - 1).
-int group_begin(int g, int G, int ndag, int split) {
+// First DAG rank of size group g of G (g = G: ndag): equal DAG counts (split 0), geometric
+// (1: group g holds 4x the DAGs of group g - 1), or head first (2: group 0 holds the `head`
+// largest DAGs -- one per SM, whose simulations are the step's longest chains and then run
+// beside the attribute sweeps of all the others -- and the rest is cut into equal groups).
+int group_begin(int g, int G, int ndag, int split, int head) {
     if (g <= 0) return 0;
     if (g >= G) return ndag;
     if (split == 0) return int(int64_t(g) * ndag / G);
+    if (split == 2) {
+        const int h = std::min(head, ndag);
+        return h + int(int64_t(g - 1) * (ndag - h) / (G - 1));
+    }
     int64_t denom = 1;
     for (int k = g; k < G; ++k) denom *= 4;
     return int(int64_t(ndag) / denom);
@@ -1541,12 +1547,15 @@ int evaluate_impl(insp_batch *b, const int64_t *unit_time_ns, int32_t *ia, int32
         CU(cudaEventRecord(S.ev_fork, s));
         CU(cudaStreamWaitEvent(S.q[0], S.ev_fork, 0));
     }
-    // size groups along the size order (largest DAGs first, equal DAG counts): the
+    // size groups along the size order (largest DAGs first; see group_begin): the
     // simulation of group g starts on its own stream as soon as the attributes of
     // group g are done, while the attributes of the later groups still run
+    DeviceInfo di;
+    if ((rc = device_info(di))) return rc;
+    const int head = di.sms;
     for (int g = 0; g < G; ++g) {
-        const int r0 = group_begin(g, G, b->ndag, b->tun.group_split);
-        const int r1 = group_begin(g + 1, G, b->ndag, b->tun.group_split);
+        const int r0 = group_begin(g, G, b->ndag, b->tun.group_split, head);
+        const int r1 = group_begin(g + 1, G, b->ndag, b->tun.group_split, head);
         int32_t *cg = ctr + 16 + 4 * g;
         if ((rc = launch_attr(b, r0, r1, cg, ut, pull, wide, d_ia, d_ie, s, s_ie))) return rc;
         A.order = b->order.as<int32_t>() + r0;
@@ -1830,6 +1839,8 @@ INSP_API int insp_batch_autotune(insp_batch *b, void *stream, insp_tuning *chose
             for (int g : {2, 3, 4}) {
                 insp_tuning t = best;
                 t.groups = g; t.attr_overlap = ov; t.group_split = 1;
+                c.push_back(t);
+                t.group_split = 2;
                 c.push_back(t);
             }
         }

@@ -29,6 +29,10 @@ TUNINGS = [
          ia_block=0),
     dict(groups=2, attr_overlap=0, ia_warps=8, ie_warps=4, ie_ring_mb=128, sim_warps=5, sim_queue=1024, group_split=0,
          ia_block=1),
+    dict(groups=3, attr_overlap=1, ia_warps=16, ie_warps=4, ie_ring_mb=512, sim_warps=2, sim_queue=32, group_split=2,
+         ia_block=0),
+    dict(groups=2, attr_overlap=0, ia_warps=8, ie_warps=8, ie_ring_mb=256, sim_warps=4, sim_queue=64, group_split=2,
+         ia_block=1),
 ]
 
 
@@ -114,7 +118,7 @@ def test_tuning_rejects_out_of_range():
     B = P.DagBatch(P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns), b)
     good = B.tuning
     for field, bad in (("groups", 0), ("groups", 17), ("attr_overlap", 2), ("ia_warps", 0), ("ia_warps", 33),
-                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48), ("group_split", 2),
+                       ("ie_warps", 17), ("ie_ring_mb", 0), ("sim_warps", 0), ("sim_queue", 48), ("group_split", 3),
                        ("ia_block", 2)):
         t = dict(good, **{field: bad})
         with pytest.raises(P.InspError):
