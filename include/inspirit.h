@@ -353,8 +353,9 @@ typedef struct {
                               bounds the warps in flight, and rings beyond L2 spill to HBM */
     int32_t sim_warps;     /* warps (= DAGs in flight) per CTA of the simulation (1..8) */
     int32_t sim_queue;     /* ready-pool entries per warp kept in shared memory: 32, 64, 128, 256, 512 or
-                              1024 (more spill to global memory); 1024 fits CTAs of at most 6 warps (5 with the
-                              learned scorer): a simulation whose CTA does not fit fails with INSP_EINVAL */
+                              1024 (more spill to global memory); 1024 fits CTAs of at most 6 warps (5 above
+                              32 workers, one less with the learned scorer): a simulation whose CTA does not
+                              fit fails with INSP_EINVAL */
     int32_t group_split;   /* 0: groups of equal DAG counts; 1: geometric, each group 4x the DAGs of the
                               one before (the largest DAGs, whose simulations take longest, start first);
                               2: the first group holds one DAG per SM (the largest), the others split the

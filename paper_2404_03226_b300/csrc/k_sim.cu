@@ -38,16 +38,19 @@ constexpr int NODE_NONE = 0xff;
 enum { MODE_FIFO = 0, MODE_ABILITY = 1, MODE_EFI = 2, MODE_EFI_LOC = 3, MODE_LEARNED = 4, MODE_PRIO = 5 };
 enum { ST_INC = 0, ST_DEC = 1 };
 
-// Pools of at least MASK_MIN shared-memory entries keep, per worker (32 workers or fewer), a
-// bitmap of its entries there, so a pop visits only the popping worker's entries instead of
-// the whole pool (the tiled DAGs hold hundreds of ready tasks over 20 workers).
+// Pools of at least MASK_MIN shared-memory entries keep, per worker, a bitmap of its entries
+// there, so a pop visits only the popping worker's entries instead of the whole pool (the tiled
+// DAGs hold hundreds of ready tasks over 20 workers, the 1,000,000-task layered DAG ~500 over
+// 40).  Rows for 32 workers, or 64 when lanes own two workers (TWO).
 constexpr int MASK_MIN = 128;
 template <int POOL_C>
 constexpr int mask_words() { return POOL_C >= MASK_MIN ? POOL_C / 32 : 1; }
+template <int POOL_C, bool TWO>
+constexpr int mask_rows() { return POOL_C >= MASK_MIN ? (TWO ? 64 : 32) : 1; }
 
 // POOL_C: ready-pool entries per warp kept in shared memory (the queue
 // capacity the autotuner picks; entries beyond it spill to global memory).
-template <int POOL_C>
+template <int POOL_C, bool TWO>
 struct WarpSmem {
     int32_t idw[POOL_C];  // task id | worker << 24
     int32_t seq[POOL_C];
@@ -58,12 +61,12 @@ struct WarpSmem {
     int32_t newly[NL_C];
     int32_t run_end[MAX_WORKERS];
     int64_t tcost[MAX_TYPES_SMEM * 2];
-    uint32_t wmask[POOL_C >= MASK_MIN ? 32 : 1][mask_words<POOL_C>()];  // entry bitmaps per worker
+    uint32_t wmask[mask_rows<POOL_C, TWO>()][mask_words<POOL_C>()];  // entry bitmaps per worker
 };
 
-template <int POOL_C>
+template <int POOL_C, bool TWO>
 struct Pool {
-    WarpSmem<POOL_C> *sm;
+    WarpSmem<POOL_C, TWO> *sm;
     int32_t *g_idw, *g_seq, *g_ia, *g_ie;
     int64_t *g_dr, *g_cost;
     __device__ __forceinline__ int32_t idw(int i) const { return i < POOL_C ? sm->idw[i] : g_idw[i - POOL_C]; }
@@ -180,8 +183,8 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
     extern __shared__ __align__(16) unsigned char dyn[];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    WarpSmem<POOL_C> *sm = reinterpret_cast<WarpSmem<POOL_C> *>(dyn) + wib;
-    unsigned char *dyn_l = dyn + (size_t(blockDim.x >> 5) * sizeof(WarpSmem<POOL_C>) + 15) / 16 * 16;
+    WarpSmem<POOL_C, TWO> *sm = reinterpret_cast<WarpSmem<POOL_C, TWO> *>(dyn) + wib;
+    unsigned char *dyn_l = dyn + (size_t(blockDim.x >> 5) * sizeof(WarpSmem<POOL_C, TWO>) + 15) / 16 * 16;
     ScorerPacked *SP = reinterpret_cast<ScorerPacked *>(dyn_l);
     LearnSmem *LS = reinterpret_cast<LearnSmem *>(dyn_l + sizeof(ScorerPacked)) + wib;
     if (LEARNED) {
@@ -190,7 +193,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         __syncthreads();
     }
     const DevBatch &B = A.B;
-    constexpr bool USE_MASK = POOL_C >= MASK_MIN && !TWO;
+    constexpr bool USE_MASK = POOL_C >= MASK_MIN;
     const int32_t P = A.n_cpu + A.n_gpu, n_cpu = A.n_cpu;
     const int64_t xfer = A.xfer;
     const bool smem_types = (A.B.task_cost == nullptr) && (B.n_types <= MAX_TYPES_SMEM);
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
         int2 *st_a = A.st_a + tb;
         longlong2 *st_b = A.st_b + tb;
         const int32_t *g_ia = A.ia + tb, *g_ie = A.ie + tb;
-        Pool<POOL_C> pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
+        Pool<POOL_C, TWO> pool{sm, A.p_idw + tb, A.p_seq + tb, A.p_ia + tb, A.p_ie + tb, A.p_dr + tb, A.p_cost + tb};
         int32_t *nl_g = A.nl + tb;
 
         // resolved policy parameters (zero = default for P workers and the attributes' unit time T)
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
             for (int i = lane; i < B.n_types * 2; i += 32) sm->tcost[i] = B.type_cost[int64_t(d) * B.n_types * 2 + i];
         }
         if (USE_MASK)
-            for (int i = lane; i < 32 * mask_words<POOL_C>(); i += 32) (&sm->wmask[0][0])[i] = 0u;
+            for (int i = lane; i < mask_rows<POOL_C, TWO>() * mask_words<POOL_C>(); i += 32) (&sm->wmask[0][0])[i] = 0u;
         for (int32_t t = lane; t < n; t += 32) {
             st_a[t] = make_int2(A.indeg0[tb + t], NODE_NONE);
             st_b[t] = make_longlong2(NEG_TIME, NEG_TIME);
@@ -623,9 +626,9 @@ __global__ void __launch_bounds__(SIM_WARPS * 32) k_sim(SimArgs A) {
 }
 
 // dynamic shared memory of a launch with `warps` warps per CTA
-template <bool L, int Q>
+template <bool L, int Q, bool TWO>
 static size_t sim_dyn_bytes(int warps) {
-    return (size_t(warps) * sizeof(WarpSmem<Q>) + 15) / 16 * 16 +
+    return (size_t(warps) * sizeof(WarpSmem<Q, TWO>) + 15) / 16 * 16 +
            (L ? sizeof(ScorerPacked) + warps * sizeof(LearnSmem) : 0);
 }
 
@@ -639,15 +642,15 @@ static size_t smem_optin() {
     return size_t(v);
 }
 // the largest CTA of this variant that fits (large queues hold fewer warps per CTA)
-template <bool L, int Q>
+template <bool L, int Q, bool TWO>
 static size_t sim_dyn_max() {
-    return std::min(sim_dyn_bytes<L, Q>(SIM_WARPS), smem_optin());
+    return std::min(sim_dyn_bytes<L, Q, TWO>(SIM_WARPS), smem_optin());
 }
 
 template <bool L, int Q, bool TWO, bool EX>
 static void launch_q(const SimArgs &A, int grid, int threads, cudaStream_t s) {
-    cudaFuncSetAttribute(k_sim<L, Q, TWO, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q>()));
-    k_sim<L, Q, TWO, EX><<<grid, threads, sim_dyn_bytes<L, Q>(threads / 32), s>>>(A);
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, EX>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q, TWO>()));
+    k_sim<L, Q, TWO, EX><<<grid, threads, sim_dyn_bytes<L, Q, TWO>(threads / 32), s>>>(A);
 }
 
 template <bool L, bool TWO, bool EX>
@@ -688,10 +691,10 @@ int sim_max_warps() { return SIM_WARPS; }
 template <bool L, int Q, bool TWO>
 static int occ_q(int threads) {
     int nb = 0;
-    if (sim_dyn_bytes<L, Q>(threads / 32) > sim_dyn_max<L, Q>()) return 0;  // the CTA does not fit
-    cudaFuncSetAttribute(k_sim<L, Q, TWO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q>()));
+    if (sim_dyn_bytes<L, Q, TWO>(threads / 32) > sim_dyn_max<L, Q, TWO>()) return 0;  // the CTA does not fit
+    cudaFuncSetAttribute(k_sim<L, Q, TWO, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sim_dyn_max<L, Q, TWO>()));
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_sim<L, Q, TWO, false>, threads,
-                                                      sim_dyn_bytes<L, Q>(threads / 32)) != cudaSuccess) {
+                                                      sim_dyn_bytes<L, Q, TWO>(threads / 32)) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }

@@ -205,3 +205,20 @@ def test_ability_by_target_blocks_on_larger_dags(ia_block):
     out = _run(B)
     for d in range(b.ndag):
         compare_dag(b, d, out, m)
+
+
+@pytest.mark.parametrize("machine", [inputs.Machine(32, 8, 20000), inputs.Machine(60, 4, 1000)])
+@pytest.mark.parametrize("queue", [128, 1024])
+def test_pool_bitmaps_with_two_workers_per_lane(machine, queue):
+    """Machines of more than 32 workers (every lane owns two) with pools of 128+ shared-memory
+    entries, where pops walk per-worker bitmaps: wide ready pools (a 300-way fan-out, wide
+    layered DAGs, a Cholesky DAG) bit-exact against the oracle."""
+    import paper_2404_03226_b300 as P
+    b = inputs.concat([inputs.layered(6, cfg=51, n_min=400, n_max=1500, w_min=48, w_max=64),
+                       inputs.concat_dags(edge_case_dags()), inputs.tiled(inputs.KIND_CHOLESKY, 12, 1, cfg=52)])
+    B = P.DagBatch(P.Machine(machine.n_cpu, machine.n_gpu, machine.xfer_ns), b)
+    B.tuning = dict(TUNINGS[0], sim_warps=2, sim_queue=queue)
+    for fused in (False, True):
+        out = _run(B, fused)
+        for d in range(b.ndag):
+            compare_dag(b, d, out, machine)
