@@ -355,6 +355,9 @@ def compare_policies(args, batch, mach, t_struct, b_main, mk_main, dev, steps=5)
     return out
 
 
+MIXED_TUNING = dict(groups=1, attr_overlap=1, ia_warps=16, ie_warps=4, ie_ring_mb=16384, sim_warps=2, sim_queue=128,
+                    group_split=0, ia_block=1)
+
 # DAGs of at most this many tasks make up the CPU-baseline and per-DAG-launch samples (the
 # oracle's exact inspiring ability grows with n^2; the mixed-size workload reaches 1,000,000)
 SAMPLE_MAX_N = 20000
@@ -433,7 +436,13 @@ def run_ours(args, rank, world, local_rank):
     if args.tuning:  # explicit launch shapes (profiling captures)
         _lib.insp_batch_set_tuning(b.handle, _lib.insp_tuning(**json.loads(args.tuning)))
         t_struct = _lib.insp_batch_get_tuning(b.handle)
-    elif args.autotune and args.workload != "mixed":  # (the mixed batch's steps take seconds each)
+    elif args.workload == "mixed":
+        # the mixed batch's steps take seconds, too long for the autotuner's ~60 candidates x 4 steps:
+        # the shapes measured best on it (target-block ability sweep, 128-entry pools with per-worker
+        # bitmaps for the 1,000,000-task DAG's ~500 ready tasks over 40 workers, full ring budget)
+        _lib.insp_batch_set_tuning(b.handle, _lib.insp_tuning(**MIXED_TUNING))
+        t_struct = _lib.insp_batch_get_tuning(b.handle)
+    elif args.autotune:
         t_struct = _lib.insp_batch_autotune(b.handle, stream)
     else:
         t_struct = _lib.insp_batch_get_tuning(b.handle)
