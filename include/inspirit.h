@@ -108,9 +108,12 @@ typedef struct insp_batch insp_dag;       /* a batch holding exactly one DAG */
  * may be NULL (all defaults).  Errors: INSP_EINVAL, INSP_ENOMEM. */
 int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, const insp_policy *policy,
                         insp_machine **out);
-/* Destroy a machine after every batch loaded on it: a destroyed batch hands its
- * kernel scratch and its device buffers back to its machine for reuse by the
- * next load (up to two sets are kept; they are freed here). */
+/* Destroy a machine.  A destroyed batch hands its kernel scratch and its device
+ * buffers back to its machine for reuse by the next load (up to two sets are
+ * kept; they are freed here).  Batches loaded on the machine may still be alive
+ * (a garbage collector may finalise the two handles in either order): they stay
+ * usable, and the machine's memory is released when the last of them is
+ * destroyed.  No call may use `m` itself afterwards.  NULL is ignored. */
 void insp_machine_destroy(insp_machine *m);
 
 /* Install the learned proposal scorer used by INSP_POLICY_LEARNED: an MLP

@@ -212,6 +212,11 @@ struct insp_machine {
     std::vector<std::unique_ptr<Scratch>> spare;
     std::vector<std::unique_ptr<BatchBufs>> spare_bufs;
     insp_tuning tun = kDefaultTuning;  // the tuning batches loaded on this machine start with
+    // Batches loaded on this machine and not yet destroyed.  A machine destroyed while some are
+    // alive (a garbage collector may finalise the handles in any order) is only marked; the last
+    // of its batches frees it.
+    int64_t live_batches = 0;
+    bool destroyed = false;
 };
 
 enum { TK_IA = 0, TK_IE = 1, TK_SIM = 2, TK_SIM_SINGLE = 3, TK_N = 4 };
@@ -281,9 +286,16 @@ struct insp_batch {
         if (graph) cudaGraphExecDestroy(graph);
         for (auto &p : pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
         if (!owner) return;
-        std::lock_guard<std::mutex> lk(owner->mu);
-        if (sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
-        if (bufs && owner->spare_bufs.size() < 2) owner->spare_bufs.push_back(std::move(bufs));
+        bool last = false;
+        {
+            std::lock_guard<std::mutex> lk(owner->mu);
+            if (!owner->destroyed) {
+                if (sc && owner->spare.size() < 2) owner->spare.push_back(std::move(sc));
+                if (bufs && owner->spare_bufs.size() < 2) owner->spare_bufs.push_back(std::move(bufs));
+            }
+            last = --owner->live_batches == 0 && owner->destroyed;
+        }
+        if (last) delete owner;  // its destroy call came first
     }
 
     insp::DevBatch dev() const {
@@ -721,7 +733,19 @@ INSP_API int insp_machine_create(int32_t n_cpu, int32_t n_gpu, int64_t xfer_ns, 
     return INSP_OK;
 }
 
-INSP_API void insp_machine_destroy(insp_machine *m) { delete m; }
+INSP_API void insp_machine_destroy(insp_machine *m) {
+    if (!m) return;
+    {
+        std::lock_guard<std::mutex> lk(m->mu);
+        if (m->live_batches > 0) {  // the last batch's destroy frees it
+            m->destroyed = true;
+            m->spare.clear();
+            m->spare_bufs.clear();
+            return;
+        }
+    }
+    delete m;
+}
 
 INSP_API int insp_set_scorer(insp_machine *m, const uint16_t *w, size_t nbytes) {
     if (!m || !w) return fail(INSP_EINVAL, "NULL argument");
@@ -847,9 +871,10 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     auto *b = new (std::nothrow) insp_batch(std::move(bb));
     if (!b) return fail(INSP_ENOMEM, "host allocation");
     auto bail = [&](int rc) { delete b; return rc; };
-    b->owner = m;
     {
         std::lock_guard<std::mutex> lk(m->mu);
+        b->owner = m;
+        ++m->live_batches;
         b->tun = m->tun;
     }
     b->mach_params.n_cpu = m->n_cpu;

@@ -376,3 +376,30 @@ def test_renumbered_dags_with_per_type_costs():
         tb, te = int(b.task_base[d]), int(b.task_base[d + 1])
         for k, v in (("ia", ia), ("ie", ie), ("worker", s.worker), ("start", s.start), ("end", s.end)):
             np.testing.assert_array_equal(v.cpu().numpy()[tb:te], np.asarray(r[k])[news[d]], err_msg=f"{k} of {d}")
+
+
+def test_machine_destroyed_before_its_batches():
+    """A machine destroyed while batches loaded on it are alive (a garbage collector may finalise
+    the handles in either order): the batches stay usable, and the last one frees the machine."""
+    import gc
+    import torch
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    b = inputs.layered(6, cfg=90, first=7, n_max=400)
+    m = inputs.MACHINE_LAYERED
+    M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
+    batches = [P.DagBatch(M, b), P.DagBatch(M, b)]
+    _lib.insp_machine_destroy(M.handle)
+    M.handle = None
+    while batches:
+        B = batches.pop()
+        ia, ie = B.attributes()
+        s = B.simulate(ia, ie)
+        torch.cuda.synchronize()
+        assert (B.status() == 0).all()
+        g = dict(ia=ia.cpu().numpy(), ie=ie.cpu().numpy(), worker=s.worker.cpu().numpy(),
+                 start=s.start.cpu().numpy(), end=s.end.cpu().numpy(), makespan=s.makespan.cpu().numpy())
+        for d in range(b.ndag):
+            compare_dag(b, d, g, m)
+        del B, s  # the first destroy leaves the machine to the second, which frees it
+        gc.collect()
