@@ -1,10 +1,9 @@
 // Inspiring efficiency (Sec. 4.2 / Sec. 4.3), "pull" form of the window sweep.
 //
-// A warp owns IE_PULL_SOURCES = 64 consecutive sources (lane j <-> v0 + j and
-// v0 + j + 32, two codes per lane) and visits every task u = v0, v0+1, ... in id
-// order (a topological order).  Each lane keeps, per task, its codes in a ring of
-// W rows (W a power of two above every edge span, so every predecessor of u is
-// still in the ring):
+// A warp owns IE_PULL_SOURCES = 64 consecutive sources (two codes per lane) and
+// visits every task u = v0, v0+1, ... in id order (a topological order).  It
+// keeps, per task, the 64 codes in a row of a ring of W rows (W a power of two
+// above every edge span, so every predecessor of u is still in the ring):
 //     "out"      u is not in the source's cone,
 //     L in 1..T  u is in the cone and every path from the source to u weighs L
 //                or less (L = the longest path weight, GPU costs, both ends),
@@ -24,8 +23,10 @@
 // staged into shared memory with coalesced loads; predecessors older than the
 // sources (outside every source's cone) are dropped while staging.  The ring is a
 // per-warp slice of global memory meant to stay in L2 (a shared-memory ring was
-// measured slower: at 33 KB per warp it caps residency at 6 warps per SM); each
-// lane only reads its own column, i.e. its own earlier writes.
+// measured slower: at 33 KB per warp it caps residency at 6 warps per SM).  With
+// 32-bit codes each lane only reads its own column (its own earlier writes); with
+// 16-bit codes lanes read words other lanes wrote, so a __syncwarp orders every
+// row's store before the later visits' loads.
 #include <type_traits>
 
 #include "common.cuh"
@@ -48,6 +49,12 @@ constexpr int NV = SPW / 32;          // codes per lane
 #ifndef IE_PULL_INFLIGHT
 #define IE_PULL_INFLIGHT 8
 #endif
+// Narrow codes: 16-byte loads per lane, so one load instruction of the warp fetches four
+// predecessor rows (lanes 8 g .. 8 g + 7 read row e + g); IE_PULL_NARROW_LOADS of them per lane
+// are in flight per round (4 x that many rows).
+#ifndef IE_PULL_NARROW_LOADS
+#define IE_PULL_NARROW_LOADS 4
+#endif
 
 // NV codes per lane, moved as one vector
 template <int V> struct CodeVec;
@@ -60,8 +67,12 @@ __device__ __forceinline__ int2 cmake(const int32_t (&v)[2]) { return make_int2(
 __device__ __forceinline__ int4 cmake(const int32_t (&v)[4]) { return make_int4(v[0], v[1], v[2], v[3]); }
 
 // Narrow codes: when T <= NARROW_T_MAX a code fits 16 bits, unsigned and ordered the same way
-// (0 = outside the cone, 1..T = in the window, 0xffff = OVER), and a lane's two codes share one
-// 32-bit word: half the ring bytes, and one packed max per predecessor row.
+// (0 = outside the cone, 1..T = in the window, 0xffff = OVER), two to a 32-bit word: half the
+// ring bytes, and one packed max per word.  A narrow row is 32 words, word w holding sources
+// 2w and 2w + 1 (low half first).  Lane 8 g + s gathers with 16-byte loads: bytes 16 s .. 16 s + 15
+// of the rows e + g, e + 4 + g, ..., so one load instruction covers four rows; a reduce-scatter
+// over the four lane groups then leaves lane 8 g + s with word 4 s + g, i.e. sources
+// 8 s + 2 g and 8 s + 2 g + 1, which it combines with the task's cost and stores.
 constexpr int64_t NARROW_T_MAX = 0xfffe;
 constexpr uint32_t NOVER = 0xffff;
 static_assert(NV == 2, "narrow codes pack the two codes of a lane into one word");
@@ -186,46 +197,55 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                 continue;
             }
         }
-        // predecessor rows in flight per round; the last round's loads are predicated (12 or 16
-        // narrow rows in flight were measured slower)
+        // wide codes: predecessor rows in flight per round; the last round's loads are predicated
         constexpr int U = IE_PULL_INFLIGHT;
         const int32_t c = I.c_cost[k];
         int32_t vv[NV];
         bool any_in = false, any_cone = false;
         if (NARROW) {
-            uint32_t ma = 0, mb = 0;
-            int32_t e = clo;
-            for (; e + U <= chi; e += U) {
-                uint32_t pv[U];
+            // gather: lane 8 g + s folds bytes 16 s .. 16 s + 15 of the rows e + 4 i + g (0 = outside,
+            // the max's identity, for the rows past the task's list)
+            constexpr int NL = IE_PULL_NARROW_LOADS;
+            const int s8 = lane & 7, g4 = lane >> 3;
+            const uint4 *__restrict__ v4 = reinterpret_cast<const uint4 *>(val) + s8;
+            uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+            for (int32_t e = clo; e < chi; e += 4 * NL) {
+                uint4 pv[NL];
 #pragma unroll
-                for (int r = 0; r < U; ++r) pv[r] = reinterpret_cast<const uint32_t *>(val)[I.c_off[e + r] + lane];
+                for (int r = 0; r < NL; ++r) {
+                    const int32_t i = e + 4 * r + g4;
+                    pv[r] = i < chi ? v4[I.c_off[i] >> 2] : make_uint4(0u, 0u, 0u, 0u);
+                }
 #pragma unroll
-                for (int r = 0; r < U; r += 2) {
-                    ma = max_u16x2(ma, pv[r]);
-                    mb = max_u16x2(mb, pv[r + 1]);
+                for (int r = 0; r < NL; ++r) {
+                    acc.x = max_u16x2(acc.x, pv[r].x);
+                    acc.y = max_u16x2(acc.y, pv[r].y);
+                    acc.z = max_u16x2(acc.z, pv[r].z);
+                    acc.w = max_u16x2(acc.w, pv[r].w);
                 }
             }
-            // the rest as one more round, loads predicated (0 = outside: the max's identity)
-            if (e < chi) {
-                uint32_t pv[U];
-#pragma unroll
-                for (int r = 0; r < U; ++r)
-                    pv[r] = e + r < chi ? reinterpret_cast<const uint32_t *>(val)[I.c_off[e + r] + lane] : 0u;
-#pragma unroll
-                for (int r = 0; r < U; r += 2) {
-                    ma = max_u16x2(ma, pv[r]);
-                    mb = max_u16x2(mb, pv[r + 1]);
-                }
-            }
-            for (int32_t f = max(lo, ne); f < hi_p; ++f) {
+            // predecessors beyond the staging, from global: lane group g takes every fourth
+            for (int32_t f = max(lo, ne) + g4; f < hi_p; f += 4) {
                 const int32_t qd = I.pc[e0 + f];
                 const int32_t rq = qd & I.wmask;
-                if (qd >= I.v0 && (!SPARSE || ((I.live[rq >> 5] >> (rq & 31)) & 1u)))
-                    ma = max_u16x2(ma, reinterpret_cast<const uint32_t *>(val)[rq * 32 + lane]);
+                if (qd >= I.v0 && (!SPARSE || ((I.live[rq >> 5] >> (rq & 31)) & 1u))) {
+                    const uint4 x = v4[rq * 8];
+                    acc.x = max_u16x2(acc.x, x.x);
+                    acc.y = max_u16x2(acc.y, x.y);
+                    acc.z = max_u16x2(acc.z, x.z);
+                    acc.w = max_u16x2(acc.w, x.w);
+                }
             }
-            const uint32_t m2 = max_u16x2(ma, mb);
+            // reduce-scatter over the four lane groups: first groups g and g ^ 2 keep words
+            // 2 (g >> 1) and 2 (g >> 1) + 1 of the slice, then g and g ^ 1 keep word g
+            const bool hi2 = (g4 >> 1) != 0, hi1 = (g4 & 1) != 0;
+            uint32_t k0 = hi2 ? acc.z : acc.x, k1 = hi2 ? acc.w : acc.y;
+            k0 = max_u16x2(k0, __shfl_xor_sync(FULL, hi2 ? acc.x : acc.z, 16));
+            k1 = max_u16x2(k1, __shfl_xor_sync(FULL, hi2 ? acc.y : acc.w, 16));
+            const uint32_t m2 = max_u16x2(hi1 ? k1 : k0, __shfl_xor_sync(FULL, hi1 ? k0 : k1, 8));
             // T <= 0xfffe and c <= T + 1: m + c fits 32 bits and fits the window iff <= T
             const uint32_t own = uint32_t(c) <= uint32_t(I.T) ? uint32_t(c) : NOVER;
+            const int32_t j0 = 8 * s8 + 2 * g4;  // this lane's sources: v0 + j0, v0 + j0 + 1
             uint32_t packed = 0;
 #pragma unroll
             for (int q = 0; q < NV; ++q) {
@@ -234,13 +254,15 @@ __device__ __forceinline__ void sweep_item(const DevBatch &B, const PullItem &I,
                 const uint32_t L = m + uint32_t(c);
                 const bool fits = live && L <= uint32_t(I.T);
                 uint32_t v = live ? (fits ? L : NOVER) : m;
-                if (u - I.v0 == lane + 32 * q) v = own;
+                if (u - I.v0 == j0 + q) v = own;
                 cnt[q] += fits;
                 any_in |= v != 0 && v != NOVER;
                 any_cone |= v != 0;
                 packed |= v << (16 * q);
             }
-            if (!SPARSE || __any_sync(FULL, any_cone)) reinterpret_cast<uint32_t *>(val)[r_u * 32 + lane] = packed;
+            if (!SPARSE || __any_sync(FULL, any_cone))
+                reinterpret_cast<uint32_t *>(val)[r_u * 32 + 4 * s8 + g4] = packed;
+            __syncwarp();  // the row is read by other lanes at later visits
             (void)vv;
         } else {
             int32_t ma[NV], mb[NV];
@@ -354,16 +376,20 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
 #pragma unroll
         for (int q = 0; q < NV; ++q) cnt[q] = 0;
         const bool sparse = dag_span[I.d] > SPARSE_SPAN;  // then W > SPARSE_SPAN + 1: the bitmap exists
-        if (I.T <= NARROW_T_MAX) {
+        const bool narrow = I.T <= NARROW_T_MAX;
+        if (narrow) {
             if (sparse) sweep_item<true, true>(B, I, ring, lane, cnt);
             else sweep_item<true, false>(B, I, ring, lane, cnt);
         } else {
             if (sparse) sweep_item<false, true>(B, I, ring, lane, cnt);
             else sweep_item<false, false>(B, I, ring, lane, cnt);
         }
+        // the sources of this lane's counts: 8 s + 2 g + q with narrow codes (lane 8 g + s), else lane + 32 q
 #pragma unroll
-        for (int q = 0; q < NV; ++q)
-            if (lane + 32 * q < I.n_src) ie_out[I.tb + I.v0 + 32 * q + lane] = cnt[q];
+        for (int q = 0; q < NV; ++q) {
+            const int32_t j = narrow ? 8 * (lane & 7) + 2 * (lane >> 3) + q : lane + 32 * q;
+            if (j < I.n_src) ie_out[I.tb + I.v0 + j] = cnt[q];
+        }
         __syncwarp();
     }
 }
