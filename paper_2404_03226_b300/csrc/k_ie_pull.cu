@@ -51,7 +51,10 @@ constexpr int NV = SPW / 32;          // codes per lane
 #endif
 // Narrow codes: 16-byte loads per lane, so one load instruction of the warp fetches four
 // predecessor rows (lanes 8 g .. 8 g + 7 read row e + g); IE_PULL_NARROW_LOADS of them per lane
-// are in flight per round (4 x that many rows).
+// are in flight per round (4 x that many rows; on the layered workload 2 and 4 alike, 8
+// slower).  The same gather for 32-bit codes (two 256-byte rows per load, six or four rows in
+// flight) was measured slower than the lane-owned rows below: tiled 16 + 32 sweep 36.4 against
+// 34.0 ms.
 #ifndef IE_PULL_NARROW_LOADS
 #define IE_PULL_NARROW_LOADS 4
 #endif
