@@ -62,6 +62,9 @@ extern "C" {
 #define INSP_ECHECK 7    /* debug builds only (INSP_CHECK): an internal bounds check failed; outputs invalid */
 #define INSP_ECYCLE 8    /* the successor lists contain a cycle: no topological numbering exists */
 
+/* insp_scorer_eval's score of a row whose tensor-core tile did not complete in time */
+#define INSP_SCORE_TIMEOUT INT64_MIN
+
 /* ---------------------------------------------------------------- policy */
 #define INSP_POLICY_INSPIRIT 0 /* adaptive priority by the Nready controller (default) */
 #define INSP_POLICY_FIFO 1     /* DMDA without priorities: pop in push order (Sec. 2.1) */
@@ -275,7 +278,11 @@ int insp_batch_status(insp_batch *b, int32_t *status);
  *
  * insp_scorer_eval: scores of n candidates, feat[n][16] int32 features (each
  *   clamped to [0, 255]) -> score[n] int64 in units of 1/64, with the scorer
- *   installed on m; the same tensor-core tile the learned pop uses.
+ *   installed on m; the same network, bit for bit, as the learned pop's.  Runs
+ *   asynchronously on the fifth-generation tensor cores (tcgen05 MMAs on tiles
+ *   of 128 rows, accumulators in tensor memory).  Its waits for the MMAs are
+ *   bounded: a row whose tile did not complete gets INSP_SCORE_TIMEOUT (no
+ *   score is that low; |score| < 2^22), so check for it where that matters.
  *
  * insp_simulate_rollout: insp_simulate_batch plus rollout controls, each
  *   optional (NULL): at pop number force_pop[d] (0-based count of pops in DAG

@@ -11,6 +11,7 @@ from . import build as _build
 
 INSP_OK, INSP_EINVAL, INSP_ENOTTOPO, INSP_ENOMEM, INSP_ECUDA, INSP_ETIMEOUT, INSP_EOVERFLOW = range(7)
 INSP_ECHECK, INSP_ECYCLE = 7, 8
+INSP_SCORE_TIMEOUT = -(1 << 63)  # insp_scorer_eval's score of a row whose tile did not complete (INT64_MIN)
 INSP_POLICY_INSPIRIT, INSP_POLICY_FIFO, INSP_POLICY_LEARNED, INSP_POLICY_DMDAP_IA, INSP_POLICY_DMDAP_BL = 0, 1, 2, 3, 4
 ERROR_NAMES = {0: "INSP_OK", 1: "INSP_EINVAL", 2: "INSP_ENOTTOPO", 3: "INSP_ENOMEM", 4: "INSP_ECUDA",
                5: "INSP_ETIMEOUT", 6: "INSP_EOVERFLOW", 7: "INSP_ECHECK", 8: "INSP_ECYCLE"}

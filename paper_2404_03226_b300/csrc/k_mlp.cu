@@ -1,7 +1,9 @@
 // Learned proposal scorer (no counterpart in the paper): MLP 16 -> 64 -> 64 -> 1.
 //
-// Inference runs on the tensor cores with mma.sync m16n8k16 (BF16 operands,
-// FP32 accumulation), one 16-candidate tile per warp.  It is exact by
+// Batched inference runs on the fifth-generation tensor cores (tcgen05, in
+// k_scorer_tc.cu); the simulation's learned pop scores its candidates with the
+// warp-level mma.sync m16n8k16 tile of mlp.cuh (BF16 operands, FP32
+// accumulation, one 16-candidate tile per warp).  Both are exact by
 // construction: features are integers in [0, 255], weights and biases are
 // k / 64 with |k| <= 128 (both exact in BF16), hidden units are
 // min(floor(max(z, 0)), 255) (integers again), so every partial sum is a
@@ -24,44 +26,6 @@
 #include "mlp.cuh"
 
 namespace insp {
-
-// ------------------------------------------------------------- inference
-// Batched scoring of feature rows feat[n][16] (int32, clamped to [0, 255]).
-__global__ void __launch_bounds__(128) k_scorer_eval(const ScorerPacked *Pg, const int32_t *feat, int64_t n,
-                                                     int64_t *score) {
-    __shared__ ScorerPacked P;
-    __shared__ uint32_t tile[4][16 * 8];
-    for (int i = threadIdx.x; i < int(sizeof(ScorerPacked) / 4); i += blockDim.x)
-        reinterpret_cast<uint32_t *>(&P)[i] = reinterpret_cast<const uint32_t *>(Pg)[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    uint32_t *my = tile[wib];
-    const int64_t tiles = (n + 15) / 16;
-    for (int64_t tt = int64_t(blockIdx.x) * 4 + wib; tt < tiles; tt += int64_t(gridDim.x) * 4) {
-        // lane r < 16 packs row r
-        if (lane < 16) {
-            const int64_t row = tt * 16 + lane;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                int f0 = 0, f1 = 0;
-                if (row < n) {
-                    f0 = min(max(feat[row * 16 + 2 * c], 0), 255);
-                    f1 = min(max(feat[row * 16 + 2 * c + 1], 0), 255);
-                }
-                my[lane * 8 + c] = pack_bf16x2(float(f0), float(f1));
-            }
-        }
-        __syncwarp();
-        float s0, s1;
-        mlp_score_tile(&P, my, lane, s0, s1);
-        if ((lane & 3) == 0) {
-            const int64_t r0 = tt * 16 + (lane >> 2), r1 = r0 + 8;
-            if (r0 < n) score[r0] = int64_t(s0 * 64.0f);
-            if (r1 < n) score[r1] = int64_t(s1 * 64.0f);
-        }
-        __syncwarp();
-    }
-}
 
 // --------------------------------------------------------------- training
 __device__ __forceinline__ float q_weight(float w) {
@@ -486,11 +450,6 @@ __global__ void k_quantize(int64_t nw, const float *w, uint16_t *out) {
 }
 
 // ----------------------------------------------------------------- launch
-void launch_scorer_eval(const ScorerPacked *P, const int32_t *feat, int64_t n, int64_t *score, cudaStream_t s) {
-    const int64_t tiles = (n + 15) / 16;
-    const int grid = int(std::min<int64_t>(std::max<int64_t>((tiles + 3) / 4, 1), 148 * 8));
-    k_scorer_eval<<<grid, 128, 0, s>>>(P, feat, n, score);
-}
 
 void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
                            const float *x, const float *target, float *work, float *grad, float *loss,

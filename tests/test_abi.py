@@ -64,3 +64,5 @@ def test_binding_constants_match_the_header():
         assert int(defs[name]) == getattr(_lib, name), name
     for code, name in _lib.ERROR_NAMES.items():
         assert int(defs[name]) == code, name
+    assert re.search(r"#define\s+INSP_SCORE_TIMEOUT\s+INT64_MIN\b", hdr)
+    assert _lib.INSP_SCORE_TIMEOUT == -(2 ** 63)

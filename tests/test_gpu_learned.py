@@ -43,6 +43,38 @@ def test_scorer_eval_matches_integer_network():
         np.testing.assert_array_equal(got, exp)
 
 
+def test_scorer_eval_many_tiles_ragged_and_clamped():
+    """The tensor-core scoring over more 128-row tiles than the persistent grid has CTAs (four
+    per SM), a ragged last tile and features outside [0, 255] (clamped): sampled rows against
+    the oracle's integer network, every row scored (no timeout sentinel)."""
+    import time
+    import torch
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    M = P.Machine(2, 1, 0)
+    k = _weights(4, 64)
+    _lib.insp_set_scorer(M.handle, _bf16_bits(k))
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    n = sms * 4 * 128 * 2 + 77
+    rng = np.random.default_rng(5)
+    feat = rng.integers(-40, 300, (n, 16)).astype(np.int32)
+    d_feat = torch.from_numpy(feat).cuda()
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    _lib.insp_scorer_eval(M.handle, d_feat, n, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert not (got == _lib.INSP_SCORE_TIMEOUT).any()
+    rows = np.unique(np.concatenate([np.arange(0, n, 211), np.arange(n - 300, n), np.arange(0, 300)]))
+    exp = np.array([oracle.mlp_score(k, np.clip(feat[r], 0, 255)) for r in rows])
+    np.testing.assert_array_equal(got[rows], exp)
+    t0 = time.perf_counter()
+    for _ in range(10):
+        _lib.insp_scorer_eval(M.handle, d_feat, n, out)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / 10
+    print(f"\nscoring {n} rows on the tensor cores: {dt * 1e3:.3f} ms ({n / dt / 1e9:.2f} G rows/s)")
+
+
 def test_set_scorer_rejects_off_grid_weights():
     import paper_2404_03226_b300 as P
     from paper_2404_03226_b300 import _lib
