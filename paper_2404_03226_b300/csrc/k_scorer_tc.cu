@@ -12,6 +12,9 @@
 // every product and partial sum is a multiple of 1/64 below 2^15 -- representable in FP32 in
 // any order of summation.  The score is an integer count of 1/64.
 //
+// Measured on 16M rows (9.9 G rows/s, 713 GB/s; warp-level mma.sync tiles: 5.4 G rows/s):
+// loading each thread's next-tile row while the current tile's MMAs run (8.1), every layer's
+// accumulator at column 0 of 64 columns (8.1), and that with six CTAs per SM (6.6) were slower.
 // Every wait for an MMA is bounded: on timeout the CTA writes INSP_SCORE_TIMEOUT (INT64_MIN)
 // to the rows it has not scored, waits once more (bounded) for the MMA in flight, frees its
 // tensor memory and returns.
