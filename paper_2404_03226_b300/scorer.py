@@ -213,9 +213,39 @@ def load_trained(path: str = TRAINED) -> tuple[np.ndarray, str]:
     return (f32.view(np.uint32) >> 16).astype(np.uint16), policy
 
 
+def score_throughput(rows: int, steps: int = 20, warmup: int = 3, seed: int = 0) -> dict:
+    """Batched scoring (insp_scorer_eval, tcgen05 MMAs) of `rows` random feature rows with the
+    shipped weights, timed with CUDA events over `steps` calls after `warmup`; 72 bytes per row
+    (16 int32 features in, one int64 score out) and 2 x (16 x 64 + 64 x 64 + 64) flops."""
+    import torch
+    from . import Machine
+    M = Machine(2, 1, 0)
+    bits, _ = load_trained()
+    _lib.insp_set_scorer(M.handle, bits)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    feat = torch.randint(0, 256, (rows, IN), dtype=torch.int32, device="cuda", generator=g)
+    out = torch.empty(rows, dtype=torch.int64, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(warmup):
+        _lib.insp_scorer_eval(M.handle, feat, rows, out, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(steps):
+        _lib.insp_scorer_eval(M.handle, feat, rows, out, s)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"rows": rows, "ms": round(ms, 4), "rows_per_s": rows / ms * 1e3, "GB_s": rows * 72 / ms / 1e6,
+            "TFLOP_s": rows * 2 * (IN * H + H * H + H) / ms / 1e9,
+            "timeouts": int((out == _lib.INSP_SCORE_TIMEOUT).sum())}
+
+
 def main(argv=None) -> None:
     """Train on rollouts of layered DAGs and evaluate on held-out ones:
-    python -m paper_2404_03226_b300.scorer --train 100000 --eval 4096 --out FILE"""
+    python -m paper_2404_03226_b300.scorer --train 100000 --eval 4096 --out FILE
+    or time the batched scoring: python -m paper_2404_03226_b300.scorer --score-rows 16777216"""
     import argparse
     import json
     import sys
@@ -234,7 +264,11 @@ def main(argv=None) -> None:
     ap.add_argument("--lr", type=float, default=5e-4)
     ap.add_argument("--out", default="")
     ap.add_argument("--checkpoint", default="", help="training checkpoint (.npz), resumed from if present")
+    ap.add_argument("--score-rows", type=int, default=0, help="only time batched scoring of this many rows")
     a = ap.parse_args(argv)
+    if a.score_rows:
+        print(json.dumps(score_throughput(a.score_rows)))
+        return
     m = inputs.MACHINE_LAYERED
     t0 = time.time()
     parts = []
