@@ -1,6 +1,7 @@
 // Fifth-generation tensor-core primitives (tcgen05) of sm_100-family GPUs, as inline PTX:
 // tensor-memory allocation, shared-memory matrix descriptors, the single-thread MMA issue
-// with its mbarrier commit, and the warp loads of accumulators from tensor memory.
+// with its mbarrier commit, the warp loads of accumulators from tensor memory, and the
+// one-dimensional bulk copy (TMA) that stages operands in shared memory.
 //
 // Layout used throughout (the PTX ISA's canonical K-major layout without swizzling): an
 // operand of R rows and K 16-bit columns is cut into core matrices of 8 rows x 8 columns
@@ -89,6 +90,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     for (uint32_t i = 0; i < limit; ++i)
         if (mbar_try_wait(mbar, parity)) return true;
     return false;
+}
+
+// One-dimensional bulk copy (TMA) of `bytes` from global to shared memory, completing on the
+// mbarrier as transaction bytes; both addresses 16-byte aligned, bytes a multiple of 16.  The
+// issuing thread first announces the bytes with its arrival (the barrier counts one arrival).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst_smem, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
 }
 
 // Warp load of 16 consecutive 32-bit accumulator columns of the warp's 32 tensor-memory lanes

@@ -67,6 +67,13 @@ def test_scorer_eval_many_tiles_ragged_and_clamped():
     rows = np.unique(np.concatenate([np.arange(0, n, 211), np.arange(n - 300, n), np.arange(0, 300)]))
     exp = np.array([oracle.mlp_score(k, np.clip(feat[r], 0, 255)) for r in rows])
     np.testing.assert_array_equal(got[rows], exp)
+    # rows that are not 16-byte aligned (one int32 in): per-thread loads instead of bulk copies
+    flat = torch.empty(n * 16 + 1, dtype=torch.int32, device="cuda")
+    flat[1:] = d_feat.reshape(-1)
+    out2 = torch.full((n,), 7, dtype=torch.int64, device="cuda")
+    _lib.insp_scorer_eval(M.handle, flat[1:], n, out2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out2.cpu().numpy(), got)
     t0 = time.perf_counter()
     for _ in range(10):
         _lib.insp_scorer_eval(M.handle, d_feat, n, out)
