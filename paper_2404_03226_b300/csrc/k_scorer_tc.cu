@@ -16,10 +16,12 @@
 // buffers, two tiles ahead of the MMAs.  Measured on 16M rows: 12.3 G rows/s (884 GB/s)
 // against 9.9 with per-thread loads and 5.4 for the warp-level mma.sync tiles; per-thread
 // register prefetch of the next row (8.1), every layer's accumulator at column 0 of 64 columns
-// (8.1), and that with six CTAs per SM (6.6) were slower.
-// Every wait for an MMA is bounded: on timeout the CTA writes INSP_SCORE_TIMEOUT (INT64_MIN)
-// to the rows it has not scored, waits once more (bounded) for the MMA in flight, frees its
-// tensor memory and returns.
+// (8.1), and that with six CTAs per SM (6.6) were slower.  Feature rows that are not 16-byte
+// aligned are loaded by each thread instead.
+//
+// Every wait (an MMA commit, a bulk copy) is bounded: on timeout the CTA writes
+// INSP_SCORE_TIMEOUT (INT64_MIN) to the rows it has not scored, waits once more (bounded) for
+// the MMA and the copies in flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include <algorithm>
