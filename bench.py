@@ -150,14 +150,15 @@ def path_bytes(batch):
     return 4 * (n + nd) + 4 * m + n + 8 * n + 20 * n + 8 * nd + costs
 
 
-def profile_record(kernel: str):
+def profile_record(kernel: str, workload: str):
     """The counters an ncu capture recorded in profiles/ for a kernel (per-step DRAM bytes and
-    warp instructions, scaled to the full workload), if the kernel source has not changed since."""
+    warp instructions, scaled to the full workload), if they were taken on this workload and the
+    kernel source has not changed since."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     if not os.path.exists(p):
         return None
     rec = json.load(open(p)).get(kernel)
-    if not rec:
+    if not rec or rec.get("workload") != workload:
         return None
     src = os.path.join(ROOT, "paper_2404_03226_b300", "csrc", rec["source"])
     if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
@@ -165,15 +166,15 @@ def profile_record(kernel: str):
     return rec
 
 
-def traffic_from_profile(kernel: str, launches_per_step: float):
+def traffic_from_profile(kernel: str, launches_per_step: float, workload: str):
     """dram bytes per launch from the per-step figure of the kernel's ncu record."""
-    rec = profile_record(kernel)
+    rec = profile_record(kernel, workload)
     if rec is None:
         return None
     return rec["bytes_per_step_full"] / max(launches_per_step, 1.0)
 
 
-def issue_roofline(names, kms, steps, sms: int, sm_mhz: float, dom: str):
+def issue_roofline(names, kms, steps, sms: int, sm_mhz: float, dom: str, workload: str):
     """Second roofline: SM instruction issue.  achieved = warp instructions per step (ncu
     smsp__inst_executed.sum of the recorded capture, scaled to the workload) over the kernel's
     measured time; peak = SMs x 4 schedulers x 1 warp instruction per cycle x the SM clock
@@ -181,7 +182,7 @@ def issue_roofline(names, kms, steps, sms: int, sm_mhz: float, dom: str):
     peak = sms * 4 * sm_mhz * 1e6 / 1e9  # G warp instructions / s
     per = {}
     for k, name in enumerate(names):
-        rec = profile_record(name)
+        rec = profile_record(name, workload)
         if rec is None or "inst_per_step_full" not in rec or kms[k] <= 0:
             per[name] = None
             continue
@@ -529,11 +530,13 @@ def run_ours(args, rank, world, local_rank):
     # each input read once and each output written once) over the dominant kernel's time per
     # step (= bytes per launch / mean launch time; one launch per size group and step)
     pb = path_bytes(batch)
+    # the recorded counters were taken on the layered workload (scaled to its 4096 DAGs)
+    rec_key = f"{args.workload}:{args.ndag}" if args.workload == "layered" else args.workload
     dom_s = kms[names.index(dom)] / 1e3 / args.steps
     achieved = pb / dom_s / 1e9
     own = alg[dom] / dom_s / 1e9  # the dominant kernel's own inputs and outputs only
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_from_profile(dom, klaunch[names.index(dom)] / args.steps), "kernel": dom,
+                "traffic": traffic_from_profile(dom, klaunch[names.index(dom)] / args.steps, rec_key), "kernel": dom,
                 "peak_source": f"{peak_kind} hbm_gbs",
                 "path_bytes_per_step": int(pb), "path_bytes_per_task": round(pb / max(n, 1), 2),
                 "kernel_own_bytes": {k: int(v) for k, v in alg.items()},
@@ -542,7 +545,7 @@ def run_ours(args, rank, world, local_rank):
                 "kernel_share": {k: round(v, 4) for k, v in share.items()},
                 "step_frac": pb / (t_max / args.steps) / 1e9 / peak}
     roofline_issue = issue_roofline(names, kms, args.steps, torch.cuda.get_device_properties(dev).multi_processor_count,
-                                    clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0, dom)
+                                    clk["sm_mhz"] or clk["sm_max_mhz"] or 2032.0, dom, rec_key)
 
     # ---- per-DAG launch form on a sample (same kernels, one DAG per launch)
     per_dag = None
@@ -614,7 +617,7 @@ def run_ours(args, rank, world, local_rank):
 
         ia_e, ie_e = torch.empty_like(ia), torch.empty_like(ie)
         streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]  # non-blocking: loads run beside them
-        k_e2e = max(1, min(args.steps, 10))
+        k_e2e = max(1, min(args.steps, 30))
         # one step at a time: load, evaluate, read back
         free0 = torch.cuda.mem_get_info(dev)[0]
         h_first = load()

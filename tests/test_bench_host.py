@@ -40,21 +40,25 @@ def _fake_root(tmp_path, src_text, sha):
     d = tmp_path / "paper_2404_03226_b300" / "csrc"
     d.mkdir(parents=True)
     (d / "k_x.cu").write_text(src_text)
-    rec = {"k_x": {"source": "k_x.cu", "source_sha": sha, "bytes_per_step_small": 100,
+    rec = {"k_x": {"source": "k_x.cu", "source_sha": sha, "workload": "layered:4096", "bytes_per_step_small": 100,
                    "bytes_per_step_full": 4000, "inst_per_step_small": 10, "inst_per_step_full": 2_000_000_000}}
     (tmp_path / "profiles" / "dram_traffic.json").write_text(json.dumps(rec))
 
 
-def test_profile_counters_only_for_the_unchanged_source(tmp_path, monkeypatch):
+def test_profile_counters_only_for_the_unchanged_source_and_their_workload(tmp_path, monkeypatch):
     src = "__global__ void k_x() {}\n"
     sha = hashlib.sha256(src.encode()).hexdigest()[:16]
     _fake_root(tmp_path, src, sha)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.traffic_from_profile("k_x", 2.0) == 2000.0  # per launch: two launches per step
-    assert bench.traffic_from_profile("k_missing", 1.0) is None
+    w = "layered:4096"
+    assert bench.traffic_from_profile("k_x", 2.0, w) == 2000.0  # per launch: two launches per step
+    assert bench.traffic_from_profile("k_missing", 1.0, w) is None
+    # counters of another workload (or the same kernel on a prefix of it) do not apply
+    assert bench.traffic_from_profile("k_x", 1.0, "tiled") is None
+    assert bench.profile_record("k_x", "layered:2048") is None
     (tmp_path / "paper_2404_03226_b300" / "csrc" / "k_x.cu").write_text(src + "// edited\n")
-    assert bench.traffic_from_profile("k_x", 1.0) is None
-    assert bench.profile_record("k_x") is None
+    assert bench.traffic_from_profile("k_x", 1.0, w) is None
+    assert bench.profile_record("k_x", w) is None
 
 
 def test_issue_roofline_arithmetic(tmp_path, monkeypatch):
@@ -62,10 +66,11 @@ def test_issue_roofline_arithmetic(tmp_path, monkeypatch):
     _fake_root(tmp_path, src, hashlib.sha256(src.encode()).hexdigest()[:16])
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     # 2 G warp instructions per step, 10 steps in 20 ms of kernel time: 1000 G/s; peak 148 x 4 x 2 GHz
-    r = bench.issue_roofline(["k_x", "k_y"], np.array([20.0, 5.0]), 10, 148, 2000.0, "k_x")
+    r = bench.issue_roofline(["k_x", "k_y"], np.array([20.0, 5.0]), 10, 148, 2000.0, "k_x", "layered:4096")
     assert r["peak"] == 1184.0
     assert r["achieved"] == 1000.0 and abs(r["frac"] - 1000.0 / 1184.0) < 1e-4
     assert r["per_kernel"]["k_y"] is None
+    assert bench.issue_roofline(["k_x"], np.array([20.0]), 10, 148, 2000.0, "k_x", "mixed")["achieved"] is None
 
 
 def test_cpu_sample_and_threaded_oracle():
