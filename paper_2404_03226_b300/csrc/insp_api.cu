@@ -403,9 +403,7 @@ int find_repeated_structures(insp_batch *b, cudaStream_t s) {
     DeviceInfo di;
     int rc = device_info(di);
     if (rc) return rc;
-    DBuf &hash = b->bufs->dag_hash;
-    if ((rc = hash.alloc(size_t(nd) * 8))) return rc;
-    insp::launch_dag_hash(b->dev(), hash.as<unsigned long long>(), std::min(nd, di.sms * 8), s);
+    DBuf &hash = b->bufs->dag_hash;  // fingerprints, summed by the validation pass
     std::vector<unsigned long long> h(nd);
     CU(cudaMemcpyAsync(h.data(), hash.p, size_t(nd) * 8, cudaMemcpyDeviceToHost, s));
     CU(cudaMemcpyAsync(b->h_dag_span.data(), b->dag_span.p, size_t(nd) * 4, cudaMemcpyDeviceToHost, s));
@@ -929,7 +927,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     if ((rc = b->indeg0.alloc(std::max<int64_t>(b->n_total, 1) * 4)) ||
         (rc = b->unit_time_def.alloc(std::max(ndag, 1) * 8)) || (rc = b->unit_time_user.alloc(std::max(ndag, 1) * 8)) ||
         (rc = b->status.alloc(std::max(ndag, 1) * 4)) || (rc = b->max_span.alloc(4)) || (rc = b->counters.alloc(512)) ||
-        (rc = b->dag_span.alloc(std::max(ndag, 1) * 4)))
+        (rc = b->dag_span.alloc(std::max(ndag, 1) * 4)) || (rc = b->bufs->dag_hash.alloc(std::max(ndag, 1) * 8)))
         return bail(rc);
     if (cudaMemsetAsync(b->indeg0.p, 0, std::max<int64_t>(b->n_total, 1) * 4, ls) != cudaSuccess ||
         cudaMemsetAsync(b->max_span.p, 0, 4, ls) != cudaSuccess)
@@ -940,7 +938,8 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
     const int grid = std::max(1, std::min(ndag, di.sms * 8));
     if (ndag > 0) {
         insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
-                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, ls);
+                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(),
+                              b->bufs->dag_hash.as<unsigned long long>(), b->max_n, grid, ls);
         insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, ls);
     }
     if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
@@ -958,7 +957,8 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
             cudaMemsetAsync(b->max_span.p, 0, 4, ls) != cudaSuccess)
             return bail(fail(INSP_ECUDA, "memset"));
         insp::launch_validate(B, b->mach.xfer, b->status.as<int32_t>(), b->indeg0.as<int32_t>(),
-                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(), grid, ls);
+                              b->max_span.as<int32_t>(), b->dag_span.as<int32_t>(),
+                              b->bufs->dag_hash.as<unsigned long long>(), b->max_n, grid, ls);
         insp::launch_unit_time(B, b->status.as<int32_t>(), b->unit_time_def.as<int64_t>(), grid, ls);
         if (cudaStreamSynchronize(ls) != cudaSuccess || cudaGetLastError() != cudaSuccess)
             return bail(fail(INSP_ECUDA, "validation kernels failed"));
@@ -1018,7 +1018,7 @@ INSP_API int insp_batch_load_csr(insp_machine *m, int32_t ndag, const int64_t *t
             (rc = cursor.alloc(std::max<int64_t>(b->n_total, 1) * 4)))
             return bail(rc);
         insp::launch_reverse_csr(B, b->indeg0.as<int32_t>(), b->pr_ptr.as<int32_t>(), cursor.as<int32_t>(),
-                                 b->pcol.as<int32_t>(), grid, ls);
+                                 b->pcol.as<int32_t>(), b->max_n, grid, ls);
         b->pull = true;
     }
     if ((rc = alloc_scratch(b, ls))) return bail(rc);

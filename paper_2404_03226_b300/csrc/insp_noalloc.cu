@@ -215,7 +215,7 @@ INSP_API int insp_simulate_noalloc(int32_t n, const int32_t *row_ptr, const int3
     B.type_cost = type_cost;
     B.task_cost = task_cost;
     int32_t *indeg0 = reinterpret_cast<int32_t *>(S + OFF_INDEG);
-    insp::launch_validate(B, xfer_ns, status, indeg0, max_span, nullptr, 1, s);
+    insp::launch_validate(B, xfer_ns, status, indeg0, max_span, nullptr, nullptr, n, 1, s);
     insp::launch_unit_time(B, status, unit_time, 1, s);
     int32_t st = 0;
     NA_CU(cudaMemcpyAsync(&st, status, 4, cudaMemcpyDeviceToHost, s));

@@ -265,35 +265,6 @@ __global__ void k_ia_copy(DevBatch B, const int2 *pairs, int32_t n_pairs, int32_
     }
 }
 
-// Structure fingerprint of every DAG: a sum (order-free, so deterministic) of 64-bit mixes of
-// (position, value) over the task count, row offsets and successor ids.  Equal structures give
-// equal fingerprints; the host confirms candidates with k_dag_equal before sharing anything.
-__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
-    x += 0x9e3779b97f4a7c15ull;
-    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
-    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
-    return x ^ (x >> 31);
-}
-__global__ void __launch_bounds__(256) k_dag_hash(DevBatch B, unsigned long long *hash) {
-    __shared__ unsigned long long s_h;
-    for (int d = blockIdx.x; d < B.ndag; d += gridDim.x) {
-        if (threadIdx.x == 0) s_h = 0;
-        __syncthreads();
-        const int64_t tb = B.task_base[d], eb = B.edge_base[d];
-        const int64_t n = B.task_base[d + 1] - tb, m = B.edge_base[d + 1] - eb;
-        const int32_t *rp = B.row_ptr + tb + d;
-        const int32_t *col = B.col_idx + eb;
-        unsigned long long h = threadIdx.x == 0 ? mix64(uint64_t(n) * 0x100000001ull + uint64_t(m)) : 0ull;
-        for (int64_t i = threadIdx.x; i <= n; i += blockDim.x) h += mix64((uint64_t(i) << 32) ^ uint32_t(rp[i]));
-        for (int64_t e = threadIdx.x; e < m; e += blockDim.x)
-            h += mix64(((uint64_t(e) + 0x80000000ull) << 32) ^ uint32_t(col[e]) ^ 0x5bd1e995ull);
-        atomicAdd(&s_h, h);
-        __syncthreads();
-        if (threadIdx.x == 0) hash[d] = s_h;
-        __syncthreads();
-    }
-}
-
 // Exact comparison of candidate pairs {dag, representative} of equal fingerprints, task counts
 // and edge counts: same[k] = 1 when their row offsets and successor ids are equal.
 __global__ void __launch_bounds__(256) k_dag_equal(DevBatch B, const int2 *pairs, int32_t n_pairs, int32_t *same) {
@@ -461,9 +432,6 @@ void launch_ia_zero(const DevBatch &B, const int32_t *dags, int32_t n_dags, int3
 }
 void launch_ia_copy(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *ia, cudaStream_t s) {
     if (n_pairs > 0) k_ia_copy<<<std::min(n_pairs, 4096), 256, 0, s>>>(B, pairs, n_pairs, ia);
-}
-void launch_dag_hash(const DevBatch &B, unsigned long long *hash, int grid, cudaStream_t s) {
-    k_dag_hash<<<grid, 256, 0, s>>>(B, hash);
 }
 void launch_dag_equal(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *same, cudaStream_t s) {
     if (n_pairs > 0) k_dag_equal<<<std::min(n_pairs, 4096), 256, 0, s>>>(B, pairs, n_pairs, same);

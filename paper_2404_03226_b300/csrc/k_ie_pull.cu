@@ -27,6 +27,7 @@
 // 32-bit codes each lane only reads its own column (its own earlier writes); with
 // 16-bit codes lanes read words other lanes wrote, so a __syncwarp orders every
 // row's store before the later visits' loads.
+#include <algorithm>
 #include <type_traits>
 
 #include "common.cuh"
@@ -397,48 +398,71 @@ __global__ void __maxnreg__(IE_PULL_MAXREG)
     }
 }
 
-// Predecessor lists of every DAG (CSR of the reversed edges, same layout as
-// row_ptr / col_idx): exclusive scan of the in-degrees, then a scatter.  Order
-// within a list is irrelevant to the max.  One CTA per DAG.
+// Exclusive prefix sum over the 256 threads of a CTA (8 warps): returns this thread's offset and
+// the CTA total.  s_w: 8 ints of shared memory, free again when the call returns.
+__device__ __forceinline__ int32_t cta_exclusive_scan(int32_t x, int32_t *s_w, int32_t &total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int32_t w = lane < 8 ? s_w[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            const int32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < 8) s_w[lane] = w;
+    }
+    __syncthreads();
+    const int32_t before = warp ? s_w[warp - 1] : 0;
+    total = s_w[7];
+    __syncthreads();
+    return before + incl - x;
+}
+
+// Predecessor lists of every DAG (CSR of the reversed edges, same layout as row_ptr / col_idx),
+// one CTA of 256 threads per DAG: exclusive scan of the in-degrees (each thread a contiguous
+// chunk, then a CTA scan of the chunk sums), then a scatter by one warp per row, its lanes over
+// the row's successors (coalesced), with the insertion cursors in shared memory for DAGs of up to
+// smem_n tasks (else in `cursor`).  Order within a list is irrelevant to the max.
 __global__ void __launch_bounds__(256) k_reverse_csr(DevBatch B, const int32_t *indeg0, int32_t *pr_ptr,
-                                                     int32_t *cursor, int32_t *pcol) {
-    __shared__ int32_t s_scan[256];
-    __shared__ int32_t s_carry;
+                                                     int32_t *cursor, int32_t *pcol, int32_t smem_n) {
+    extern __shared__ int32_t s_cur[];  // smem_n cursors
+    __shared__ int32_t s_w[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int d = blockIdx.x; d < B.ndag; d += gridDim.x) {
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];
         const int32_t n = int32_t(B.task_base[d + 1] - tb);
         int32_t *pp = pr_ptr + tb + d;
-        if (threadIdx.x == 0) s_carry = 0;
-        __syncthreads();
-        for (int32_t base = 0; base < n; base += blockDim.x) {
-            const int32_t i = base + threadIdx.x;
-            const int32_t x = i < n ? indeg0[tb + i] : 0;
-            s_scan[threadIdx.x] = x;
-            __syncthreads();
-            for (int off = 1; off < int(blockDim.x); off <<= 1) {
-                const int32_t y = threadIdx.x >= unsigned(off) ? s_scan[threadIdx.x - off] : 0;
-                __syncthreads();
-                s_scan[threadIdx.x] += y;
-                __syncthreads();
-            }
-            const int32_t incl = s_scan[threadIdx.x];
-            if (i < n) {
-                pp[i] = s_carry + incl - x;
-                cursor[tb + i] = s_carry + incl - x;
-            }
-            __syncthreads();
-            if (threadIdx.x == blockDim.x - 1) s_carry += incl;
-            __syncthreads();
+        const bool in_smem = n <= smem_n;
+        int32_t *cur = in_smem ? s_cur : cursor + tb;
+        const int32_t chunk = (n + 255) / 256, c0 = min(n, int32_t(threadIdx.x) * chunk), c1 = min(n, c0 + chunk);
+        int32_t sum = 0;
+        for (int32_t i = c0; i < c1; ++i) sum += indeg0[tb + i];
+        int32_t total;
+        int32_t off = cta_exclusive_scan(sum, s_w, total);
+        for (int32_t i = c0; i < c1; ++i) {
+            pp[i] = off;
+            cur[i] = off;
+            off += indeg0[tb + i];
         }
-        if (threadIdx.x == 0) pp[n] = s_carry;
+        if (threadIdx.x == 0) pp[n] = total;
         __syncthreads();
         const int32_t *rp = B.row_ptr + tb + d;
-        for (int32_t u = threadIdx.x; u < n; u += blockDim.x)
-            for (int32_t e = rp[u]; e < rp[u + 1]; ++e) {
-                const int32_t v = B.col_idx[eb + e];
-                const int32_t pos = atomicAdd(&cursor[tb + v], 1);
-                pcol[eb + pos] = u;
+        const int32_t *col = B.col_idx + eb;
+        for (int32_t u = warp; u < n; u += 8) {
+            const int32_t lo = rp[u], hi = rp[u + 1];
+            for (int32_t e = lo + lane; e < hi; e += 32) {
+                const int32_t v = col[e];
+                pcol[eb + atomicAdd(&cur[v], 1)] = u;
             }
+        }
         __syncthreads();
     }
 }
@@ -470,8 +494,10 @@ void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pco
 }
 
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
-                        int grid, cudaStream_t s) {
-    k_reverse_csr<<<grid, 256, 0, s>>>(B, indeg0, pr_ptr, cursor, pcol);
+                        int32_t max_n, int grid, cudaStream_t s) {
+    const int32_t smem_n = std::max(0, std::min(max_n, VALIDATE_SMEM_TASKS));
+    cudaFuncSetAttribute(k_reverse_csr, cudaFuncAttributeMaxDynamicSharedMemorySize, VALIDATE_SMEM_TASKS * 4);
+    k_reverse_csr<<<grid, 256, size_t(smem_n) * 4, s>>>(B, indeg0, pr_ptr, cursor, pcol, smem_n);
 }
 
 }  // namespace insp

@@ -1,17 +1,34 @@
 // DAG ingest: validation of the CSR and cost tables, in-degrees, the largest
 // edge span per DAG and over the batch (window sizes of the inspiring-efficiency
 // sweep) and each DAG's default unit time (4 x the lower median of its GPU costs).
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 
 namespace insp {
 
-// One CTA per DAG (grid-stride over DAGs).  Error precedence matches the
-// header: INSP_EINVAL, then INSP_ENOTTOPO, then INSP_EOVERFLOW.
+// Structure fingerprint terms (splitmix64 finaliser): a DAG's fingerprint is the wrapping sum of
+// mix64 over its task and edge counts, every row offset with its index and every successor id
+// with its edge index.  Equal structures have equal fingerprints; the load compares candidate
+// pairs exactly before sharing anything.
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// Per DAG (one CTA each, grid-stride over DAGs): validation (error precedence as in the header:
+// INSP_EINVAL, then INSP_ENOTTOPO, then INSP_EOVERFLOW), then -- for DAGs whose edges are in range -- one coalesced
+// pass over the flat successor array that counts in-degrees (in shared memory for DAGs of up to
+// smem_n tasks, else by global atomics) and sums the structure fingerprint (hash may be NULL).
 __global__ void __launch_bounds__(256) k_validate(DevBatch B, int64_t xfer, int32_t *status, int32_t *indeg0,
-                                                  int32_t *max_span, int32_t *dag_span) {
+                                                  int32_t *max_span, int32_t *dag_span, unsigned long long *hash,
+                                                  int32_t smem_n) {
+    extern __shared__ int32_t s_indeg[];  // smem_n counters
     __shared__ uint32_t s_flags;
-    __shared__ unsigned long long s_sum;
+    __shared__ unsigned long long s_sum, s_h;
     __shared__ int32_t s_span;
     for (int d = blockIdx.x; d < B.ndag; d += gridDim.x) {
         const int64_t tb = B.task_base[d], eb = B.edge_base[d];
@@ -61,12 +78,30 @@ __global__ void __launch_bounds__(256) k_validate(DevBatch B, int64_t xfer, int3
             atomicMax(max_span, s_span);
             if (dag_span) dag_span[d] = s_span;
         }
-        // in-degrees (valid DAGs, and DAGs whose numbering is not topological: renumbering uses them)
+        // in-degrees and fingerprint (valid DAGs, and DAGs whose numbering is not topological:
+        // renumbering uses the in-degrees, and they are validated again afterwards)
         if (st == INSP_OK || st == INSP_ENOTTOPO) {
-            const int32_t n = int32_t(n64);
+            const int32_t n = int32_t(n64), m = int32_t(m64);
             const int32_t *rp = B.row_ptr + tb + d;
-            for (int32_t t = threadIdx.x; t < n; t += blockDim.x)
-                for (int32_t e = rp[t]; e < rp[t + 1]; ++e) atomicAdd(&indeg0[tb + B.col_idx[eb + e]], 1);
+            const int32_t *col = B.col_idx + eb;
+            const bool in_smem = n <= smem_n;
+            if (in_smem)
+                for (int32_t t = threadIdx.x; t < n; t += blockDim.x) s_indeg[t] = 0;
+            if (threadIdx.x == 0) s_h = 0;
+            __syncthreads();
+            unsigned long long h = threadIdx.x == 0 ? mix64(uint64_t(n) * 0x100000001ull + uint64_t(m)) : 0ull;
+            for (int32_t i = threadIdx.x; i <= n; i += blockDim.x) h += mix64((uint64_t(i) << 32) ^ uint32_t(rp[i]));
+            for (int32_t e = threadIdx.x; e < m; e += blockDim.x) {
+                const int32_t v = col[e];
+                if (in_smem) atomicAdd(&s_indeg[v], 1);
+                else atomicAdd(&indeg0[tb + v], 1);
+                h += mix64(((uint64_t(e) + 0x80000000ull) << 32) ^ uint32_t(v) ^ 0x5bd1e995ull);
+            }
+            atomicAdd(&s_h, h);
+            __syncthreads();
+            if (in_smem)
+                for (int32_t t = threadIdx.x; t < n; t += blockDim.x) indeg0[tb + t] = s_indeg[t];
+            if (hash && threadIdx.x == 0) hash[d] = s_h;
         }
         __syncthreads();
     }
@@ -366,9 +401,10 @@ void launch_permute(const int64_t *task_base, int32_t ndag, const int32_t *old_o
 }
 
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
-                     int32_t *dag_span,
-                     int grid, cudaStream_t s) {
-    k_validate<<<grid, 256, 0, s>>>(B, xfer, status, indeg0, max_span, dag_span);
+                     int32_t *dag_span, unsigned long long *hash, int32_t max_n, int grid, cudaStream_t s) {
+    const int32_t smem_n = std::max(0, std::min(max_n, VALIDATE_SMEM_TASKS));
+    cudaFuncSetAttribute(k_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, VALIDATE_SMEM_TASKS * 4);
+    k_validate<<<grid, 256, size_t(smem_n) * 4, s>>>(B, xfer, status, indeg0, max_span, dag_span, hash, smem_n);
 }
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s) {
     k_unit_time<<<grid, 256, 0, s>>>(B, status, unit_time);

@@ -47,9 +47,12 @@ struct SimArgs {
     int32_t *tr_pop_task, *tr_pop_worker, *tr_pop_nready, *tr_pop_mode;
 };
 
+// DAGs of up to this many tasks count their in-degrees (validation) and predecessor-list cursors
+// in shared memory; larger ones use global atomics
+constexpr int32_t VALIDATE_SMEM_TASKS = 16384;
+// validation, in-degrees, spans and (hash != NULL) structure fingerprints; max_n: the largest DAG
 void launch_validate(const DevBatch &B, int64_t xfer, int32_t *status, int32_t *indeg0, int32_t *max_span,
-                     int32_t *dag_span,
-                     int grid, cudaStream_t s);
+                     int32_t *dag_span, unsigned long long *hash, int32_t max_n, int grid, cudaStream_t s);
 void launch_unit_time(const DevBatch &B, const int32_t *status, int64_t *unit_time, int grid, cudaStream_t s);
 // Renumbering of the listed DAGs (ids not topological): Kahn rounds, ascending old id within a
 // round (k_load.cu).  Scratch cnt, level, qa, qb: per task (global indexing); n_levels: per
@@ -90,7 +93,6 @@ void launch_ia_blk(const DevBatch &B, const int2 *items, int32_t n_items, int32_
                    int grid, int warps, cudaStream_t s);
 void launch_ia_zero(const DevBatch &B, const int32_t *dags, int32_t n_dags, int32_t *ia, cudaStream_t s);
 void launch_ia_copy(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *ia, cudaStream_t s);
-void launch_dag_hash(const DevBatch &B, unsigned long long *hash, int grid, cudaStream_t s);
 void launch_dag_equal(const DevBatch &B, const int2 *pairs, int32_t n_pairs, int32_t *same, cudaStream_t s);
 int ia_blk_occupancy(int warps);
 // inspiring efficiency, pull form (k_ie_pull.cu)
@@ -111,7 +113,7 @@ void launch_ie_pull(const DevBatch &B, const int32_t *pr_ptr, const int32_t *pco
                     const int64_t *unit_time, const int32_t *dag_span, int32_t W, int32_t *gring, int32_t *ie,
                     int grid, int warps, cudaStream_t s);
 void launch_reverse_csr(const DevBatch &B, const int32_t *indeg0, int32_t *pr_ptr, int32_t *cursor, int32_t *pcol,
-                        int grid, cudaStream_t s);
+                        int32_t max_n, int grid, cudaStream_t s);
 // learned scorer (k_mlp.cu)
 void launch_scorer_eval(const ScorerPacked *P, const int32_t *feat, int64_t n, int64_t *score, cudaStream_t s);
 void launch_mlp_train_grad(int32_t in, int32_t h1, int32_t h2, const float *w, int32_t mode, int64_t n,
