@@ -630,12 +630,16 @@ def run_ours(args, rank, world, local_rank):
         t_serial = (time.perf_counter() - t0) / k_e2e
         assert np.array_equal(o_m.numpy(), mk.cpu().numpy())
 
-        # as a serving loop runs it: the next batch loads (H2D, validation, predecessor lists) on a
-        # host thread and its own stream while this one evaluates, and each step's read-back
-        # (asynchronous, into pinned memory) overlaps the next step's kernels; steps alternate
-        # between two streams and two sets of outputs
-        # three batches alive at once (loading, evaluating, reading back) must fit the device
-        serving = torch.cuda.mem_get_info(dev)[0] > 3.2 * per_batch
+        # as a serving loop runs it: the next batches load (H2D, validation, predecessor lists) on
+        # host threads, each batch on its own stream, while this one evaluates, and each step's
+        # read-back (asynchronous, into pinned memory) overlaps the next step's kernels; steps
+        # alternate between two streams and two sets of outputs.  A load's ingest kernels get SM
+        # slots only as the evaluation's persistent CTAs retire, so one loader thread cannot keep
+        # up (12.3 ms per load beside an evaluation against 8.6 alone); three can.  Batches alive:
+        # one per loader, the one evaluating, the one reading back.
+        free_now = torch.cuda.mem_get_info(dev)[0]
+        loaders = max((k for k in (3, 2, 1) if free_now > (k + 2.2) * per_batch), default=0)
+        serving = loaders > 0
         if serving:
             import queue
             import threading
@@ -643,13 +647,13 @@ def run_ours(args, rank, world, local_rank):
                     (torch.empty_like(ia), torch.empty_like(ie), torch.empty(n, dtype=torch.int32).pin_memory(),
                      torch.empty(n, dtype=torch.int64).pin_memory(), torch.empty(n, dtype=torch.int64).pin_memory(),
                      torch.empty(ndag, dtype=torch.int64).pin_memory())]
-            slots = threading.Semaphore(3)  # batches alive: loading, evaluating, reading back
+            slots = threading.Semaphore(loaders + 2)  # batches alive: loading, evaluating, reading back
             q = queue.Queue()
-            warm = 2
+            warm = 2 + loaders
 
-            def loader():
+            def loader(count):
                 try:
-                    for _ in range(warm + k_e2e):
+                    for _ in range(count):
                         slots.acquire()
                         q.put(load())
                 except Exception as exc:  # handed to the evaluating thread
@@ -664,8 +668,14 @@ def run_ours(args, rank, world, local_rank):
                 if rc != 0:
                     raise RuntimeError("device-side status not OK in the e2e loop: " + _lib.last_error())
 
-            th = threading.Thread(target=loader, daemon=True)  # never blocks the exit after an error
-            th.start()
+            # the loaders run on past the timed steps by the pipeline's depth, so that the window ends
+            # as full as it began (batches loaded before it are balanced by loads in flight after it)
+            extra = loaders + 2
+            total = warm + k_e2e + extra
+            ths = [threading.Thread(target=loader, args=(total // loaders + (i < total % loaders),), daemon=True)
+                   for i in range(loaders)]  # daemons: never block the exit after an error
+            for th in ths:
+                th.start()
             pending = None
             for k in range(warm + k_e2e):
                 if k == warm:
@@ -684,12 +694,20 @@ def run_ours(args, rank, world, local_rank):
                 pending = (h, j)
             finish(pending)
             t_e2e = (time.perf_counter() - t0) / k_e2e
-            th.join()
+            for _ in range(extra):  # the fill after the window: loaded, not evaluated
+                h = q.get()
+                if isinstance(h, Exception):
+                    raise h
+                _lib.insp_batch_destroy(h)
+                slots.release()
+            for th in ths:
+                th.join()
             for o in outs:
                 assert np.array_equal(o[5].numpy(), mk.cpu().numpy())
             e2e = {"value": n / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                    "ms_per_step": t_e2e * 1e3, "steps": k_e2e,
-                   "mode": "serving loop: the next step's load and this step's read-back overlap the kernels",
+                   "mode": f"serving loop: {loaders} loader threads load the next batches and this step's read-back "
+                           f"overlaps the kernels",
                    "serial": {"value": n / t_serial, "ms_per_step": t_serial * 1e3}}
         else:  # one batch at a time: the serial figure is the end-to-end one
             e2e = {"value": n / t_serial, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
