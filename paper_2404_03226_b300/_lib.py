@@ -291,7 +291,24 @@ def insp_simulate_noalloc(n, row_ptr, col_idx, type, n_types, type_cost, task_co
                                       ptr(worker), ptr(start), ptr(end), ptr(makespan), stream_ptr(stream)))
 
 
+def _check_tensor(name, x, dtype: str, numel: int):
+    """A raw pointer is taken from x: its dtype, layout, length and device are checked first."""
+    if x is None or not hasattr(x, "data_ptr"):
+        return  # the library rejects NULL and host pointers itself (INSP_EINVAL)
+    import torch
+    if x.dtype != getattr(torch, dtype):
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if x.numel() < numel:
+        raise ValueError(f"{name} holds {x.numel()} elements, {numel} needed")
+    if x.is_cuda and x.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {x.device}, not on the current device cuda:{torch.cuda.current_device()}")
+
+
 def insp_scorer_eval(m, feat, n, score, stream=None) -> None:
+    _check_tensor("feat", feat, "int32", 16 * n)
+    _check_tensor("score", score, "int64", n)
     check(lib().insp_scorer_eval(m, ptr(feat), n, ptr(score), stream_ptr(stream)))
 
 

@@ -66,3 +66,21 @@ def test_binding_constants_match_the_header():
         assert int(defs[name]) == code, name
     assert re.search(r"#define\s+INSP_SCORE_TIMEOUT\s+INT64_MIN\b", hdr)
     assert _lib.INSP_SCORE_TIMEOUT == -(2 ** 63)
+
+
+def test_scorer_eval_wrapper_checks_its_tensors():
+    """The binding checks dtype, layout and length before taking raw pointers (no GPU needed:
+    the checks run before the library is called)."""
+    import torch
+    from paper_2404_03226_b300 import _lib
+    f32 = torch.zeros(4 * 16, dtype=torch.float32)
+    i32 = torch.zeros(4 * 16, dtype=torch.int32)
+    i64 = torch.zeros(4, dtype=torch.int64)
+    with pytest.raises(TypeError):
+        _lib.insp_scorer_eval(None, f32, 4, i64)
+    with pytest.raises(TypeError):
+        _lib.insp_scorer_eval(None, i32, 4, i64.to(torch.int32))
+    with pytest.raises(ValueError):
+        _lib.insp_scorer_eval(None, i32[: 3 * 16], 4, i64)
+    with pytest.raises(ValueError):
+        _lib.insp_scorer_eval(None, i32.view(16, 4).t(), 4, i64)
