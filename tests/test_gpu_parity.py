@@ -403,3 +403,55 @@ def test_machine_destroyed_before_its_batches():
             compare_dag(b, d, g, m)
         del B, s  # the first destroy leaves the machine to the second, which frees it
         gc.collect()
+
+
+def test_concurrent_loads_from_host_threads():
+    """Batches of one machine loaded from three host threads at once (each load on its batch's own
+    stream, the machine's spare lists shared) while another batch evaluates, as the serving loop
+    does: every schedule equals the oracle's."""
+    import threading
+    from types import SimpleNamespace
+    import torch
+    import paper_2404_03226_b300 as P
+    from paper_2404_03226_b300 import _lib
+    b = inputs.layered(24, cfg=90, first=11, n_max=500)
+    m = inputs.MACHINE_LAYERED
+    M = P.Machine(m.n_cpu, m.n_gpu, m.xfer_ns)
+    running = P.DagBatch(M, b)
+    ia0, ie0, s0 = running.evaluate(stream=torch.cuda.Stream())  # in flight while the loads run
+    handles, errors = [None] * 3, []
+
+    def load(k):
+        try:
+            handles[k] = _lib.insp_batch_load_csr(M.handle, b.ndag, np.ascontiguousarray(b.task_base, np.int64),
+                                                  np.ascontiguousarray(b.edge_base, np.int64),
+                                                  np.ascontiguousarray(b.row_ptr, np.int32),
+                                                  np.ascontiguousarray(b.col_idx, np.int32),
+                                                  np.ascontiguousarray(b.type, np.uint8), b.n_types,
+                                                  np.ascontiguousarray(b.type_cost, np.int64), None)
+        except Exception as exc:  # reported below
+            errors.append(exc)
+
+    threads = [threading.Thread(target=load, args=(k,)) for k in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    results = [(ia0, ie0, s0)]
+    for h in handles:
+        n = int(b.task_base[-1])
+        ia = torch.empty(n, dtype=torch.int32, device="cuda"); ie = torch.empty_like(ia)
+        w = torch.empty_like(ia); st = torch.empty(n, dtype=torch.int64, device="cuda"); en = torch.empty_like(st)
+        mk = torch.empty(b.ndag, dtype=torch.int64, device="cuda")
+        _lib.insp_evaluate_batch(h, None, ia, ie, w, st, en, mk)
+        torch.cuda.synchronize()
+        assert _lib.insp_batch_status(h) == 0
+        results.append((ia, ie, SimpleNamespace(worker=w, start=st, end=en, makespan=mk)))
+        _lib.insp_batch_destroy(h)
+    for ia, ie, s in results:
+        g = dict(ia=ia.cpu().numpy(), ie=ie.cpu().numpy(), worker=s.worker.cpu().numpy(),
+                 start=s.start.cpu().numpy(), end=s.end.cpu().numpy(), makespan=s.makespan.cpu().numpy())
+        for d in range(b.ndag):
+            compare_dag(b, d, g, m)
